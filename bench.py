@@ -1,0 +1,478 @@
+#!/usr/bin/env python3
+"""Benchmark of the nested-mesh harmonic volume-potential path on GB300.
+
+One step = one pass of the hot path over the workload's harmonics, through the
+C ABI: V_{k1}[p1] on the fundamental grid, then for each harmonic n >= 2 the
+restriction of the lower harmonics onto grid n, the fused source assembly and the
+volume potential.  Kernel spectra are built before timing (cached per plan, timed
+separately); the incident field p1 is an input and is generated before timing.
+
+Default workload: harmonics 1-3 on nested 128^3 / 192^3 / 256^3 focal grids of a
+3 cm / 6 cm / 1.1 MHz bowl in water (the FP32-vs-FP64 configuration).
+
+Prints ONE JSON line (rank 0).  --impl reference times the FP64 CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "voxel-potentials/s"
+L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="nested3", choices=["small", "nested3", "nested5"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--check", action="store_true", help="per-harmonic rel-L2 vs the FP64 oracle (slow)")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------------------- distributed
+
+def dist_init(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def max_over_ranks(value: float, world: int) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# --------------------------------------------------------------------------- workload on GPU
+
+def sweep_bytes(n, m, harmonic, fused_source: bool):
+    """Algorithmic bytes of each of the five sweeps of one volume-potential evaluation."""
+    Nx, Ny, Nz = n
+    Mx, My, Mz = m
+    W = 8
+    nvox = Nx * Ny * Nz
+    src_fields = (harmonic - 1) if fused_source else 1
+    octant = (Mx // 2 + 1) * (My // 2 + 1) * (Mz // 2 + 1)
+    return [
+        W * (src_fields * nvox + Mx * Ny * Nz),
+        W * (Mx * Ny * Nz + Mx * My * Nz),
+        W * (2 * Mx * My * Nz + octant),
+        W * (Mx * My * Nz + Mx * Ny * Nz),
+        W * (Mx * Ny * Nz + nvox),
+    ]
+
+
+SWEEP_NAMES = ["x_forward_source", "y_forward", "z_conv", "y_inverse", "x_inverse"]
+
+
+class GpuWorkload:
+    def __init__(self, w, device):
+        import torch
+        from paper_2011_03009_gb300 import synth
+        from paper_2011_03009_gb300 import vp
+        self.w, self.vp, self.torch, self.dev = w, vp, torch, device
+        pts = synth.sample_bowl_points(w.bowl, w.n_points, w.seed)
+        self.pts = torch.from_numpy(pts).to(device)
+        c64 = torch.complex64
+        # inputs: p1 on the grid of harmonic 2 (and on the fundamental grid for V_{k1})
+        self.p1 = torch.empty(w.p1_grid.n, dtype=c64, device=device)
+        vp.vp_incident_field(w.p1_grid, self.pts, w.bowl, w.medium, self.p1)
+        self.p1_v1 = None
+        if w.v1_grid is not None:
+            self.p1_v1 = torch.empty(w.v1_grid.n, dtype=c64, device=device)
+            vp.vp_incident_field(w.v1_grid, self.pts, w.bowl, w.medium, self.p1_v1)
+        self.plans, self.outs = {}, {}
+        if w.v1_grid is not None:
+            self.plans[1] = vp.vp_plan(w.v1_grid, 1, w.bowl.f0, w.medium)
+            self.outs[1] = torch.empty(w.v1_grid.n, dtype=c64, device=device)
+        home = {1: w.p1_grid}
+        self.restrict_bufs = {}
+        for st in w.steps:
+            n = st.harmonic
+            self.plans[n] = vp.vp_plan(st.grid, n, w.bowl.f0, w.medium)
+            self.outs[n] = torch.empty(st.grid.n, dtype=c64, device=device)
+            for m in range(1, n):
+                if home[m] is not st.grid:
+                    self.restrict_bufs[(n, m)] = torch.empty(st.grid.n, dtype=c64, device=device)
+            home[n] = st.grid
+        self.grids = {st.harmonic: st.grid for st in w.steps}
+        if w.v1_grid is not None:
+            self.grids_v1 = w.v1_grid
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for p in self.plans.values():
+            p.kernel_fft()
+        torch.cuda.synchronize()
+        self.khat_build_ms = 1e3 * (time.perf_counter() - t0)
+
+    def launches_per_step(self) -> int:
+        n = 0
+        if 1 in self.plans and self.p1_v1 is not None:
+            n += 5
+        for st in self.w.steps:
+            n += 5
+        n += len(self.restrict_bufs)
+        return n
+
+    def step(self, p1=None, p1_v1=None):
+        vp = self.vp
+        w = self.w
+        p1 = self.p1 if p1 is None else p1
+        p1_v1 = self.p1_v1 if p1_v1 is None else p1_v1
+        if w.v1_grid is not None:
+            self.plans[1].apply(p1_v1, self.outs[1])
+        fields = {1: (p1, w.p1_grid)}
+        for st in w.steps:
+            n = st.harmonic
+            lower = []
+            for m in range(1, n):
+                f, g = fields[m]
+                if g is st.grid:
+                    lower.append(f)
+                else:
+                    buf = self.restrict_bufs[(n, m)]
+                    vp.vp_restrict_to_nested_box(g, f, st.grid, buf)
+                    lower.append(buf)
+            plan = self.plans[n]
+            plan.source_assemble(lower)
+            plan.apply(None, self.outs[n])
+            fields[n] = (self.outs[n], st.grid)
+
+    def plan_geometry(self):
+        out = {}
+        for n, p in self.plans.items():
+            inf = p.info()
+            out[n] = (tuple(inf.n), tuple(inf.m))
+        return out
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    from paper_2011_03009_gb300 import synth
+
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    w = synth.WORKLOADS[args.workload]()
+    gw = GpuWorkload(w, device)
+    voxels = w.voxels_per_step
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(max(3, args.warmup)):
+        gw.step()
+    torch.cuda.synchronize()
+
+    for p in gw.plans.values():
+        p.profile_read(reset=True)
+        p.profile_enable(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    t_wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()  # evict the previous step's data from L2 (outside the timed events)
+        ev[i][0].record(stream)
+        gw.step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    t_wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = max_over_ranks(sum(step_ms), world)
+    ms_per_step = total_ms / args.steps
+    value = voxels * args.steps * world / (total_ms / 1e3)
+
+    # per-sweep kernel timing (events on the launching stream, inside the timed region)
+    geo = gw.plan_geometry()
+    sweeps = []
+    for n, p in gw.plans.items():
+        p.profile_enable(False)
+        ms, cnt = p.profile_read(reset=True)
+        nn, mm = geo[n]
+        fused = n >= 2
+        by = sweep_bytes(nn, mm, n, fused)
+        for s in range(5):
+            if cnt[s] == 0:
+                continue
+            per_launch_ms = ms[s] / cnt[s]
+            sweeps.append({"harmonic": n, "sweep": SWEEP_NAMES[s], "n": list(nn), "m": list(mm),
+                           "launches": cnt[s], "ms_per_launch": per_launch_ms, "bytes_per_launch": by[s],
+                           "gbs": by[s] / (per_launch_ms * 1e-3) / 1e9, "total_ms": ms[s]})
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except OSError:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    dom = max(sweeps, key=lambda r: r["total_ms"]) if sweeps else None
+    roofline = None
+    if dom:
+        roofline = {"bound": "hbm", "kernel": f"line_sweep_kernel<conv> harmonic {dom['harmonic']}"
+                    if dom["sweep"] == "z_conv" else f"col_sweep_kernel {dom['sweep']} harmonic {dom['harmonic']}",
+                    "achieved": round(dom["gbs"], 1), "peak": hbm_peak, "peak_source": peak_src,
+                    "unit": "GB/s", "frac": round(dom["gbs"] / hbm_peak, 4), "traffic": None,
+                    "bytes_per_launch": dom["bytes_per_launch"], "ms_per_launch": round(dom["ms_per_launch"], 5)}
+    # whole-apply model bytes ((25 + n) words per voxel for M = 2N) per harmonic
+    per_h = {}
+    for n, p in gw.plans.items():
+        rows = [r for r in sweeps if r["harmonic"] == n]
+        t = sum(r["ms_per_launch"] for r in rows)
+        by = sum(r["bytes_per_launch"] for r in rows)
+        vox = geo[n][0][0] * geo[n][0][1] * geo[n][0][2]
+        per_h[str(n)] = {"voxels": vox, "apply_ms": round(t, 4), "voxels_per_s": vox / (t * 1e-3),
+                         "model_gbs": round(by / (t * 1e-3) / 1e9, 1), "hbm_frac": round(by / (t * 1e-3) / 1e9 / hbm_peak, 4)}
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = measure_e2e(gw, args, world, voxels, flush)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w)
+
+    check = None
+    if args.check and rank == 0:
+        check = rel_l2_check(gw)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+        "config": {"workload": w.name, "harmonics": ([1] if w.v1_grid is not None else []) + [s.harmonic for s in w.steps],
+                   "grids": {str(n): list(geo[n][0]) for n in geo}, "embedding": {str(n): list(geo[n][1]) for n in geo},
+                   "voxels_per_step": voxels, "bowl_points": w.n_points, "parallelism": f"replicas x{world}",
+                   "l2": "flushed between steps (256 MiB write outside the timed events)",
+                   "khat_build_ms": round(gw.khat_build_ms, 2)},
+        "roofline": roofline, "per_harmonic": per_h, "sweeps": sweeps,
+        "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
+        "gpu_launches": gw.launches_per_step() * args.steps, "wall_s_timed": round(t_wall, 4),
+    }
+    if check is not None:
+        line["rel_l2_vs_oracle"] = check
+    if rank == 0:
+        print(json.dumps(line))
+
+
+def measure_e2e(gw, args, world, voxels, flush):
+    """Same metric through the public API with pinned host inputs/outputs, copies inside."""
+    import torch
+    dev = gw.dev
+    h_p1 = gw.p1.cpu().pin_memory()
+    h_v1 = gw.p1_v1.cpu().pin_memory() if gw.p1_v1 is not None else None
+    h_out = {n: torch.empty(o.shape, dtype=o.dtype).pin_memory() for n, o in gw.outs.items()}
+    d_p1 = torch.empty_like(gw.p1)
+    d_v1 = torch.empty_like(gw.p1_v1) if gw.p1_v1 is not None else None
+    stream = torch.cuda.current_stream()
+    bi = h_p1.numel() * 8 + (h_v1.numel() * 8 if h_v1 is not None else 0)
+    bo = sum(o.numel() * 8 for o in h_out.values())
+    K = max(3, min(args.steps, 10))
+
+    def one():
+        d_p1.copy_(h_p1, non_blocking=True)
+        if d_v1 is not None:
+            d_v1.copy_(h_v1, non_blocking=True)
+        gw.step(p1=d_p1, p1_v1=d_v1)
+        for n, o in gw.outs.items():
+            h_out[n].copy_(o, non_blocking=True)
+
+    for _ in range(2):
+        one()
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = 0.0
+    for _ in range(K):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        one()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms += a.elapsed_time(b)
+    ms = max_over_ranks(ms, world)
+    return {"value": voxels * K * world / (ms / 1e3), "unit": METRIC, "h2d_bytes_per_step": bi,
+            "d2h_bytes_per_step": bo, "steps": K}
+
+
+# --------------------------------------------------------------------------- CPU oracle legs
+
+def oracle_sample(w):
+    """Bounded sample of the workload for the FP64 oracle: the fundamental-grid operator
+    V_{k1}[p1] on the first grid of the run (kernel spectrum prepared outside the timing)."""
+    import numpy as np
+    from oracle import physics, potential
+    from paper_2011_03009_gb300 import synth
+    g = w.v1_grid if w.v1_grid is not None else w.steps[0].grid
+    n_h = 1 if w.v1_grid is not None else w.steps[0].harmonic
+    k = physics.wavenumber(n_h, w.bowl.f0, w.medium)
+    f = synth.smooth_blob_field(g, (w.bowl.l, 0.0, 0.0), 20 * g.h, k.real)
+    khat = potential.kernel_spectrum(g.n, g.h, k)
+    return g, f, k, khat, np.prod(g.n)
+
+
+def cpu_baseline(w):
+    from oracle import potential
+    g, f, k, khat, vox = oracle_sample(w)
+    reps, t_total = 0, 0.0
+    while t_total < 10.0 and reps < 20:
+        t0 = time.perf_counter()
+        potential.apply_fft(f, g.h, k, khat=khat)
+        t_total += time.perf_counter() - t0
+        reps += 1
+    return {"value": vox * reps / t_total, "unit": METRIC, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"FP64 oracle apply_fft (zero-padded FFT convolution, spectrum precomputed) on the "
+                      f"{'x'.join(map(str, g.n))} grid, {reps} repetitions"}
+
+
+def rel_l2_check(gw):
+    import numpy as np
+    from oracle import cascade, interp, physics, potential
+    w = gw.w
+    res = {}
+    if w.v1_grid is not None:
+        p1 = gw.p1_v1.cpu().numpy().astype(np.complex128)
+        ref = potential.apply_fft(p1, w.v1_grid.h, physics.wavenumber(1, w.bowl.f0, w.medium))
+        got = gw.outs[1].cpu().numpy().astype(np.complex128)
+        res["1"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    fields = {1: (gw.p1.cpu().numpy().astype(np.complex128), w.p1_grid)}
+    for st in w.steps:
+        n = st.harmonic
+        lower = []
+        for m in range(1, n):
+            f, g = fields[m]
+            lower.append(f if g is st.grid else interp.restrict_trilinear(f, g, st.grid))
+        ref = cascade.harmonic(n, lower, st.grid.h, w.bowl.f0, w.medium)
+        got = gw.outs[n].cpu().numpy().astype(np.complex128)
+        res[str(n)] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        fields[n] = (got, st.grid)
+    return res
+
+
+def run_reference(args, world, rank):
+    from paper_2011_03009_gb300 import synth
+    from oracle import potential
+    if rank != 0:
+        return
+    w = synth.WORKLOADS[args.workload]()
+    g, f, k, khat, vox = oracle_sample(w)
+    for _ in range(max(1, args.warmup)):
+        potential.apply_fft(f, g.h, k, khat=khat)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        potential.apply_fft(f, g.h, k, khat=khat)
+    dt = time.perf_counter() - t0
+    value = vox * args.steps / dt
+    sample = (f"FP64 oracle apply_fft on the {'x'.join(map(str, g.n))} grid of {w.name} "
+              f"(spectrum precomputed), one evaluation per step")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+            "data": "synthetic", "config": {"workload": w.name, "sample_grid": list(g.n)},
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    world, rank, local = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    world, rank, local = dist_init(args)
+    run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

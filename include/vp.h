@@ -1,0 +1,207 @@
+/*
+ * vp.h -- C ABI of the GB300 voxel volume-potential library (libvp.so).
+ *
+ * The library evaluates, on one NVIDIA GB300 (sm_103a), the per-harmonic voxel
+ * volume potential of the nested-mesh method for weakly nonlinear focused
+ * ultrasound:
+ *
+ *     u = V_k[f],   u(x_i) = sum_{j != i} h^3 G_k(x_i - x_j) f(x_j) + S(k,h) f(x_i)
+ *
+ * with G_k(r) = exp(i k r) / (4 pi r) (Eq. 3.3), the midpoint rule off the diagonal
+ * and the equal-volume-sphere integral S(k,h) = ((1 - i k a) e^{i k a} - 1) / k^2,
+ * a = (3/(4 pi))^{1/3} h, on the diagonal (Eq. 3.9).  The sum is a 3-level Toeplitz
+ * product evaluated by zero padding to a circulant of size M >= 2N - 1 per axis
+ * and FFTs (Section 3.1).  Harmonic sources come from products of lower
+ * harmonics (Eq. 2.6, written out in Eqs. 3.5-3.8); lower harmonics move between
+ * nested grids by linear interpolation (Section 6).
+ *
+ * Conventions shared by every call
+ * - Fields are complex64: interleaved (re, im) float32 pairs, C order (nx, ny, nz),
+ *   z fastest, densely packed.  Field pointers are DEVICE pointers owned by the
+ *   caller, 8-byte aligned.
+ * - A grid is (n[3], origin[3], h): voxel (i,j,k) has centre origin + h*(i,j,k), in
+ *   metres.
+ * - Every call that takes a stream is asynchronous on that stream (a
+ *   cudaStream_t passed as void*; NULL = the legacy default stream).  Host-side
+ *   argument errors are detected before anything is enqueued.
+ * - Every function returns an int status: VP_OK (0) or a negative VP_ERR_* code.
+ *   Nothing throws across the ABI.  vp_status_string() names a code.
+ * - Thread safety: distinct plans may be used from distinct host threads; one
+ *   plan must not be used by two threads at once.
+ *
+ * Wavenumber and source coefficient (Section 2, readings of the paper):
+ *   k_n = 2 pi n f0 / c0 + i alpha(n f0),
+ *   alpha(f) [Np/m] = alpha0 [dB/m/MHz^eta] (f / 1 MHz)^eta / (20 log10 e),
+ *   C_n = -beta omega^2 n^2 / (2 rho0 c0^4), omega = 2 pi f0
+ *   (the minus sign of Eq. 3.2 is folded into C_n, so vp_apply is +int G f).
+ */
+#ifndef VP_H
+#define VP_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define VP_API __attribute__((visibility("default")))
+#else
+#define VP_API
+#endif
+
+/* ---- status codes ------------------------------------------------------------ */
+#define VP_OK               0
+#define VP_ERR_ARG         -1  /* null pointer, non-positive size or spacing, bad harmonic */
+#define VP_ERR_SIZE        -2  /* no FFT schedule for the requested embedding size        */
+#define VP_ERR_NOMEM       -3  /* device allocation failed                                 */
+#define VP_ERR_CUDA        -4  /* a CUDA runtime call or kernel launch failed              */
+#define VP_ERR_NOT_NESTED  -5  /* restriction target not inside the source grid           */
+#define VP_ERR_STATE       -6  /* call out of order (no staged source; spectrum not built) */
+#define VP_ERR_TIMEOUT     -7  /* a bounded device wait expired                            */
+#define VP_ERR_UNSUPPORTED -8  /* valid request outside what this build implements        */
+
+typedef void* vp_stream_t; /* cudaStream_t */
+
+typedef struct vp_grid {
+    int n[3];          /* voxels per axis (x, y, z), each >= 1            */
+    double origin[3];  /* centre of voxel (0,0,0), metres                  */
+    double h;          /* voxel side, metres, > 0                          */
+} vp_grid;
+
+typedef struct vp_medium {
+    double c0;      /* speed of sound, m/s                                   */
+    double rho0;    /* density, kg/m^3                                       */
+    double beta;    /* coefficient of nonlinearity                           */
+    double alpha0;  /* attenuation prefactor, dB/m/MHz^eta (>= 0)            */
+    double eta;     /* attenuation power-law exponent                        */
+} vp_medium;
+
+typedef struct vp_plan_s* vp_plan_t;
+
+/* Optional plan overrides; zero-initialise and set only what you need. */
+typedef struct vp_plan_opts {
+    int m[3];           /* embedding size per axis; 0 = smallest even 5-smooth >= 2N     */
+    int radix[3][8];    /* radix schedule per axis (product must equal M); 0-terminated,
+                           all zero = default schedule                                    */
+    int autotune;       /* nonzero: time candidate schedules at plan time on `stream`   */
+} vp_plan_opts;
+
+typedef struct vp_plan_info {
+    int n[3];
+    int m[3];
+    int radix[3][8];     /* 0-terminated                                                 */
+    double k_re, k_im;   /* k_n                                                          */
+    double c_n;          /* source coefficient C_n                                       */
+    double self_re, self_im;      /* self-cell integral S(k_n, h)                        */
+    unsigned long long workspace_bytes;  /* device bytes held by the plan               */
+    int khat_ready;      /* 1 once vp_kernel_fft has been enqueued                       */
+} vp_plan_info;
+
+/* ---- plans --------------------------------------------------------------------
+ * vp_plan: create a plan for harmonic n (>= 1) on grid g (Section 6 algorithm, step 1:
+ * one voxel mesh per harmonic).  Computes k_n and C_n, picks the embedding size M
+ * (default: smallest even 2^a 3^b 5^c >= 2N on each axis; Section 3.1 needs
+ * M >= 2N - 1, Section 6 uses 2N) and its radix schedule, and allocates the plan's
+ * device workspace (about 8 * (M_x N_y N_z + M_x M_y N_z) bytes) and the storage of
+ * the kernel spectrum (8 * prod(M/2 + 1) bytes) on the current device.
+ * `opts` may be NULL.  `stream` is used only when opts->autotune is set.
+ * Errors: VP_ERR_ARG (null pointers, n[i] < 1, h <= 0, harmonic < 1, c0 <= 0,
+ * rho0 <= 0, alpha0 < 0, f0 <= 0), VP_ERR_SIZE (M < 2N - 1, or an axis the FFT
+ * engine cannot hold: M > 1600, or a radix schedule whose product is not M or that
+ * uses a radix outside {2,3,4,5,8,16}), VP_ERR_NOMEM, VP_ERR_CUDA.
+ * On error *out is set to NULL and nothing is leaked. */
+VP_API int vp_plan(const vp_grid* g, int harmonic_n, double f0_hz, const vp_medium* m,
+                   const vp_plan_opts* opts, vp_stream_t stream, vp_plan_t* out);
+
+/* Release every device and host resource of the plan.  Synchronises the device
+ * first (pending work that uses the plan completes).  NULL is accepted. */
+VP_API int vp_destroy(vp_plan_t p);
+
+/* Fill *info.  Errors: VP_ERR_ARG. */
+VP_API int vp_plan_get_info(vp_plan_t p, vp_plan_info* info);
+
+/* ---- kernel spectrum ----------------------------------------------------------
+ * Build the spectrum of the circulant-embedded quadrature kernel (Section 6,
+ * step 2b; Eq. 3.9): the lattice h^3 G_{k_n}(|d| h) for offsets d in (-N, N)^3 placed
+ * at d mod M, the self-cell integral at d = 0 (FP64 on the device), zero at every
+ * index no offset maps to; then its 3-D FFT.  The kernel is even in every axis, so
+ * only the octant of frequencies [0, M/2]^3 is kept.  Phases k |d| h are formed in
+ * FP64 and reduced modulo 2 pi before the single-precision sine/cosine.
+ * Idempotent: later calls return VP_OK without work.  Uses a temporary device
+ * buffer of 8 * M_x M_y M_z bytes, freed before return.
+ * Errors: VP_ERR_ARG, VP_ERR_NOMEM, VP_ERR_CUDA. */
+VP_API int vp_kernel_fft(vp_plan_t p, vp_stream_t stream);
+
+/* Copy the octant spectrum (prod(M/2 + 1) complex64, C order) to/from a device
+ * buffer, e.g. to cache it across processes.  Errors: VP_ERR_ARG, VP_ERR_STATE
+ * (get before the spectrum was built), VP_ERR_CUDA. */
+VP_API int vp_kernel_spectrum_get(vp_plan_t p, void* dst_device, vp_stream_t stream);
+VP_API int vp_kernel_spectrum_set(vp_plan_t p, const void* src_device, vp_stream_t stream);
+
+/* ---- source assembly -----------------------------------------------------------
+ * f_n = C_n * sum_{m=1}^{n-1} p_m p_{n-m} (Eq. 2.6; Eqs. 3.5-3.8 for n = 2..5).
+ * lower[m-1] is p_m on the plan's grid (device pointer, N voxels), n_lower must be
+ * n - 1 (>= 1).  flags must be 0 (conjugate terms of Eq. 2.5 are not implemented).
+ * f_out != NULL: write f_n (N voxels, complex64) there.
+ * f_out == NULL: fuse the assembly with the zero padding and the first FFT sweep of
+ *   vp_apply, leaving the transformed source in the plan's workspace; the next
+ *   vp_apply(p, NULL, u, ...) on the same stream consumes it.
+ * Errors: VP_ERR_ARG (null plan or field pointer, n_lower != n - 1, flags != 0),
+ * VP_ERR_CUDA. */
+VP_API int vp_source_assemble(vp_plan_t p, const void* const* lower, int n_lower, int flags,
+                              void* f_out, vp_stream_t stream);
+
+/* ---- volume potential ----------------------------------------------------------
+ * u = V_{k_n}[f] (Eq. 3.9 via the circulant embedding of Section 3.1): zero pad f to
+ * M, forward 3-D FFT, multiply by the kernel spectrum, inverse FFT, crop to N.
+ * f == NULL uses the source staged by vp_source_assemble(..., f_out = NULL).
+ * u must not alias f.  Errors: VP_ERR_ARG (null plan or u), VP_ERR_STATE (spectrum
+ * not built, or f == NULL with nothing staged), VP_ERR_CUDA. */
+VP_API int vp_apply(vp_plan_t p, const void* f, void* u, vp_stream_t stream);
+
+/* ---- restriction between nested grids ------------------------------------------
+ * dst_field = linear (trilinear) interpolation of src_field, given on grid src, at
+ * the voxel centres of grid dst (Section 6, step 2a).  For a target coordinate on
+ * one axis, t = (x - o_src)/h_src, i0 = floor(t) clamped to [0, N-2], w = t - i0;
+ * the result is the tensor product of (1-w) v[i0] + w v[i0+1].  Axis positions are
+ * computed in FP64, weights applied in FP32.
+ * Every target centre must lie within the box spanned by the source centres (a
+ * relative slack of 1e-9 voxel is allowed); otherwise VP_ERR_NOT_NESTED unless
+ * flags & VP_RESTRICT_ZERO_OUTSIDE, which writes zero there instead.
+ * Errors: VP_ERR_ARG, VP_ERR_NOT_NESTED, VP_ERR_CUDA. */
+#define VP_RESTRICT_ZERO_OUTSIDE 1
+VP_API int vp_restrict_to_nested_box(const vp_grid* src, const void* src_field, const vp_grid* dst,
+                                     void* dst_field, int flags, vp_stream_t stream);
+
+/* ---- incident field (input generator) -------------------------------------------
+ * p1 on grid g from a bowl of focal length l and aperture radius R driven at f0 with
+ * surface pressure p0, as a monopole sum over n_points bowl points (Eq. 3.10):
+ *   p1(x) = -2 i k_1 p0 (A / n_p) sum_i G_{k_1}(x - r_i),  A = 2 pi l (l - sqrt(l^2 - R^2)).
+ * (Reading: uniform normal velocity p0/(rho0 c0) in the Rayleigh integral; the paper
+ * normalises to a radiated power instead.)  points: DEVICE pointer to n_points x 3
+ * float64 (x, y, z).  Distances and phases in FP64, reduced modulo 2 pi before the
+ * single-precision sine/cosine; accumulation in FP32 per point block, FP64 across
+ * blocks.  Errors: VP_ERR_ARG, VP_ERR_CUDA. */
+VP_API int vp_incident_field(const vp_grid* g, const double* points, int n_points, double l,
+                             double R, double f0_hz, double p0, const vp_medium* m, void* out,
+                             vp_stream_t stream);
+
+/* ---- diagnostics ----------------------------------------------------------------- */
+/* Static, NUL-terminated name of a status code. */
+VP_API const char* vp_status_string(int status);
+
+/* Per-kernel timing of vp_apply / vp_source_assemble: when enabled, the plan records
+ * a CUDA event pair around each FFT sweep it launches, on the launching stream.
+ * vp_profile_read returns, for sweep s in 0..4 (x forward with source, y forward,
+ * z forward + spectrum multiply + z inverse, y inverse, x inverse), the summed
+ * milliseconds and launch counts since the last reset, synchronising on the
+ * recorded events.  Errors: VP_ERR_ARG, VP_ERR_CUDA. */
+VP_API int vp_profile_enable(vp_plan_t p, int on);
+VP_API int vp_profile_read(vp_plan_t p, double ms[5], int count[5], int reset);
+
+/* Library build identification string (static). */
+VP_API const char* vp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VP_H */

@@ -1,0 +1,264 @@
+// Shared-memory mixed-radix FFT engine for the volume-potential sweeps.
+//
+// A CTA holds a tile of kTileB = 16 independent lines of length L in shared memory,
+// element (row i, line b) at tile[i * P + b].  Lane b of every half-warp owns line b,
+// so each half-warp touches 16 consecutive complex values (128 B) per access: no
+// bank conflicts for any radix or stride.
+//
+// Forward transforms are in-place decimation-in-frequency (DIF): natural-order input,
+// output in mixed-radix digit-reversed order.  Inverse transforms are the matching
+// decimation-in-time (DIT) passes run in reverse order with conjugate twiddles: they
+// take the digit-reversed order and return natural order, scaled by L.  The
+// convolution never needs the natural frequency order, so no permutation pass exists;
+// the spectrum multiply looks frequencies up through per-axis position tables.
+//
+// DIF pass p with radix R over sub-transforms of length Lp (stride s = Lp / R):
+//   for every block start b0 (multiple of Lp) and k in [0, s):
+//     v[r] = x[b0 + k + r s];  y = DFT_R(v);  x[b0 + k + q s] = y[q] * w_Lp^(q k)
+// with w_Lp = exp(-2 pi i / Lp) = tw[L / Lp].  The DIT pass is the conjugate transpose
+// of the same step.
+#pragma once
+
+#include "vp_internal.cuh"
+
+namespace vp {
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// a * conj(b)
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// multiply by -i (forward) or +i (inverse)
+template <bool INV>
+__device__ __forceinline__ float2 mul_mi(float2 a) {
+  return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+// multiply by the constant (cr, ci) or its conjugate
+template <bool INV>
+__device__ __forceinline__ float2 mul_const(float2 a, float cr, float ci) {
+  const float c = INV ? -ci : ci;
+  return make_float2(fmaf(a.x, cr, -a.y * c), fmaf(a.x, c, a.y * cr));
+}
+
+// ---- small DFTs: y[q] = sum_r v[r] exp(-+2 pi i r q / R), natural order in and out ----
+
+template <bool INV>
+__device__ __forceinline__ void dft2(float2& a, float2& b) {
+  float2 t = a;
+  a = cadd(t, b);
+  b = csub(t, b);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft4(float2& v0, float2& v1, float2& v2, float2& v3) {
+  float2 t0 = cadd(v0, v2), t1 = csub(v0, v2);
+  float2 t2 = cadd(v1, v3), t3 = mul_mi<INV>(csub(v1, v3));
+  v0 = cadd(t0, t2);
+  v2 = csub(t0, t2);
+  v1 = cadd(t1, t3);
+  v3 = csub(t1, t3);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft3(float2* v) {
+  const float c = -0.5f, s = 0.86602540378443865f;  // cos(2pi/3), sin(2pi/3)
+  float2 t = cadd(v[1], v[2]);
+  float2 d = csub(v[1], v[2]);
+  float2 m = make_float2(fmaf(c, t.x, v[0].x), fmaf(c, t.y, v[0].y));
+  v[0] = cadd(v[0], t);
+  float2 sd = mul_mi<INV>(cscale(d, s));
+  v[1] = cadd(m, sd);
+  v[2] = csub(m, sd);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft5(float2* v) {
+  const float c1 = 0.30901699437494742f;   // cos(2pi/5)
+  const float c2 = -0.80901699437494742f;  // cos(4pi/5)
+  const float s1 = 0.95105651629515357f;   // sin(2pi/5)
+  const float s2 = 0.58778525229247313f;   // sin(4pi/5)
+  float2 t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]);
+  float2 d1 = csub(v[1], v[4]), d2 = csub(v[2], v[3]);
+  float2 a1 = make_float2(v[0].x + c1 * t1.x + c2 * t2.x, v[0].y + c1 * t1.y + c2 * t2.y);
+  float2 a2 = make_float2(v[0].x + c2 * t1.x + c1 * t2.x, v[0].y + c2 * t1.y + c1 * t2.y);
+  float2 b1 = make_float2(s1 * d1.x + s2 * d2.x, s1 * d1.y + s2 * d2.y);
+  float2 b2 = make_float2(s2 * d1.x - s1 * d2.x, s2 * d1.y - s1 * d2.y);
+  v[0] = cadd(v[0], cadd(t1, t2));
+  float2 ib1 = mul_mi<INV>(b1), ib2 = mul_mi<INV>(b2);
+  v[1] = cadd(a1, ib1);
+  v[4] = csub(a1, ib1);
+  v[2] = cadd(a2, ib2);
+  v[3] = csub(a2, ib2);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft8(float2* v) {
+  const float c = 0.70710678118654752f;
+  // radix-2 decimation in time over two 4-point DFTs
+  dft4<INV>(v[0], v[2], v[4], v[6]);
+  dft4<INV>(v[1], v[3], v[5], v[7]);
+  float2 o1 = mul_const<INV>(v[3], c, -c);
+  float2 o2 = mul_mi<INV>(v[5]);
+  float2 o3 = mul_const<INV>(v[7], -c, -c);
+  float2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6], o0 = v[1];
+  v[0] = cadd(e0, o0);
+  v[4] = csub(e0, o0);
+  v[1] = cadd(e1, o1);
+  v[5] = csub(e1, o1);
+  v[2] = cadd(e2, o2);
+  v[6] = csub(e2, o2);
+  v[3] = cadd(e3, o3);
+  v[7] = csub(e3, o3);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft16(float2* v) {
+  const float c1 = 0.92387953251128674f;  // cos(pi/8)
+  const float s1 = 0.38268343236508977f;  // sin(pi/8)
+  const float c = 0.70710678118654752f;
+  // 4 x 4: first DFT4 over r1 for each r2 (elements r2 + 4 r1)
+#pragma unroll
+  for (int r2 = 0; r2 < 4; ++r2) dft4<INV>(v[r2], v[r2 + 4], v[r2 + 8], v[r2 + 12]);
+  // now v[r2 + 4 q1] = Z_{r2}[q1]; twiddle by w16^(r2 q1)
+  v[5] = mul_const<INV>(v[5], c1, -s1);    // r2=1,q1=1: w^1
+  v[9] = mul_const<INV>(v[9], c, -c);      // r2=1,q1=2: w^2
+  v[13] = mul_const<INV>(v[13], s1, -c1);  // r2=1,q1=3: w^3
+  v[6] = mul_const<INV>(v[6], c, -c);      // r2=2,q1=1: w^2
+  v[10] = mul_mi<INV>(v[10]);              // r2=2,q1=2: w^4
+  v[14] = mul_const<INV>(v[14], -c, -c);   // r2=2,q1=3: w^6
+  v[7] = mul_const<INV>(v[7], s1, -c1);    // r2=3,q1=1: w^3
+  v[11] = mul_const<INV>(v[11], -c, -c);   // r2=3,q1=2: w^6
+  v[15] = mul_const<INV>(v[15], -c1, s1);  // r2=3,q1=3: w^9
+  // second DFT4 over r2 for each q1: y[q1 + 4 q2]
+  float2 t[16];
+#pragma unroll
+  for (int q1 = 0; q1 < 4; ++q1) {
+    float2 a = v[4 * q1 + 0], b = v[4 * q1 + 1], d = v[4 * q1 + 2], e = v[4 * q1 + 3];
+    dft4<INV>(a, b, d, e);
+    t[q1 + 0] = a;
+    t[q1 + 4] = b;
+    t[q1 + 8] = d;
+    t[q1 + 12] = e;
+  }
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = t[i];
+}
+
+template <int R, bool INV>
+__device__ __forceinline__ void dft(float2* v) {
+  if constexpr (R == 2) dft2<INV>(v[0], v[1]);
+  else if constexpr (R == 3) dft3<INV>(v);
+  else if constexpr (R == 4) dft4<INV>(v[0], v[1], v[2], v[3]);
+  else if constexpr (R == 5) dft5<INV>(v);
+  else if constexpr (R == 8) dft8<INV>(v);
+  else if constexpr (R == 16) dft16<INV>(v);
+}
+
+// ---- passes over a shared-memory tile -----------------------------------------------
+
+// Forward DIF pass.  Rows >= rows_nz are treated as zero without being read.
+template <int R, int P>
+__device__ __forceinline__ void dif_pass(float2* tile, int L, int Lp, const float2* __restrict__ tw,
+                                         int rows_nz) {
+  const int s = Lp / R;
+  const int tws = L / Lp;
+  const int nb = (L / R) * kTileB;
+  for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+    const int b = t & (kTileB - 1);
+    const int u = t >> 4;
+    const int blk = u / s;
+    const int k = u - blk * s;
+    const int base = blk * Lp + k;
+    float2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int row = base + r * s;
+      v[r] = row < rows_nz ? tile[row * P + b] : make_float2(0.f, 0.f);
+    }
+    dft<R, false>(v);
+    if (k != 0) {
+#pragma unroll
+      for (int q = 1; q < R; ++q) v[q] = cmul(v[q], __ldg(&tw[q * k * tws]));
+    }
+#pragma unroll
+    for (int q = 0; q < R; ++q) tile[(base + q * s) * P + b] = v[q];
+  }
+}
+
+// Inverse DIT pass (conjugate transpose of dif_pass).
+template <int R, int P>
+__device__ __forceinline__ void dit_pass(float2* tile, int L, int Lp, const float2* __restrict__ tw) {
+  const int s = Lp / R;
+  const int tws = L / Lp;
+  const int nb = (L / R) * kTileB;
+  for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+    const int b = t & (kTileB - 1);
+    const int u = t >> 4;
+    const int blk = u / s;
+    const int k = u - blk * s;
+    const int base = blk * Lp + k;
+    float2 v[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) v[q] = tile[(base + q * s) * P + b];
+    if (k != 0) {
+#pragma unroll
+      for (int q = 1; q < R; ++q) v[q] = cmulc(v[q], __ldg(&tw[q * k * tws]));
+    }
+    dft<R, true>(v);
+#pragma unroll
+    for (int r = 0; r < R; ++r) tile[(base + r * s) * P + b] = v[r];
+  }
+}
+
+template <int P>
+__device__ __forceinline__ void dif_pass_rt(int R, float2* tile, int L, int Lp,
+                                            const float2* __restrict__ tw, int rows_nz) {
+  switch (R) {
+    case 16: dif_pass<16, P>(tile, L, Lp, tw, rows_nz); break;
+    case 8: dif_pass<8, P>(tile, L, Lp, tw, rows_nz); break;
+    case 4: dif_pass<4, P>(tile, L, Lp, tw, rows_nz); break;
+    case 2: dif_pass<2, P>(tile, L, Lp, tw, rows_nz); break;
+    case 5: dif_pass<5, P>(tile, L, Lp, tw, rows_nz); break;
+    case 3: dif_pass<3, P>(tile, L, Lp, tw, rows_nz); break;
+    default: break;
+  }
+}
+
+template <int P>
+__device__ __forceinline__ void dit_pass_rt(int R, float2* tile, int L, int Lp,
+                                            const float2* __restrict__ tw) {
+  switch (R) {
+    case 16: dit_pass<16, P>(tile, L, Lp, tw); break;
+    case 8: dit_pass<8, P>(tile, L, Lp, tw); break;
+    case 4: dit_pass<4, P>(tile, L, Lp, tw); break;
+    case 2: dit_pass<2, P>(tile, L, Lp, tw); break;
+    case 5: dit_pass<5, P>(tile, L, Lp, tw); break;
+    case 3: dit_pass<3, P>(tile, L, Lp, tw); break;
+    default: break;
+  }
+}
+
+// Full forward transform of the tile (DIF, digit-reversed output).
+template <int P>
+__device__ __forceinline__ void tile_forward(float2* tile, const AxisDesc& ax, int rows_nz) {
+  for (int p = 0; p < ax.npass; ++p) {
+    dif_pass_rt<P>(ax.radix[p], tile, ax.L, ax.lp[p], ax.tw, p == 0 ? rows_nz : ax.L);
+    __syncthreads();
+  }
+}
+
+// Full inverse transform of the tile (DIT, digit-reversed input, natural output, x L).
+template <int P>
+__device__ __forceinline__ void tile_inverse(float2* tile, const AxisDesc& ax) {
+  for (int p = ax.npass - 1; p >= 0; --p) {
+    dit_pass_rt<P>(ax.radix[p], tile, ax.L, ax.lp[p], ax.tw);
+    __syncthreads();
+  }
+}
+
+}  // namespace vp

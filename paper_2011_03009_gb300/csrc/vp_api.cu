@@ -1,0 +1,620 @@
+// C ABI of libvp.so: plans, kernel spectrum, source assembly, volume potential,
+// restriction and incident field.  Host-side validation happens before anything is
+// enqueued; every CUDA error becomes VP_ERR_CUDA.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "vp.h"
+#include "vp_internal.cuh"
+
+using vp::AxisDesc;
+using vp::ColSweep;
+using vp::LineSweep;
+
+namespace {
+
+constexpr double kPi = 3.141592653589793238462643383279502884;
+
+struct ProfRec {
+  int sweep;
+  cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct vp_plan_s {
+  int dev = 0;
+  int n[3] = {0, 0, 0};
+  double origin[3] = {0, 0, 0};
+  double h = 0;
+  int harmonic = 0;
+  double f0 = 0;
+  vp_medium med{};
+  double kr = 0, ki = 0, cn = 0, self_re = 0, self_im = 0;
+  int m[3] = {0, 0, 0};
+  int oct[3] = {0, 0, 0};
+  int radix[3][vp::kMaxPass] = {};
+  int npass[3] = {0, 0, 0};
+  float2* tw[3] = {nullptr, nullptr, nullptr};
+  int* pos[3] = {nullptr, nullptr, nullptr};   // frequency -> position after the DIF passes
+  int* fold[3] = {nullptr, nullptr, nullptr};  // position -> min(f, M - f)
+  float2* khat = nullptr;
+  float2* wsA = nullptr;  // M_x N_y N_z
+  float2* wsB = nullptr;  // M_x M_y N_z
+  unsigned long long bytes = 0;
+  bool khat_ready = false;
+  bool staged = false;
+  bool prof_on = false;
+  std::vector<ProfRec> prof;
+  size_t prof_used = 0;
+  double prof_ms[5] = {0, 0, 0, 0, 0};
+  int prof_cnt[5] = {0, 0, 0, 0, 0};
+};
+
+namespace {
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return VP_OK;
+  if (e == cudaErrorMemoryAllocation) return VP_ERR_NOMEM;
+  return VP_ERR_CUDA;
+}
+
+#define VP_TRY_CUDA(expr)                    \
+  do {                                       \
+    cudaError_t _e = (expr);                 \
+    if (_e != cudaSuccess) return cuda_status(_e); \
+  } while (0)
+
+bool grid_ok(const vp_grid* g) {
+  if (!g) return false;
+  for (int a = 0; a < 3; ++a)
+    if (g->n[a] < 1 || !std::isfinite(g->origin[a])) return false;
+  return std::isfinite(g->h) && g->h > 0;
+}
+
+bool medium_ok(const vp_medium* m) {
+  return m && m->c0 > 0 && m->rho0 > 0 && m->alpha0 >= 0 && std::isfinite(m->beta) &&
+         std::isfinite(m->eta) && std::isfinite(m->alpha0) && std::isfinite(m->c0);
+}
+
+// alpha(f) [Np/m] from alpha0 [dB/m/MHz^eta]
+double attenuation(double f, const vp_medium& m) {
+  return m.alpha0 * std::pow(f / 1.0e6, m.eta) / (20.0 * std::log10(std::exp(1.0)));
+}
+
+bool smooth5(int v) {
+  for (int p : {2, 3, 5})
+    while (v % p == 0) v /= p;
+  return v == 1;
+}
+
+int default_m(int n) {
+  int m = 2 * n;
+  while (!smooth5(m)) m += 2;
+  return m;
+}
+
+// Default radix schedule: as few passes as possible, radix <= 16, power-of-two bits
+// spread evenly over the power-of-two passes, then the 5s, then the 3s.
+int default_schedule(int L, int* out) {
+  int a = 0, b = 0, c = 0, v = L;
+  while (v % 2 == 0) { v /= 2; ++a; }
+  while (v % 3 == 0) { v /= 3; ++b; }
+  while (v % 5 == 0) { v /= 5; ++c; }
+  if (v != 1) return 0;
+  int np = 0;
+  const int p2 = (a + 3) / 4;
+  for (int i = 0; i < p2; ++i) {
+    const int bits = a / p2 + (i < a % p2 ? 1 : 0);
+    out[np++] = 1 << bits;
+  }
+  for (int i = 0; i < c; ++i) out[np++] = 5;
+  for (int i = 0; i < b; ++i) out[np++] = 3;
+  if (np > vp::kMaxPass) return 0;
+  for (int i = np; i < vp::kMaxPass; ++i) out[i] = 0;
+  return np;
+}
+
+bool radix_ok(int r) { return r == 2 || r == 3 || r == 4 || r == 5 || r == 8 || r == 16; }
+
+void free_plan(vp_plan_s* p) {
+  if (!p) return;
+  for (int a = 0; a < 3; ++a) {
+    cudaFree(p->tw[a]);
+    cudaFree(p->pos[a]);
+    cudaFree(p->fold[a]);
+  }
+  cudaFree(p->khat);
+  cudaFree(p->wsA);
+  cudaFree(p->wsB);
+  for (auto& r : p->prof) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  delete p;
+}
+
+template <typename T>
+int upload(T** dst, const std::vector<T>& v, unsigned long long* bytes) {
+  VP_TRY_CUDA(cudaMalloc((void**)dst, v.size() * sizeof(T)));
+  *bytes += v.size() * sizeof(T);
+  VP_TRY_CUDA(cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return VP_OK;
+}
+
+int build_axis_tables(vp_plan_s* p, int a) {
+  const int L = p->m[a];
+  const int np = p->npass[a];
+  std::vector<float2> tw(L);
+  for (int t = 0; t < L; ++t) {
+    const double ang = 2.0 * kPi * (double)t / (double)L;
+    tw[t] = make_float2((float)std::cos(ang), (float)-std::sin(ang));
+  }
+  // position of frequency f after the DIF passes: f = q0 + R0 q1 + R0 R1 q2 + ...,
+  // position = q0 s0 + q1 s1 + ..., s_i = L / (R0 ... Ri)
+  std::vector<int> stride(np);
+  int acc = L;
+  for (int i = 0; i < np; ++i) {
+    acc /= p->radix[a][i];
+    stride[i] = acc;
+  }
+  std::vector<int> pos(L), fold(L);
+  for (int pp = 0; pp < L; ++pp) {
+    int f = 0, mul = 1;
+    for (int i = 0; i < np; ++i) {
+      const int q = (pp / stride[i]) % p->radix[a][i];
+      f += q * mul;
+      mul *= p->radix[a][i];
+    }
+    pos[f] = pp;
+    fold[pp] = std::min(f, L - f);
+  }
+  int st;
+  if ((st = upload(&p->tw[a], tw, &p->bytes)) != VP_OK) return st;
+  if ((st = upload(&p->pos[a], pos, &p->bytes)) != VP_OK) return st;
+  if ((st = upload(&p->fold[a], fold, &p->bytes)) != VP_OK) return st;
+  return VP_OK;
+}
+
+AxisDesc axis_desc(const vp_plan_s* p, int a) {
+  AxisDesc d{};
+  d.L = p->m[a];
+  d.npass = p->npass[a];
+  int lp = d.L;
+  for (int i = 0; i < vp::kMaxPass; ++i) {
+    d.radix[i] = p->radix[a][i];
+    d.lp[i] = i < d.npass ? lp : 0;
+    if (i < d.npass) lp /= d.radix[i];
+  }
+  d.tw = p->tw[a];
+  return d;
+}
+
+std::complex<double> self_cell_host(std::complex<double> k, double h) {
+  const double a = std::cbrt(3.0 / (4.0 * kPi)) * h;
+  const std::complex<double> ka = k * a, I(0.0, 1.0);
+  if (std::abs(ka) < 0.1) {
+    std::complex<double> total = 0.0, term = 1.0;
+    for (int m = 0; m < 24; ++m) {
+      total += term / (double)(m + 2);
+      term *= I * ka / (double)(m + 1);
+    }
+    return total * a * a;
+  }
+  return ((1.0 - I * ka) * std::exp(I * ka) - 1.0) / (k * k);
+}
+
+int prof_begin(vp_plan_s* p, int sweep, cudaStream_t s, ProfRec** rec) {
+  *rec = nullptr;
+  if (!p->prof_on) return VP_OK;
+  if (p->prof_used == p->prof.size()) {
+    ProfRec r{};
+    VP_TRY_CUDA(cudaEventCreate(&r.a));
+    VP_TRY_CUDA(cudaEventCreate(&r.b));
+    p->prof.push_back(r);
+  }
+  ProfRec* r = &p->prof[p->prof_used++];
+  r->sweep = sweep;
+  VP_TRY_CUDA(cudaEventRecord(r->a, s));
+  *rec = r;
+  return VP_OK;
+}
+
+int prof_end(ProfRec* r, cudaStream_t s) {
+  if (r) VP_TRY_CUDA(cudaEventRecord(r->b, s));
+  return VP_OK;
+}
+
+// The five sweeps; sweep 1 either loads f or assembles the source.
+int run_sweep(vp_plan_s* p, int which, const float2* f, const float2* const* lower, float2* u,
+              cudaStream_t s) {
+  const int Nx = p->n[0], Ny = p->n[1], Nz = p->n[2];
+  const int Mx = p->m[0], My = p->m[1];
+  ProfRec* rec = nullptr;
+  int st = prof_begin(p, which, s, &rec);
+  if (st != VP_OK) return st;
+  cudaError_t e = cudaSuccess;
+  if (which == 0 || which == 4) {
+    ColSweep c{};
+    c.ax = axis_desc(p, 0);
+    c.C = Nz;
+    c.n_outer = Ny;
+    c.scale = 1.0f;
+    if (which == 0) {
+      c.in = f;
+      c.in_rs = (long long)Ny * Nz;
+      c.in_os = Nz;
+      c.rows_in = Nx;
+      c.out = p->wsA;
+      c.out_rs = (long long)Ny * Nz;
+      c.out_os = Nz;
+      c.rows_out = Mx;
+      if (lower) {
+        c.harmonic = p->harmonic;
+        c.cn = (float)p->cn;
+        for (int i = 0; i < p->harmonic - 1; ++i) c.lower[i] = lower[i];
+      }
+      e = vp::launch_col_sweep(c, vp::kForward, lower != nullptr, s);
+    } else {
+      c.in = p->wsA;
+      c.in_rs = (long long)Ny * Nz;
+      c.in_os = Nz;
+      c.rows_in = Mx;
+      c.out = u;
+      c.out_rs = (long long)Ny * Nz;
+      c.out_os = Nz;
+      c.rows_out = Nx;
+      c.scale = (float)(1.0 / ((double)p->m[0] * p->m[1] * p->m[2]));
+      e = vp::launch_col_sweep(c, vp::kInverse, false, s);
+    }
+  } else if (which == 1 || which == 3) {
+    ColSweep c{};
+    c.ax = axis_desc(p, 1);
+    c.C = Nz;
+    c.n_outer = Mx;
+    c.scale = 1.0f;
+    if (which == 1) {
+      c.in = p->wsA;
+      c.in_rs = Nz;
+      c.in_os = (long long)Ny * Nz;
+      c.rows_in = Ny;
+      c.out = p->wsB;
+      c.out_rs = Nz;
+      c.out_os = (long long)My * Nz;
+      c.rows_out = My;
+      e = vp::launch_col_sweep(c, vp::kForward, false, s);
+    } else {
+      c.in = p->wsB;
+      c.in_rs = Nz;
+      c.in_os = (long long)My * Nz;
+      c.rows_in = My;
+      c.out = p->wsA;
+      c.out_rs = Nz;
+      c.out_os = (long long)Ny * Nz;
+      c.rows_out = Ny;
+      e = vp::launch_col_sweep(c, vp::kInverse, false, s);
+    }
+  } else {
+    LineSweep l{};
+    l.ax = axis_desc(p, 2);
+    l.data = p->wsB;
+    l.nlines = (long long)Mx * My;
+    l.ld = Nz;
+    l.n_in = Nz;
+    l.n_out = Nz;
+    l.khat = p->khat;
+    l.My = My;
+    l.Oy = p->oct[1];
+    l.Oz = p->oct[2];
+    l.fold_x = p->fold[0];
+    l.fold_y = p->fold[1];
+    l.fold_z = p->fold[2];
+    e = vp::launch_line_sweep(l, vp::kConv, s);
+  }
+  if (e != cudaSuccess) return cuda_status(e);
+  return prof_end(rec, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+VP_API const char* vp_status_string(int status) {
+  switch (status) {
+    case VP_OK: return "VP_OK";
+    case VP_ERR_ARG: return "VP_ERR_ARG: invalid argument";
+    case VP_ERR_SIZE: return "VP_ERR_SIZE: no FFT schedule for this embedding size";
+    case VP_ERR_NOMEM: return "VP_ERR_NOMEM: device allocation failed";
+    case VP_ERR_CUDA: return "VP_ERR_CUDA: CUDA runtime error";
+    case VP_ERR_NOT_NESTED: return "VP_ERR_NOT_NESTED: target grid not inside source grid";
+    case VP_ERR_STATE: return "VP_ERR_STATE: call out of order";
+    case VP_ERR_TIMEOUT: return "VP_ERR_TIMEOUT: bounded device wait expired";
+    case VP_ERR_UNSUPPORTED: return "VP_ERR_UNSUPPORTED: not implemented in this build";
+    default: return "unknown vp status";
+  }
+}
+
+VP_API const char* vp_version(void) { return "libvp 0.1 sm_103a"; }
+
+VP_API int vp_plan(const vp_grid* g, int harmonic_n, double f0_hz, const vp_medium* med,
+                   const vp_plan_opts* opts, vp_stream_t stream, vp_plan_t* out) {
+  (void)stream;
+  if (out) *out = nullptr;
+  if (!out || !grid_ok(g) || !medium_ok(med) || harmonic_n < 1 || !(f0_hz > 0) ||
+      !std::isfinite(f0_hz))
+    return VP_ERR_ARG;
+  if (harmonic_n - 1 > vp::kMaxLower) return VP_ERR_UNSUPPORTED;
+  // sizes and schedules are validated before any device work
+  int m[3], radix[3][vp::kMaxPass], npass[3];
+  for (int a = 0; a < 3; ++a) {
+    const int N = g->n[a];
+    if (N > vp::kMaxL) return VP_ERR_SIZE;
+    m[a] = (opts && opts->m[a] > 0) ? opts->m[a] : default_m(N);
+    if (m[a] < 2 * N - 1 || m[a] > vp::kMaxL) return VP_ERR_SIZE;
+    if (opts && opts->radix[a][0] != 0) {
+      int prod = 1, np = 0;
+      for (int i = 0; i < vp::kMaxPass && opts->radix[a][i] != 0; ++i) {
+        if (!radix_ok(opts->radix[a][i])) return VP_ERR_SIZE;
+        prod *= opts->radix[a][i];
+        radix[a][np++] = opts->radix[a][i];
+      }
+      if (prod != m[a]) return VP_ERR_SIZE;
+      for (int i = np; i < vp::kMaxPass; ++i) radix[a][i] = 0;
+      npass[a] = np;
+    } else {
+      npass[a] = default_schedule(m[a], radix[a]);
+      if (npass[a] == 0) return VP_ERR_SIZE;
+    }
+  }
+  vp_plan_s* p = new (std::nothrow) vp_plan_s();
+  if (!p) return VP_ERR_NOMEM;
+  cudaError_t e = cudaGetDevice(&p->dev);
+  if (e != cudaSuccess) {
+    delete p;
+    return cuda_status(e);
+  }
+  for (int a = 0; a < 3; ++a) {
+    p->n[a] = g->n[a];
+    p->origin[a] = g->origin[a];
+    p->m[a] = m[a];
+    p->oct[a] = m[a] / 2 + 1;
+    p->npass[a] = npass[a];
+    for (int i = 0; i < vp::kMaxPass; ++i) p->radix[a][i] = radix[a][i];
+  }
+  p->h = g->h;
+  p->harmonic = harmonic_n;
+  p->f0 = f0_hz;
+  p->med = *med;
+  const double f = harmonic_n * f0_hz;
+  p->kr = 2.0 * kPi * f / med->c0;
+  p->ki = attenuation(f, *med);
+  const double omega = 2.0 * kPi * f0_hz;
+  p->cn = -med->beta * omega * omega * harmonic_n * harmonic_n / (2.0 * med->rho0 * std::pow(med->c0, 4));
+  const std::complex<double> sc = self_cell_host({p->kr, p->ki}, p->h);
+  p->self_re = sc.real();
+  p->self_im = sc.imag();
+
+  int st = VP_OK;
+  for (int a = 0; a < 3 && st == VP_OK; ++a) st = build_axis_tables(p, a);
+  const size_t nA = (size_t)m[0] * g->n[1] * g->n[2];
+  const size_t nB = (size_t)m[0] * m[1] * g->n[2];
+  const size_t nK = (size_t)p->oct[0] * p->oct[1] * p->oct[2];
+  if (st == VP_OK) st = cuda_status(cudaMalloc((void**)&p->wsA, nA * sizeof(float2)));
+  if (st == VP_OK) st = cuda_status(cudaMalloc((void**)&p->wsB, nB * sizeof(float2)));
+  if (st == VP_OK) st = cuda_status(cudaMalloc((void**)&p->khat, nK * sizeof(float2)));
+  if (st != VP_OK) {
+    free_plan(p);
+    return st;
+  }
+  p->bytes += (nA + nB + nK) * sizeof(float2);
+  *out = p;
+  return VP_OK;
+}
+
+VP_API int vp_destroy(vp_plan_t p) {
+  if (!p) return VP_OK;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(p->dev);
+  cudaError_t e = cudaDeviceSynchronize();
+  free_plan(p);
+  cudaSetDevice(prev);
+  return cuda_status(e);
+}
+
+VP_API int vp_plan_get_info(vp_plan_t p, vp_plan_info* info) {
+  if (!p || !info) return VP_ERR_ARG;
+  std::memset(info, 0, sizeof(*info));
+  for (int a = 0; a < 3; ++a) {
+    info->n[a] = p->n[a];
+    info->m[a] = p->m[a];
+    for (int i = 0; i < vp::kMaxPass; ++i) info->radix[a][i] = p->radix[a][i];
+  }
+  info->k_re = p->kr;
+  info->k_im = p->ki;
+  info->c_n = p->cn;
+  info->self_re = p->self_re;
+  info->self_im = p->self_im;
+  info->workspace_bytes = p->bytes;
+  info->khat_ready = p->khat_ready ? 1 : 0;
+  return VP_OK;
+}
+
+VP_API int vp_kernel_fft(vp_plan_t p, vp_stream_t stream) {
+  if (!p) return VP_ERR_ARG;
+  if (p->khat_ready) return VP_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int Mx = p->m[0], My = p->m[1], Mz = p->m[2];
+  const size_t total = (size_t)Mx * My * Mz;
+  float2* tmp = nullptr;
+  VP_TRY_CUDA(cudaMallocAsync((void**)&tmp, total * sizeof(float2), s));
+  cudaError_t e = vp::launch_kernel_lattice(tmp, p->n, p->m, p->h, p->kr, p->ki, s);
+  if (e == cudaSuccess) {
+    ColSweep c{};  // x, in place over the full cube
+    c.ax = axis_desc(p, 0);
+    c.in = tmp;
+    c.out = tmp;
+    c.in_rs = c.out_rs = (long long)My * Mz;
+    c.in_os = c.out_os = Mz;
+    c.C = Mz;
+    c.n_outer = My;
+    c.rows_in = Mx;
+    c.rows_out = Mx;
+    c.scale = 1.0f;
+    e = vp::launch_col_sweep(c, vp::kForward, false, s);
+  }
+  if (e == cudaSuccess) {
+    ColSweep c{};  // y, in place
+    c.ax = axis_desc(p, 1);
+    c.in = tmp;
+    c.out = tmp;
+    c.in_rs = c.out_rs = Mz;
+    c.in_os = c.out_os = (long long)My * Mz;
+    c.C = Mz;
+    c.n_outer = Mx;
+    c.rows_in = My;
+    c.rows_out = My;
+    c.scale = 1.0f;
+    e = vp::launch_col_sweep(c, vp::kForward, false, s);
+  }
+  if (e == cudaSuccess) {
+    LineSweep l{};
+    l.ax = axis_desc(p, 2);
+    l.data = tmp;
+    l.nlines = (long long)Mx * My;
+    l.ld = Mz;
+    l.n_in = Mz;
+    l.n_out = Mz;
+    e = vp::launch_line_sweep(l, vp::kForwardOnly, s);
+  }
+  if (e == cudaSuccess) e = vp::launch_octant_extract(tmp, p->khat, p->m, p->oct, p->pos[0], p->pos[1], p->pos[2], s);
+  cudaError_t e2 = cudaFreeAsync(tmp, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (e2 != cudaSuccess) return cuda_status(e2);
+  p->khat_ready = true;
+  return VP_OK;
+}
+
+VP_API int vp_kernel_spectrum_get(vp_plan_t p, void* dst, vp_stream_t stream) {
+  if (!p || !dst) return VP_ERR_ARG;
+  if (!p->khat_ready) return VP_ERR_STATE;
+  const size_t nK = (size_t)p->oct[0] * p->oct[1] * p->oct[2];
+  VP_TRY_CUDA(cudaMemcpyAsync(dst, p->khat, nK * sizeof(float2), cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  return VP_OK;
+}
+
+VP_API int vp_kernel_spectrum_set(vp_plan_t p, const void* src, vp_stream_t stream) {
+  if (!p || !src) return VP_ERR_ARG;
+  const size_t nK = (size_t)p->oct[0] * p->oct[1] * p->oct[2];
+  VP_TRY_CUDA(cudaMemcpyAsync(p->khat, src, nK * sizeof(float2), cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  p->khat_ready = true;
+  return VP_OK;
+}
+
+VP_API int vp_source_assemble(vp_plan_t p, const void* const* lower, int n_lower, int flags, void* f_out,
+                              vp_stream_t stream) {
+  if (!p || !lower || flags != 0) return VP_ERR_ARG;
+  if (p->harmonic < 2 || n_lower != p->harmonic - 1) return VP_ERR_ARG;
+  for (int i = 0; i < n_lower; ++i)
+    if (!lower[i]) return VP_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const float2* lo[vp::kMaxLower] = {};
+  for (int i = 0; i < n_lower; ++i) lo[i] = (const float2*)lower[i];
+  if (f_out) {
+    const long long count = (long long)p->n[0] * p->n[1] * p->n[2];
+    cudaError_t e = vp::launch_source_assemble(lo, p->harmonic, (float)p->cn, (float2*)f_out, count, s);
+    return cuda_status(e);
+  }
+  int st = run_sweep(p, 0, nullptr, lo, nullptr, s);
+  if (st != VP_OK) return st;
+  p->staged = true;
+  return VP_OK;
+}
+
+VP_API int vp_apply(vp_plan_t p, const void* f, void* u, vp_stream_t stream) {
+  if (!p || !u) return VP_ERR_ARG;
+  if (!p->khat_ready) return VP_ERR_STATE;
+  if (!f && !p->staged) return VP_ERR_STATE;
+  cudaStream_t s = (cudaStream_t)stream;
+  int st;
+  if (f) {
+    if ((st = run_sweep(p, 0, (const float2*)f, nullptr, nullptr, s)) != VP_OK) return st;
+  }
+  p->staged = false;
+  for (int w = 1; w <= 4; ++w)
+    if ((st = run_sweep(p, w, nullptr, nullptr, (float2*)u, s)) != VP_OK) return st;
+  return VP_OK;
+}
+
+VP_API int vp_restrict_to_nested_box(const vp_grid* src, const void* src_field, const vp_grid* dst,
+                                     void* dst_field, int flags, vp_stream_t stream) {
+  if (!grid_ok(src) || !grid_ok(dst) || !src_field || !dst_field) return VP_ERR_ARG;
+  if (flags & ~VP_RESTRICT_ZERO_OUTSIDE) return VP_ERR_ARG;
+  double a[3], b[3];
+  const double tol = 1e-9;
+  for (int ax = 0; ax < 3; ++ax) {
+    a[ax] = (dst->origin[ax] - src->origin[ax]) / src->h;
+    b[ax] = dst->h / src->h;
+    const double t0 = a[ax];
+    const double t1 = std::fma((double)(dst->n[ax] - 1), b[ax], a[ax]);
+    const double lo = std::min(t0, t1), hi = std::max(t0, t1);
+    if (!(flags & VP_RESTRICT_ZERO_OUTSIDE) && (lo < -tol || hi > (double)(src->n[ax] - 1) + tol))
+      return VP_ERR_NOT_NESTED;
+  }
+  cudaError_t e = vp::launch_restrict((const float2*)src_field, src->n, (float2*)dst_field, dst->n, a, b,
+                                      flags & VP_RESTRICT_ZERO_OUTSIDE, (cudaStream_t)stream);
+  return cuda_status(e);
+}
+
+VP_API int vp_incident_field(const vp_grid* g, const double* points, int n_points, double l, double R,
+                             double f0_hz, double p0, const vp_medium* m, void* out, vp_stream_t stream) {
+  if (!grid_ok(g) || !points || n_points < 1 || !out || !medium_ok(m) || !(l > 0) || !(R > 0) || R > l ||
+      !(f0_hz > 0) || !std::isfinite(p0))
+    return VP_ERR_ARG;
+  const double kr = 2.0 * kPi * f0_hz / m->c0;
+  const double ki = attenuation(f0_hz, *m);
+  const double area = 2.0 * kPi * l * (l - std::sqrt(l * l - R * R));
+  // scale = -2 i k p0 A / n_p
+  const std::complex<double> sc = std::complex<double>(0.0, -2.0) * std::complex<double>(kr, ki) * p0 * area /
+                                  (double)n_points;
+  cudaError_t e = vp::launch_incident(points, n_points, g->n, g->origin, g->h, kr, ki, sc.real(), sc.imag(),
+                                      (float2*)out, (cudaStream_t)stream);
+  return cuda_status(e);
+}
+
+VP_API int vp_profile_enable(vp_plan_t p, int on) {
+  if (!p) return VP_ERR_ARG;
+  p->prof_on = on != 0;
+  return VP_OK;
+}
+
+VP_API int vp_profile_read(vp_plan_t p, double ms[5], int count[5], int reset) {
+  if (!p) return VP_ERR_ARG;
+  for (size_t i = 0; i < p->prof_used; ++i) {
+    ProfRec& r = p->prof[i];
+    VP_TRY_CUDA(cudaEventSynchronize(r.b));
+    float t = 0.f;
+    VP_TRY_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
+    p->prof_ms[r.sweep] += t;
+    p->prof_cnt[r.sweep] += 1;
+  }
+  p->prof_used = 0;
+  for (int i = 0; i < 5; ++i) {
+    if (ms) ms[i] = p->prof_ms[i];
+    if (count) count[i] = p->prof_cnt[i];
+    if (reset) {
+      p->prof_ms[i] = 0;
+      p->prof_cnt[i] = 0;
+    }
+  }
+  return VP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,82 @@
+// Internal declarations shared by the translation units of libvp.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "vp.h"
+
+namespace vp {
+
+constexpr int kMaxPass = 8;      // radix passes per axis
+constexpr int kMaxLower = 8;     // lower harmonics fed to one source assembly
+constexpr int kTileB = 16;       // lines per CTA tile in every FFT sweep
+constexpr int kThreads = 256;    // threads per CTA of the FFT sweeps
+constexpr int kMaxL = 1600;      // longest FFT line the shared-memory tile holds
+
+// One FFT axis: its length, radix schedule and twiddle table.
+struct AxisDesc {
+  int L;
+  int npass;
+  int radix[kMaxPass];
+  int lp[kMaxPass];        // sub-transform length entering pass p (L, L/R0, L/(R0 R1), ...)
+  const float2* tw;        // L entries, exp(-2 pi i t / L), built in FP64 on the host
+};
+
+// Column sweep: FFT along a strided axis, batched over 16 contiguous columns.
+// Element (outer o, row i, column c) lives at base + o*os + i*rs + c.
+struct ColSweep {
+  const float2* in;
+  float2* out;
+  long long in_os, in_rs, out_os, out_rs;
+  int C;          // columns (contiguous extent)
+  int n_outer;
+  int rows_in;    // rows read (rows beyond are zero padding)
+  int rows_out;   // rows written
+  float scale;
+  AxisDesc ax;
+  // source-assembly prologue (first forward sweep fused with Eq. 2.6)
+  int harmonic;   // n; the prologue forms sum_{m=1}^{n-1} p_m p_{n-m}
+  float cn;       // C_n
+  const float2* lower[kMaxLower];
+};
+
+// Line sweep: FFT along the contiguous axis, 16 lines per CTA.
+struct LineSweep {
+  float2* data;
+  long long nlines;
+  long long ld;   // distance between consecutive lines (elements)
+  int n_in;       // elements read per line (rest is zero padding up to L)
+  int n_out;      // elements written per line
+  AxisDesc ax;
+  // spectrum multiply (convolution mode)
+  const float2* khat;   // octant (Ox, Oy, Oz)
+  int My, Oy, Oz;
+  const int* fold_x;    // position -> folded frequency, per axis
+  const int* fold_y;
+  const int* fold_z;
+};
+
+enum SweepDir { kForward = 0, kInverse = 1 };
+enum LineMode { kConv = 0, kForwardOnly = 1 };
+
+// Launchers (vp_sweeps.cu).  Return a cudaError_t.
+cudaError_t launch_col_sweep(const ColSweep& p, int dir, bool source_prologue, cudaStream_t s);
+cudaError_t launch_line_sweep(const LineSweep& p, int mode, cudaStream_t s);
+
+// Other kernels (vp_kernels.cu).
+cudaError_t launch_kernel_lattice(float2* out, const int n[3], const int m[3], double h,
+                                  double kr, double ki, cudaStream_t s);
+cudaError_t launch_octant_extract(const float2* scr, float2* oct, const int m[3], const int o[3],
+                                  const int* pos_x, const int* pos_y, const int* pos_z,
+                                  cudaStream_t s);
+cudaError_t launch_source_assemble(const float2* const* lower, int harmonic, float cn, float2* out,
+                                   long long count, cudaStream_t s);
+cudaError_t launch_restrict(const float2* src, const int ns[3], float2* dst, const int nd[3],
+                            const double a[3], const double b[3], int zero_outside,
+                            cudaStream_t s);
+cudaError_t launch_incident(const double* pts, int npts, const int n[3], const double origin[3],
+                            double h, double kr, double ki, double scale_re, double scale_im,
+                            float2* out, cudaStream_t s);
+
+}  // namespace vp

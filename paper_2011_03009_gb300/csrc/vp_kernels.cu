@@ -1,0 +1,299 @@
+// Non-FFT kernels: quadrature-kernel lattice with the self cell (Eq. 3.9), octant
+// extraction of its spectrum, standalone source assembly (Eq. 2.6), trilinear
+// restriction between nested grids (Section 6) and the incident field (Eq. 3.10).
+#include <math.h>
+
+#include "fft_engine.cuh"
+
+namespace vp {
+
+namespace {
+
+constexpr double kPi = 3.141592653589793238462643383279502884;
+constexpr double kTwoPi = 6.283185307179586476925286766559005768;
+constexpr double kInvTwoPi = 0.159154943091895335768883763372514362;
+
+// exp(i * phase) with the phase reduced modulo 2 pi in FP64 before the FP32 sine/cosine.
+__device__ __forceinline__ float2 unit_phasor(double phase) {
+  const double red = fma(-kTwoPi, rint(phase * kInvTwoPi), phase);
+  float s, c;
+  sincosf((float)red, &s, &c);
+  return make_float2(c, s);
+}
+
+struct cd { double re, im; };
+__device__ __forceinline__ cd cd_mul(cd a, cd b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+__device__ __forceinline__ cd cd_div(cd a, cd b) {
+  const double d = b.re * b.re + b.im * b.im;
+  return {(a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d};
+}
+
+// Integral of G_k over the ball of radius a about its centre: ((1 - i k a) e^{i k a} - 1) / k^2,
+// or, for |k a| < 0.1, the power series sum_m (i k a)^m a^2 / (m! (m + 2)) of the same integral.
+__device__ cd self_cell_fp64(double kr, double ki, double a) {
+  const cd ka = {kr * a, ki * a};
+  if (sqrt(ka.re * ka.re + ka.im * ka.im) < 0.1) {
+    cd total = {0.0, 0.0}, term = {1.0, 0.0};
+    const cd ika = {-ka.im, ka.re};
+    for (int m = 0; m < 24; ++m) {
+      total.re += term.re / (m + 2);
+      total.im += term.im / (m + 2);
+      term = cd_mul(term, ika);
+      term.re /= (m + 1);
+      term.im /= (m + 1);
+    }
+    return {total.re * a * a, total.im * a * a};
+  }
+  // e^{i k a} = e^{-Im(ka)} (cos Re(ka) + i sin Re(ka))
+  double s, c;
+  sincos(ka.re, &s, &c);
+  const double m = exp(-ka.im);
+  const cd e = {m * c, m * s};
+  const cd one_m_ika = {1.0 + ka.im, -ka.re};  // 1 - i k a
+  cd num = cd_mul(one_m_ika, e);
+  num.re -= 1.0;
+  const cd k = {kr, ki};
+  return cd_div(num, cd_mul(k, k));
+}
+
+__device__ __forceinline__ int lattice_offset(int m, int n, int M) {
+  if (m < n) return m;
+  if (m > M - n) return m - M;
+  return INT_MIN;
+}
+
+__global__ void lattice_kernel(float2* out, int nx, int ny, int nz, int mx, int my, int mz, double h,
+                               double kr, double ki) {
+  const long long total = (long long)mx * my * mz;
+  const double h3_4pi = h * h * h / (4.0 * kPi);
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int iz = (int)(idx % mz);
+    const long long r1 = idx / mz;
+    const int iy = (int)(r1 % my);
+    const int ix = (int)(r1 / my);
+    const int dx = lattice_offset(ix, nx, mx);
+    const int dy = lattice_offset(iy, ny, my);
+    const int dz = lattice_offset(iz, nz, mz);
+    float2 v = make_float2(0.f, 0.f);
+    if (dx != INT_MIN && dy != INT_MIN && dz != INT_MIN) {
+      if (dx == 0 && dy == 0 && dz == 0) {
+        const double a = 0.62035049089940001666800681204778 * h;  // (3 / (4 pi))^(1/3) h
+        const cd s = self_cell_fp64(kr, ki, a);
+        v = make_float2((float)s.re, (float)s.im);
+      } else {
+        const double d2 = (double)((long long)dx * dx + (long long)dy * dy + (long long)dz * dz);
+        const double d = sqrt(d2);
+        const double r = d * h;
+        const double amp = h3_4pi * exp(-ki * r) / r;
+        const float2 ph = unit_phasor(kr * r);
+        v = make_float2((float)amp * ph.x, (float)amp * ph.y);
+      }
+    }
+    out[idx] = v;
+  }
+}
+
+__global__ void octant_kernel(const float2* __restrict__ scr, float2* __restrict__ oct, int my, int mz,
+                              int ox, int oy, int oz, const int* __restrict__ pos_x,
+                              const int* __restrict__ pos_y, const int* __restrict__ pos_z) {
+  const long long total = (long long)ox * oy * oz;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int iz = (int)(idx % oz);
+    const long long r1 = idx / oz;
+    const int iy = (int)(r1 % oy);
+    const int ix = (int)(r1 / oy);
+    oct[idx] = scr[((long long)pos_x[ix] * my + pos_y[iy]) * mz + pos_z[iz]];
+  }
+}
+
+struct LowerPtrs { const float2* p[kMaxLower]; };
+
+__global__ void source_kernel(LowerPtrs lo, int harmonic, float cn, float2* __restrict__ out,
+                              long long count) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x) {
+    float2 acc = make_float2(0.f, 0.f);
+    for (int m = 1; m < harmonic; ++m) acc = cadd(acc, cmul(__ldg(&lo.p[m - 1][i]), __ldg(&lo.p[harmonic - m - 1][i])));
+    out[i] = cscale(acc, cn);
+  }
+}
+
+struct AxisMap { double a, b; int n; };
+
+__device__ __forceinline__ bool axis_weights(const AxisMap& m, int i, int& i0, float& w) {
+  const double t = fma((double)i, m.b, m.a);
+  const double tol = 1e-9;
+  const bool inside = t >= -tol && t <= (double)(m.n - 1) + tol;
+  if (m.n == 1) {
+    i0 = 0;
+    w = 0.f;
+    return inside;
+  }
+  double fl = floor(t);
+  if (fl < 0.0) fl = 0.0;
+  if (fl > (double)(m.n - 2)) fl = (double)(m.n - 2);
+  i0 = (int)fl;
+  double wd = t - fl;
+  if (wd < 0.0) wd = 0.0;
+  if (wd > 1.0) wd = 1.0;
+  w = (float)wd;
+  return inside;
+}
+
+__global__ void restrict_kernel(const float2* __restrict__ src, int snx, int sny, int snz,
+                                float2* __restrict__ dst, int dnx, int dny, int dnz, AxisMap mx,
+                                AxisMap my, AxisMap mz, int zero_outside) {
+  const long long total = (long long)dnx * dny * dnz;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int iz = (int)(idx % dnz);
+    const long long r1 = idx / dnz;
+    const int iy = (int)(r1 % dny);
+    const int ix = (int)(r1 / dny);
+    int x0, y0, z0;
+    float wx, wy, wz;
+    bool in = axis_weights(mx, ix, x0, wx);
+    in &= axis_weights(my, iy, y0, wy);
+    in &= axis_weights(mz, iz, z0, wz);
+    if (!in && zero_outside) {
+      dst[idx] = make_float2(0.f, 0.f);
+      continue;
+    }
+    const int x1 = snx > 1 ? x0 + 1 : x0;
+    const int y1 = sny > 1 ? y0 + 1 : y0;
+    const int z1 = snz > 1 ? z0 + 1 : z0;
+    const long long sy = snz, sx = (long long)sny * snz;
+    const float2 c000 = __ldg(&src[x0 * sx + y0 * sy + z0]);
+    const float2 c001 = __ldg(&src[x0 * sx + y0 * sy + z1]);
+    const float2 c010 = __ldg(&src[x0 * sx + y1 * sy + z0]);
+    const float2 c011 = __ldg(&src[x0 * sx + y1 * sy + z1]);
+    const float2 c100 = __ldg(&src[x1 * sx + y0 * sy + z0]);
+    const float2 c101 = __ldg(&src[x1 * sx + y0 * sy + z1]);
+    const float2 c110 = __ldg(&src[x1 * sx + y1 * sy + z0]);
+    const float2 c111 = __ldg(&src[x1 * sx + y1 * sy + z1]);
+    const float uz = 1.f - wz, uy = 1.f - wy, ux = 1.f - wx;
+    float2 c00 = make_float2(uz * c000.x + wz * c001.x, uz * c000.y + wz * c001.y);
+    float2 c01 = make_float2(uz * c010.x + wz * c011.x, uz * c010.y + wz * c011.y);
+    float2 c10 = make_float2(uz * c100.x + wz * c101.x, uz * c100.y + wz * c101.y);
+    float2 c11 = make_float2(uz * c110.x + wz * c111.x, uz * c110.y + wz * c111.y);
+    float2 c0 = make_float2(uy * c00.x + wy * c01.x, uy * c00.y + wy * c01.y);
+    float2 c1 = make_float2(uy * c10.x + wy * c11.x, uy * c10.y + wy * c11.y);
+    dst[idx] = make_float2(ux * c0.x + wx * c1.x, ux * c0.y + wx * c1.y);
+  }
+}
+
+constexpr int kIncBlock = 256;
+
+// Distance in FP64 without a full-precision square root: one Newton step on the
+// single-precision reciprocal square root brings it to about 1e-14 relative.
+__device__ __forceinline__ double fp64_norm(double r2) {
+  double y = (double)rsqrtf((float)r2);
+  y = y * fma(-0.5 * r2, y * y, 1.5);
+  return r2 * y;
+}
+
+__global__ void __launch_bounds__(kIncBlock) incident_kernel(const double* __restrict__ pts, int npts,
+                                                             int nx, int ny, int nz, double ox,
+                                                             double oy, double oz, double h, double kr,
+                                                             double ki, double sre, double sim,
+                                                             float2* __restrict__ out) {
+  __shared__ double sp[3][kIncBlock];
+  const long long total = (long long)nx * ny * nz;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool active = idx < total;
+  double x = 0, y = 0, z = 0;
+  if (active) {
+    const int iz = (int)(idx % nz);
+    const long long r1 = idx / nz;
+    const int iy = (int)(r1 % ny);
+    const int ix = (int)(r1 / ny);
+    x = fma((double)ix, h, ox);
+    y = fma((double)iy, h, oy);
+    z = fma((double)iz, h, oz);
+  }
+  const float inv4pi = (float)(1.0 / (4.0 * kPi));
+  double are = 0.0, aim = 0.0;
+  for (int c0 = 0; c0 < npts; c0 += kIncBlock) {
+    const int j = c0 + threadIdx.x;
+    if (j < npts) {
+      sp[0][threadIdx.x] = pts[3 * (long long)j + 0];
+      sp[1][threadIdx.x] = pts[3 * (long long)j + 1];
+      sp[2][threadIdx.x] = pts[3 * (long long)j + 2];
+    }
+    __syncthreads();
+    const int cnt = min(kIncBlock, npts - c0);
+    float fre = 0.f, fim = 0.f;
+    if (active) {
+      for (int q = 0; q < cnt; ++q) {
+        const double dx = x - sp[0][q], dy = y - sp[1][q], dz = z - sp[2][q];
+        const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+        const double r = fp64_norm(r2);
+        const float2 ph = unit_phasor(kr * r);
+        const float amp = expf(-(float)(ki * r)) * inv4pi / (float)r;
+        fre = fmaf(amp, ph.x, fre);
+        fim = fmaf(amp, ph.y, fim);
+      }
+    }
+    are += fre;
+    aim += fim;
+    __syncthreads();
+  }
+  if (active) out[idx] = make_float2((float)(sre * are - sim * aim), (float)(sre * aim + sim * are));
+}
+
+int grid_for(long long total, int threads) {
+  long long b = (total + threads - 1) / threads;
+  const long long cap = 152LL * 64;  // grid-stride beyond 64 CTAs per SM
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+}  // namespace
+
+cudaError_t launch_kernel_lattice(float2* out, const int n[3], const int m[3], double h, double kr,
+                                  double ki, cudaStream_t s) {
+  const long long total = (long long)m[0] * m[1] * m[2];
+  lattice_kernel<<<grid_for(total, 256), 256, 0, s>>>(out, n[0], n[1], n[2], m[0], m[1], m[2], h, kr, ki);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_octant_extract(const float2* scr, float2* oct, const int m[3], const int o[3],
+                                  const int* pos_x, const int* pos_y, const int* pos_z, cudaStream_t s) {
+  const long long total = (long long)o[0] * o[1] * o[2];
+  octant_kernel<<<grid_for(total, 256), 256, 0, s>>>(scr, oct, m[1], m[2], o[0], o[1], o[2], pos_x, pos_y,
+                                                      pos_z);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_source_assemble(const float2* const* lower, int harmonic, float cn, float2* out,
+                                   long long count, cudaStream_t s) {
+  LowerPtrs lo;
+  for (int i = 0; i < kMaxLower; ++i) lo.p[i] = i < harmonic - 1 ? lower[i] : nullptr;
+  source_kernel<<<grid_for(count, 256), 256, 0, s>>>(lo, harmonic, cn, out, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_restrict(const float2* src, const int ns[3], float2* dst, const int nd[3],
+                            const double a[3], const double b[3], int zero_outside, cudaStream_t s) {
+  const long long total = (long long)nd[0] * nd[1] * nd[2];
+  AxisMap mx{a[0], b[0], ns[0]}, my{a[1], b[1], ns[1]}, mz{a[2], b[2], ns[2]};
+  restrict_kernel<<<grid_for(total, 256), 256, 0, s>>>(src, ns[0], ns[1], ns[2], dst, nd[0], nd[1], nd[2], mx,
+                                                        my, mz, zero_outside);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_incident(const double* pts, int npts, const int n[3], const double origin[3], double h,
+                            double kr, double ki, double scale_re, double scale_im, float2* out,
+                            cudaStream_t s) {
+  const long long total = (long long)n[0] * n[1] * n[2];
+  const long long blocks = (total + kIncBlock - 1) / kIncBlock;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  incident_kernel<<<(unsigned)blocks, kIncBlock, 0, s>>>(pts, npts, n[0], n[1], n[2], origin[0], origin[1],
+                                                         origin[2], h, kr, ki, scale_re, scale_im, out);
+  return cudaGetLastError();
+}
+
+}  // namespace vp

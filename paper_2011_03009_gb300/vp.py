@@ -1,0 +1,240 @@
+"""Thin Python binding of libvp.so (the C ABI declared in include/vp.h).
+
+Argument marshalling only: every step of the computation runs in the library's
+CUDA kernels.  Fields are torch.complex64 CUDA tensors (contiguous, C order);
+torch supplies device memory and streams.  There is no CPU fallback: if libvp.so
+is missing or fails to load, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libvp.so")
+
+VP_OK = 0
+VP_ERR_ARG = -1
+VP_ERR_SIZE = -2
+VP_ERR_NOMEM = -3
+VP_ERR_CUDA = -4
+VP_ERR_NOT_NESTED = -5
+VP_ERR_STATE = -6
+VP_ERR_TIMEOUT = -7
+VP_ERR_UNSUPPORTED = -8
+VP_RESTRICT_ZERO_OUTSIDE = 1
+MAX_PASS = 8
+
+
+class VpError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} ({status})")
+
+
+class vp_grid(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int * 3), ("origin", ctypes.c_double * 3), ("h", ctypes.c_double)]
+
+
+class vp_medium(ctypes.Structure):
+    _fields_ = [("c0", ctypes.c_double), ("rho0", ctypes.c_double), ("beta", ctypes.c_double),
+                ("alpha0", ctypes.c_double), ("eta", ctypes.c_double)]
+
+
+class vp_plan_opts(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int * 3), ("radix", (ctypes.c_int * MAX_PASS) * 3), ("autotune", ctypes.c_int)]
+
+
+class vp_plan_info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int * 3), ("m", ctypes.c_int * 3), ("radix", (ctypes.c_int * MAX_PASS) * 3),
+                ("k_re", ctypes.c_double), ("k_im", ctypes.c_double), ("c_n", ctypes.c_double),
+                ("self_re", ctypes.c_double), ("self_im", ctypes.c_double),
+                ("workspace_bytes", ctypes.c_ulonglong), ("khat_ready", ctypes.c_int)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libvp.so not built ({LIB_PATH}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    I = ctypes.c_int
+    D = ctypes.c_double
+    sig = {
+        "vp_plan": (I, [ctypes.POINTER(vp_grid), I, D, ctypes.POINTER(vp_medium), ctypes.POINTER(vp_plan_opts), P,
+                        ctypes.POINTER(P)]),
+        "vp_destroy": (I, [P]),
+        "vp_plan_get_info": (I, [P, ctypes.POINTER(vp_plan_info)]),
+        "vp_kernel_fft": (I, [P, P]),
+        "vp_kernel_spectrum_get": (I, [P, P, P]),
+        "vp_kernel_spectrum_set": (I, [P, P, P]),
+        "vp_source_assemble": (I, [P, ctypes.POINTER(P), I, I, P, P]),
+        "vp_apply": (I, [P, P, P, P]),
+        "vp_restrict_to_nested_box": (I, [ctypes.POINTER(vp_grid), P, ctypes.POINTER(vp_grid), P, I, P]),
+        "vp_incident_field": (I, [ctypes.POINTER(vp_grid), P, I, D, D, D, D, ctypes.POINTER(vp_medium), P, P]),
+        "vp_status_string": (ctypes.c_char_p, [I]),
+        "vp_profile_enable": (I, [P, I]),
+        "vp_profile_read": (I, [P, ctypes.POINTER(D), ctypes.POINTER(I), I]),
+        "vp_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def status_string(status: int) -> str:
+    return lib.vp_status_string(int(status)).decode()
+
+
+def _check(status: int, where: str):
+    if status != VP_OK:
+        raise VpError(status, where)
+
+
+def make_grid(n, origin, h) -> vp_grid:
+    g = vp_grid()
+    for a in range(3):
+        g.n[a] = int(n[a])
+        g.origin[a] = float(origin[a])
+    g.h = float(h)
+    return g
+
+
+def grid_of(obj) -> vp_grid:
+    """vp_grid from any object with .n, .origin, .h (e.g. synth.Grid)."""
+    return make_grid(obj.n, obj.origin, obj.h)
+
+
+def make_medium(m) -> vp_medium:
+    return vp_medium(float(m.c0), float(m.rho0), float(m.beta), float(m.alpha0), float(m.eta))
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(int(stream.cuda_stream))
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    import torch
+    if t is None:
+        return ctypes.c_void_p(0)
+    if not (t.is_cuda and t.dtype == torch.complex64 and t.is_contiguous()):
+        raise ValueError("fields must be contiguous torch.complex64 CUDA tensors")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Plan:
+    """A vp_plan_t with its grid; methods mirror the C ABI calls."""
+
+    def __init__(self, grid, harmonic: int, f0: float, medium, m: Optional[Sequence[int]] = None,
+                 radix: Optional[Sequence[Sequence[int]]] = None, autotune: bool = False, stream=None):
+        self.grid = grid
+        self.harmonic = int(harmonic)
+        self._h = ctypes.c_void_p(0)
+        opts = vp_plan_opts()
+        if m is not None:
+            for a in range(3):
+                opts.m[a] = int(m[a])
+        if radix is not None:
+            for a in range(3):
+                for i, r in enumerate(radix[a] or []):
+                    opts.radix[a][i] = int(r)
+        opts.autotune = 1 if autotune else 0
+        g = grid if isinstance(grid, vp_grid) else grid_of(grid)
+        self._g = g
+        med = medium if isinstance(medium, vp_medium) else make_medium(medium)
+        st = lib.vp_plan(ctypes.byref(g), self.harmonic, float(f0), ctypes.byref(med), ctypes.byref(opts),
+                         _stream(stream) if autotune else ctypes.c_void_p(0), ctypes.byref(self._h))
+        _check(st, "vp_plan")
+        self.n = tuple(int(v) for v in g.n)
+
+    def info(self) -> vp_plan_info:
+        inf = vp_plan_info()
+        _check(lib.vp_plan_get_info(self._h, ctypes.byref(inf)), "vp_plan_get_info")
+        return inf
+
+    def kernel_fft(self, stream=None):
+        _check(lib.vp_kernel_fft(self._h, _stream(stream)), "vp_kernel_fft")
+
+    def kernel_spectrum_get(self, dst, stream=None):
+        _check(lib.vp_kernel_spectrum_get(self._h, _ptr(dst), _stream(stream)), "vp_kernel_spectrum_get")
+
+    def kernel_spectrum_set(self, src, stream=None):
+        _check(lib.vp_kernel_spectrum_set(self._h, _ptr(src), _stream(stream)), "vp_kernel_spectrum_set")
+
+    def source_assemble(self, lower, f_out=None, stream=None):
+        arr = (ctypes.c_void_p * max(1, len(lower)))(*[_ptr(t).value for t in lower])
+        _check(lib.vp_source_assemble(self._h, arr, len(lower), 0, _ptr(f_out), _stream(stream)),
+               "vp_source_assemble")
+
+    def apply(self, f, u, stream=None):
+        _check(lib.vp_apply(self._h, _ptr(f), _ptr(u), _stream(stream)), "vp_apply")
+
+    def profile_enable(self, on: bool = True):
+        _check(lib.vp_profile_enable(self._h, 1 if on else 0), "vp_profile_enable")
+
+    def profile_read(self, reset: bool = True):
+        ms = (ctypes.c_double * 5)()
+        cnt = (ctypes.c_int * 5)()
+        _check(lib.vp_profile_read(self._h, ms, cnt, 1 if reset else 0), "vp_profile_read")
+        return list(ms), list(cnt)
+
+    def close(self):
+        if self._h and self._h.value:
+            lib.vp_destroy(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---- module-level calls with the C ABI's names ---------------------------------------
+
+def vp_plan(grid, harmonic: int, f0: float, medium, **kw) -> Plan:
+    return Plan(grid, harmonic, f0, medium, **kw)
+
+
+def vp_kernel_fft(plan: Plan, stream=None):
+    plan.kernel_fft(stream)
+
+
+def vp_source_assemble(plan: Plan, lower, f_out=None, stream=None):
+    plan.source_assemble(lower, f_out, stream)
+
+
+def vp_apply(plan: Plan, f, u, stream=None):
+    plan.apply(f, u, stream)
+
+
+def vp_restrict_to_nested_box(src_grid, src, dst_grid, dst, zero_outside: bool = False, stream=None):
+    gs = src_grid if isinstance(src_grid, vp_grid) else grid_of(src_grid)
+    gd = dst_grid if isinstance(dst_grid, vp_grid) else grid_of(dst_grid)
+    flags = VP_RESTRICT_ZERO_OUTSIDE if zero_outside else 0
+    _check(lib.vp_restrict_to_nested_box(ctypes.byref(gs), _ptr(src), ctypes.byref(gd), _ptr(dst), flags,
+                                         _stream(stream)), "vp_restrict_to_nested_box")
+
+
+def vp_incident_field(grid, points, bowl, medium, out, stream=None):
+    """p1 on `grid` (Eq. 3.10); points: (n_p, 3) float64 CUDA tensor."""
+    import torch
+    if not (points.is_cuda and points.dtype == torch.float64 and points.is_contiguous()):
+        raise ValueError("points must be a contiguous float64 CUDA tensor of shape (n_p, 3)")
+    g = grid if isinstance(grid, vp_grid) else grid_of(grid)
+    med = medium if isinstance(medium, vp_medium) else make_medium(medium)
+    _check(lib.vp_incident_field(ctypes.byref(g), ctypes.c_void_p(points.data_ptr()), int(points.shape[0]),
+                                 float(bowl.l), float(bowl.R), float(bowl.f0), float(bowl.p0), ctypes.byref(med),
+                                 _ptr(out), _stream(stream)), "vp_incident_field")
+
+
+def vp_version() -> str:
+    return lib.vp_version().decode()

@@ -1,0 +1,112 @@
+"""C ABI checks that need no GPU: the library loads, exports every declared entry
+point, and rejects bad arguments on the host before touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "vp.h")
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"VP_API\s+[\w\s\*]+?\b(vp_\w+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def vp():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2011_03009_gb300 import vp as vpmod
+    return vpmod
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("vp_plan", "vp_kernel_fft", "vp_source_assemble", "vp_apply",
+                     "vp_restrict_to_nested_box", "vp_destroy", "vp_status_string"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(vp):
+    lib = ctypes.CDLL(vp.LIB_PATH)
+    missing = [n for n in _declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings(vp):
+    assert vp.status_string(0) == "VP_OK"
+    for code in range(-8, 0):
+        assert vp.status_string(code).startswith("VP_ERR_")
+    assert "unknown" in vp.status_string(-99)
+    assert "sm_103a" in vp.vp_version()
+
+
+def _medium(vp):
+    return vp.vp_medium(1500.0, 1000.0, 3.5, 0.22, 2.0)
+
+
+def _plan_status(vp, grid, harmonic=2, f0=1e6, med=None, opts=None):
+    h = ctypes.c_void_p(0)
+    st = vp.lib.vp_plan(ctypes.byref(grid) if grid is not None else None, harmonic, f0,
+                        ctypes.byref(med if med is not None else _medium(vp)),
+                        ctypes.byref(opts) if opts is not None else None, None, ctypes.byref(h))
+    return st, h
+
+
+def test_plan_rejects_bad_arguments_on_the_host(vp):
+    good = vp.make_grid((8, 8, 8), (0, 0, 0), 1e-4)
+    assert _plan_status(vp, None)[0] == vp.VP_ERR_ARG
+    assert _plan_status(vp, vp.make_grid((0, 8, 8), (0, 0, 0), 1e-4))[0] == vp.VP_ERR_ARG
+    assert _plan_status(vp, vp.make_grid((8, 8, 8), (0, 0, 0), 0.0))[0] == vp.VP_ERR_ARG
+    assert _plan_status(vp, vp.make_grid((8, 8, 8), (0, 0, 0), -1e-4))[0] == vp.VP_ERR_ARG
+    assert _plan_status(vp, good, harmonic=0)[0] == vp.VP_ERR_ARG
+    assert _plan_status(vp, good, f0=0.0)[0] == vp.VP_ERR_ARG
+    bad_med = vp.vp_medium(0.0, 1000.0, 3.5, 0.22, 2.0)
+    assert _plan_status(vp, good, med=bad_med)[0] == vp.VP_ERR_ARG
+    neg_att = vp.vp_medium(1500.0, 1000.0, 3.5, -1.0, 2.0)
+    assert _plan_status(vp, good, med=neg_att)[0] == vp.VP_ERR_ARG
+    st, h = _plan_status(vp, good, harmonic=99)
+    assert st == vp.VP_ERR_UNSUPPORTED and not h.value
+
+
+def test_plan_rejects_bad_sizes_on_the_host(vp):
+    good = vp.make_grid((8, 8, 8), (0, 0, 0), 1e-4)
+    o = vp.vp_plan_opts()
+    o.m[0], o.m[1], o.m[2] = 14, 16, 16          # M < 2N - 1
+    assert _plan_status(vp, good, opts=o)[0] == vp.VP_ERR_SIZE
+    o = vp.vp_plan_opts()
+    o.m[0], o.m[1], o.m[2] = 22, 16, 16          # 22 = 2 * 11 has no schedule
+    assert _plan_status(vp, good, opts=o)[0] == vp.VP_ERR_SIZE
+    o = vp.vp_plan_opts()
+    o.radix[0][0], o.radix[0][1] = 4, 2          # product 8 != M = 16
+    assert _plan_status(vp, good, opts=o)[0] == vp.VP_ERR_SIZE
+    o = vp.vp_plan_opts()
+    o.radix[0][0], o.radix[0][1] = 7, 2          # radix 7 unsupported
+    assert _plan_status(vp, good, opts=o)[0] == vp.VP_ERR_SIZE
+    assert _plan_status(vp, vp.make_grid((801, 8, 8), (0, 0, 0), 1e-4))[0] == vp.VP_ERR_SIZE
+
+
+def test_other_calls_reject_bad_arguments_on_the_host(vp):
+    P = ctypes.c_void_p
+    assert vp.lib.vp_kernel_fft(None, None) == vp.VP_ERR_ARG
+    assert vp.lib.vp_apply(None, None, P(16), None) == vp.VP_ERR_ARG
+    assert vp.lib.vp_source_assemble(None, None, 1, 0, None, None) == vp.VP_ERR_ARG
+    assert vp.lib.vp_destroy(None) == vp.VP_OK
+    assert vp.lib.vp_profile_enable(None, 1) == vp.VP_ERR_ARG
+    src = vp.make_grid((5, 5, 5), (0.0, 0.0, 0.0), 1e-3)
+    dst_out = vp.make_grid((3, 3, 3), (0.0, 0.0, 0.0031), 1e-3)
+    assert vp.lib.vp_restrict_to_nested_box(ctypes.byref(src), P(64), ctypes.byref(dst_out), P(64), 0,
+                                            None) == vp.VP_ERR_NOT_NESTED
+    assert vp.lib.vp_restrict_to_nested_box(ctypes.byref(src), None, ctypes.byref(src), P(64), 0,
+                                            None) == vp.VP_ERR_ARG
+    assert vp.lib.vp_restrict_to_nested_box(ctypes.byref(src), P(64), ctypes.byref(src), P(64), 8,
+                                            None) == vp.VP_ERR_ARG
+    med = _medium(vp)
+    assert vp.lib.vp_incident_field(ctypes.byref(src), P(64), 0, 0.02, 0.01, 1e6, 1e5, ctypes.byref(med), P(64),
+                                    None) == vp.VP_ERR_ARG
+    assert vp.lib.vp_incident_field(ctypes.byref(src), P(64), 10, 0.02, 0.03, 1e6, 1e5, ctypes.byref(med), P(64),
+                                    None) == vp.VP_ERR_ARG

@@ -1,0 +1,225 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerance: relative L2 error <= 1e-5 over every output voxel for the FP32 path
+(the single-precision target of the method's volume potential), tighter where the
+arithmetic allows.  Sizes span several 16-line tiles, ragged tails and odd axes.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import cascade, interp, physics, potential, rayleigh
+from paper_2011_03009_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+REL_L2 = 1e-5
+
+
+@pytest.fixture(scope="module")
+def vp(cuda_device):
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2011_03009_gb300 import vp as vpmod
+    return vpmod
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a).astype(np.complex64)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy().astype(np.complex128)
+
+
+def rel_l2(got, ref):
+    return float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+
+
+def grid(n, h=1.25e-4, origin=(0.0, 0.0, 0.0)):
+    return synth.Grid(tuple(n), tuple(origin), h)
+
+
+def gpu_apply(vp, g, f, harmonic, f0=1.0e6, m=None, radix=None):
+    plan = vp.vp_plan(g, harmonic, f0, synth.WATER, m=m, radix=radix)
+    vp.vp_kernel_fft(plan)
+    u = torch.empty(g.n, dtype=torch.complex64, device="cuda")
+    vp.vp_apply(plan, dev(f), u)
+    out = host(u)
+    plan.close()
+    return out
+
+
+@pytest.mark.parametrize("n", [(8, 8, 8), (12, 9, 7), (16, 16, 16), (33, 20, 17), (1, 5, 3), (40, 48, 36),
+                               (2, 1, 1), (1, 1, 1)])
+def test_apply_matches_oracle(vp, n):
+    g = grid(n)
+    k = physics.wavenumber(2, 1.0e6, synth.WATER)
+    f = synth.random_field(n, seed=sum(n))
+    ref = potential.apply_fft(f, g.h, k)
+    got = gpu_apply(vp, g, f, 2)
+    assert rel_l2(got, ref) <= REL_L2
+
+
+@pytest.mark.parametrize("m,radix", [
+    ((32, 32, 36), ((2, 16), (4, 8), (4, 3, 3))),
+    ((40, 30, 45), ((8, 5), (5, 3, 2), (5, 3, 3))),
+    ((48, 45, 50), ((16, 3), (5, 3, 3), (5, 5, 2))),
+    ((64, 60, 80), ((4, 4, 4), (3, 4, 5), (16, 5))),
+])
+def test_every_radix_and_embedding_size(vp, m, radix):
+    n = (16, 15, 17)
+    g = grid(n, h=9e-5)
+    k = physics.wavenumber(3, 1.1e6, synth.WATER)
+    f = synth.random_field(n, seed=5)
+    ref = potential.apply_fft(f, g.h, k)
+    got = gpu_apply(vp, g, f, 3, f0=1.1e6, m=m, radix=radix)
+    assert rel_l2(got, ref) <= REL_L2
+
+
+def test_apply_matches_bruteforce_definition(vp):
+    n = (10, 13, 9)
+    g = grid(n, h=6e-5)
+    k = physics.wavenumber(4, 1.1e6, synth.WATER)
+    f = synth.random_field(n, seed=9)
+    ref = potential.apply_bruteforce(f, g.h, k)
+    got = gpu_apply(vp, g, f, 4, f0=1.1e6)
+    assert rel_l2(got, ref) <= REL_L2
+
+
+def test_kernel_spectrum_octant(vp):
+    n = (12, 10, 9)
+    g = grid(n)
+    plan = vp.vp_plan(g, 2, 1.0e6, synth.WATER)
+    vp.vp_kernel_fft(plan)
+    inf = plan.info()
+    m = tuple(inf.m)
+    o = tuple(v // 2 + 1 for v in m)
+    buf = torch.empty(o, dtype=torch.complex64, device="cuda")
+    plan.kernel_spectrum_get(buf)
+    got = host(buf)
+    plan.close()
+    full = potential.kernel_spectrum(n, g.h, physics.wavenumber(2, 1.0e6, synth.WATER), m)
+    ref = full[: o[0], : o[1], : o[2]]
+    assert rel_l2(got, ref) <= 1e-6
+    # even spectrum: K^(q) = K^(M - q)
+    assert np.allclose(full[1:, :, :], full[:0:-1, :, :], rtol=1e-10, atol=1e-10 * np.abs(full).max())
+
+
+def test_plan_info_constants(vp):
+    g = grid((8, 8, 8))
+    plan = vp.vp_plan(g, 3, 1.1e6, synth.WATER)
+    inf = plan.info()
+    k = physics.wavenumber(3, 1.1e6, synth.WATER)
+    assert abs(complex(inf.k_re, inf.k_im) - k) <= 1e-12 * abs(k)
+    assert abs(inf.c_n - physics.source_coefficient(3, 1.1e6, synth.WATER)) <= 1e-12 * abs(inf.c_n)
+    from oracle import greens
+    sc = greens.self_cell(k, g.h)
+    assert abs(complex(inf.self_re, inf.self_im) - sc) <= 1e-12 * abs(sc)
+    assert tuple(inf.m) == (16, 16, 16)
+    plan.close()
+
+
+@pytest.mark.parametrize("harmonic", [2, 3, 4, 5])
+def test_source_assembly_matches_oracle(vp, harmonic):
+    n = (9, 17, 20)
+    g = grid(n)
+    lower = [synth.random_field(n, seed=100 + m) for m in range(1, harmonic)]
+    plan = vp.vp_plan(g, harmonic, 1.1e6, synth.WATER)
+    f = torch.empty(n, dtype=torch.complex64, device="cuda")
+    plan.source_assemble([dev(x) for x in lower], f_out=f)
+    got = host(f)
+    ref = cascade.source_term(harmonic, lower, 1.1e6, synth.WATER)
+    assert rel_l2(got, ref) <= 1e-6
+    # fused path: assembly straight into the first FFT sweep, then the apply
+    vp.vp_kernel_fft(plan)
+    u = torch.empty(n, dtype=torch.complex64, device="cuda")
+    plan.source_assemble([dev(x) for x in lower])
+    plan.apply(None, u)
+    got_u = host(u)
+    plan.close()
+    ref_u = cascade.harmonic(harmonic, lower, g.h, 1.1e6, synth.WATER)
+    assert rel_l2(got_u, ref_u) <= REL_L2
+
+
+def test_call_order_errors(vp):
+    g = grid((8, 8, 8))
+    plan = vp.vp_plan(g, 2, 1.0e6, synth.WATER)
+    u = torch.empty(g.n, dtype=torch.complex64, device="cuda")
+    with pytest.raises(vp.VpError) as e:
+        plan.apply(dev(np.zeros(g.n)), u)
+    assert e.value.status == vp.VP_ERR_STATE
+    vp.vp_kernel_fft(plan)
+    with pytest.raises(vp.VpError) as e:
+        plan.apply(None, u)
+    assert e.value.status == vp.VP_ERR_STATE
+    with pytest.raises(vp.VpError) as e:
+        plan.source_assemble([dev(np.zeros(g.n)), dev(np.zeros(g.n))])
+    assert e.value.status == vp.VP_ERR_ARG
+    plan.close()
+
+
+def test_restriction_matches_oracle(vp):
+    src = synth.Grid((21, 19, 23), (0.01, -0.003, -0.0032), 3.1e-4)
+    dst = synth.centred_grid((30, 27, 33), 1.7e-4, (0.0131, -0.0001, 0.0002))
+    f = synth.random_field(src.n, seed=3)
+    out = torch.empty(dst.n, dtype=torch.complex64, device="cuda")
+    vp.vp_restrict_to_nested_box(src, dev(f), dst, out)
+    got = host(out)
+    ref = interp.restrict_trilinear(f, src, dst)
+    assert rel_l2(got, ref) <= 1e-6
+    # identical grids: identity
+    same = torch.empty(src.n, dtype=torch.complex64, device="cuda")
+    vp.vp_restrict_to_nested_box(src, dev(f), src, same)
+    assert rel_l2(host(same), f.astype(np.complex64).astype(np.complex128)) <= 1e-7
+
+
+def test_restriction_not_nested(vp):
+    src = synth.Grid((5, 5, 5), (0.0, 0.0, 0.0), 1e-3)
+    dst = synth.Grid((3, 3, 3), (0.0, 0.0, 0.0031), 1e-3)
+    out = torch.empty(dst.n, dtype=torch.complex64, device="cuda")
+    with pytest.raises(vp.VpError) as e:
+        vp.vp_restrict_to_nested_box(src, dev(np.ones(src.n)), dst, out)
+    assert e.value.status == vp.VP_ERR_NOT_NESTED
+    vp.vp_restrict_to_nested_box(src, dev(np.ones(src.n)), dst, out, zero_outside=True)
+    got = host(out)
+    assert np.all(got[:, :, 1:] == 0) and np.allclose(got[:, :, 0], 1.0)
+
+
+def test_incident_field_matches_oracle(vp):
+    bowl = synth.Bowl(l=0.02, R=0.01, f0=1.0e6, p0=0.5e6)
+    g = synth.focus_grid(bowl, (14, 11, 9), 2)
+    pts = synth.sample_bowl_points(bowl, 700, seed=4)
+    out = torch.empty(g.n, dtype=torch.complex64, device="cuda")
+    vp.vp_incident_field(g, torch.from_numpy(pts).cuda(), bowl, synth.WATER, out)
+    got = host(out)
+    ref = rayleigh.incident_field(g, pts, bowl, synth.WATER)
+    assert rel_l2(got, ref) <= 2e-6
+
+
+def test_small_workload_end_to_end(vp):
+    """32^3 second harmonic of the 1 cm / 2 cm / 1 MHz bowl, against oracle and brute force."""
+    w = synth.workload_small_p2()
+    g = w.steps[0].grid
+    pts = synth.sample_bowl_points(w.bowl, w.n_points, w.seed)
+    p1 = torch.empty(g.n, dtype=torch.complex64, device="cuda")
+    vp.vp_incident_field(g, torch.from_numpy(pts).cuda(), w.bowl, w.medium, p1)
+    plan = vp.vp_plan(g, 2, w.bowl.f0, w.medium)
+    vp.vp_kernel_fft(plan)
+    u = torch.empty(g.n, dtype=torch.complex64, device="cuda")
+    vp.vp_source_assemble(plan, [p1])
+    vp.vp_apply(plan, None, u)
+    got = host(u)
+    plan.close()
+    p1_ref = rayleigh.incident_field(g, pts, w.bowl, w.medium)
+    assert rel_l2(host(p1), p1_ref) <= 2e-6
+    ref = cascade.harmonic(2, [p1_ref], g.h, w.bowl.f0, w.medium)
+    assert rel_l2(got, ref) <= REL_L2
+    f = cascade.source_term(2, [p1_ref], w.bowl.f0, w.medium)
+    k2 = physics.wavenumber(2, w.bowl.f0, w.medium)
+    rng = np.random.default_rng(0)
+    tg = rng.integers(0, 32, size=(12, 3))
+    bf = potential.apply_bruteforce(f, g.h, k2, targets=tg)
+    sel = got[tg[:, 0], tg[:, 1], tg[:, 2]]
+    assert np.linalg.norm(sel - bf) <= REL_L2 * np.linalg.norm(bf) * 3
