@@ -106,7 +106,7 @@ typedef struct vp_plan_info {
  * `opts` may be NULL.  `stream` is used only when opts->autotune is set.
  * Errors: VP_ERR_ARG (null pointers, n[i] < 1, h <= 0, harmonic < 1, c0 <= 0,
  * rho0 <= 0, alpha0 < 0, f0 <= 0), VP_ERR_SIZE (M < 2N - 1, or an axis the FFT
- * engine cannot hold: M > 1600, or a radix schedule whose product is not M or that
+ * engine cannot hold: M > 1536, or a radix schedule whose product is not M or that
  * uses a radix outside {2,3,4,5,8,16}), VP_ERR_NOMEM, VP_ERR_CUDA.
  * On error *out is set to NULL and nothing is leaked. */
 VP_API int vp_plan(const vp_grid* g, int harmonic_n, double f0_hz, const vp_medium* m,

@@ -25,17 +25,19 @@ def nvcc() -> str:
     return exe
 
 
-def _flags(verbose: bool) -> list:
+def _flags(verbose: bool, debug: bool = False) -> list:
     f = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-fvisibility=hidden",
          "-I", INCLUDE, "-I", CSRC, *ARCH]
     if verbose:
         f += ["-Xptxas", "-v"]
+    if debug:
+        f += ["-DVP_DEBUG_CHECKS"]
     return f
 
 
-def _compile(src: str, verbose: bool) -> tuple:
+def _compile(src: str, verbose: bool, debug: bool = False) -> tuple:
     obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
-    cmd = [nvcc(), "-c", os.path.join(CSRC, src), "-o", obj, *_flags(verbose)]
+    cmd = [nvcc(), "-c", os.path.join(CSRC, src), "-o", obj, *_flags(verbose, debug)]
     r = subprocess.run(cmd, capture_output=True, text=True)
     return src, obj, r.returncode, r.stdout + r.stderr
 
@@ -48,13 +50,15 @@ def _stale() -> bool:
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile every CUDA source and link libvp.so next to this file; return its path."""
-    if not force and not _stale():
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    """Compile every CUDA source and link libvp.so next to this file; return its path.
+
+    debug=True adds the kernels' bounds self-checks (VP_DEBUG_CHECKS)."""
+    if not force and not debug and not _stale():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     with concurrent.futures.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        results = list(ex.map(lambda s: _compile(s, verbose), SOURCES))
+        results = list(ex.map(lambda s: _compile(s, verbose, debug), SOURCES))
     failed = [r for r in results if r[2] != 0]
     for src, _, rc, out in results:
         if verbose or rc != 0:
@@ -71,5 +75,5 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose="-v" in sys.argv)
+    build(force="--force" in sys.argv, verbose="-v" in sys.argv, debug="--debug" in sys.argv)
     print(LIB)

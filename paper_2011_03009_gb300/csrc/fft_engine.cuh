@@ -23,6 +23,36 @@
 
 namespace vp {
 
+// Debug builds (-DVP_DEBUG_CHECKS) check every shared- and global-memory index of the
+// sweep kernels: an index outside [0, n) is recorded (first one wins) and replaced by
+// 0, so the access stays in bounds.  Release builds compile the checks away.
+#ifdef VP_DEBUG_CHECKS
+static __device__ int g_vp_debug[8];  // per translation unit; read by vp_debug_checks
+__device__ __forceinline__ long long vp_chk(long long i, long long n, int code, int x0 = 0, int x1 = 0,
+                                            int x2 = 0, int x3 = 0) {
+  if (i < 0 || i >= n) {
+    if (atomicCAS(&g_vp_debug[0], 0, code) == 0) {
+      g_vp_debug[1] = (int)i;
+      g_vp_debug[2] = (int)n;
+      g_vp_debug[3] = (int)blockIdx.x;
+      g_vp_debug[4] = x0;
+      g_vp_debug[5] = x1;
+      g_vp_debug[6] = x2;
+      g_vp_debug[7] = x3;
+    }
+    return 0;
+  }
+  return i;
+}
+#define VP_CHK(i, n, code) ((int)vp_chk((i), (n), (code)))
+#define VP_CHKL(i, n, code) (vp_chk((i), (n), (code)))
+#define VP_CHKX(i, n, code, a, b, c, d) ((int)vp_chk((i), (n), (code), (a), (b), (c), (d)))
+#else
+#define VP_CHK(i, n, code) (i)
+#define VP_CHKL(i, n, code) (i)
+#define VP_CHKX(i, n, code, a, b, c, d) (i)
+#endif
+
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
@@ -159,106 +189,142 @@ __device__ __forceinline__ void dft(float2* v) {
   else if constexpr (R == 16) dft16<INV>(v);
 }
 
+// ---- asynchronous global -> shared copies (cp.async, all in flight at once) ---------
+
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool valid) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  const int n = valid ? 8 : 0;  // 0: zero-fill, nothing read
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// u / s for 0 <= u < 2^16 and 1 < s < 2^16 with magic = floor(2^32 / s) + 1: the
+// high word of u * magic is u/s + u e / 2^32 with 0 < e <= 1, exact below 2^16.
+// magic = 0 encodes s = 1.
+__device__ __forceinline__ int fast_div(int u, unsigned magic) {
+  return magic == 0u ? u : (int)__umulhi((unsigned)u, magic);
+}
+
 // ---- passes over a shared-memory tile -----------------------------------------------
+// tw points to the twiddle table (shared or global memory).  Element (row, line b) of
+// the tile sits at row * P + b, or with SW at row * 16 + (b ^ (row & 15)) (P = 16): the
+// XOR swizzle keeps both row-wise accesses (16 lines of one row) and column-wise
+// accesses (16 consecutive rows of one line) free of bank conflicts.
+template <int P, bool SW>
+__device__ __forceinline__ int tix(int row, int b) {
+  return SW ? row * 16 + (b ^ (row & 15)) : row * P + b;
+}
 
 // Forward DIF pass.  Rows >= rows_nz are treated as zero without being read.
-template <int R, int P>
-__device__ __forceinline__ void dif_pass(float2* tile, int L, int Lp, const float2* __restrict__ tw,
-                                         int rows_nz) {
+template <int R, int P, bool SW>
+__device__ __forceinline__ void dif_pass(float2* tile, int L, int Lp, unsigned magic,
+                                         const float2* tw, int rows_nz) {
   const int s = Lp / R;
   const int tws = L / Lp;
   const int nb = (L / R) * kTileB;
   for (int t = threadIdx.x; t < nb; t += blockDim.x) {
     const int b = t & (kTileB - 1);
     const int u = t >> 4;
-    const int blk = u / s;
+    const int blk = fast_div(u, magic);
     const int k = u - blk * s;
     const int base = blk * Lp + k;
     float2 v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int row = base + r * s;
-      v[r] = row < rows_nz ? tile[row * P + b] : make_float2(0.f, 0.f);
+      v[r] = row < rows_nz ? tile[VP_CHKX((tix<P, SW>(row, b)), L * 16, 101, u, Lp, (int)magic, blk)]
+                           : make_float2(0.f, 0.f);
     }
     dft<R, false>(v);
-    if (k != 0) {
 #pragma unroll
-      for (int q = 1; q < R; ++q) v[q] = cmul(v[q], __ldg(&tw[q * k * tws]));
-    }
+    for (int q = 1; q < R; ++q) v[q] = cmul(v[q], tw[VP_CHK(q * k * tws, L, 102)]);
 #pragma unroll
-    for (int q = 0; q < R; ++q) tile[(base + q * s) * P + b] = v[q];
+    for (int q = 0; q < R; ++q) tile[VP_CHK((tix<P, SW>(base + q * s, b)), L * 16, 103)] = v[q];
   }
 }
 
 // Inverse DIT pass (conjugate transpose of dif_pass).
-template <int R, int P>
-__device__ __forceinline__ void dit_pass(float2* tile, int L, int Lp, const float2* __restrict__ tw) {
+template <int R, int P, bool SW>
+__device__ __forceinline__ void dit_pass(float2* tile, int L, int Lp, unsigned magic,
+                                         const float2* tw) {
   const int s = Lp / R;
   const int tws = L / Lp;
   const int nb = (L / R) * kTileB;
   for (int t = threadIdx.x; t < nb; t += blockDim.x) {
     const int b = t & (kTileB - 1);
     const int u = t >> 4;
-    const int blk = u / s;
+    const int blk = fast_div(u, magic);
     const int k = u - blk * s;
     const int base = blk * Lp + k;
     float2 v[R];
 #pragma unroll
-    for (int q = 0; q < R; ++q) v[q] = tile[(base + q * s) * P + b];
-    if (k != 0) {
+    for (int q = 0; q < R; ++q) v[q] = tile[VP_CHK((tix<P, SW>(base + q * s, b)), L * 16, 104)];
 #pragma unroll
-      for (int q = 1; q < R; ++q) v[q] = cmulc(v[q], __ldg(&tw[q * k * tws]));
-    }
+    for (int q = 1; q < R; ++q) v[q] = cmulc(v[q], tw[VP_CHK(q * k * tws, L, 105)]);
     dft<R, true>(v);
 #pragma unroll
-    for (int r = 0; r < R; ++r) tile[(base + r * s) * P + b] = v[r];
+    for (int r = 0; r < R; ++r) tile[VP_CHK((tix<P, SW>(base + r * s, b)), L * 16, 106)] = v[r];
   }
 }
 
-template <int P>
-__device__ __forceinline__ void dif_pass_rt(int R, float2* tile, int L, int Lp,
-                                            const float2* __restrict__ tw, int rows_nz) {
-  switch (R) {
-    case 16: dif_pass<16, P>(tile, L, Lp, tw, rows_nz); break;
-    case 8: dif_pass<8, P>(tile, L, Lp, tw, rows_nz); break;
-    case 4: dif_pass<4, P>(tile, L, Lp, tw, rows_nz); break;
-    case 2: dif_pass<2, P>(tile, L, Lp, tw, rows_nz); break;
-    case 5: dif_pass<5, P>(tile, L, Lp, tw, rows_nz); break;
-    case 3: dif_pass<3, P>(tile, L, Lp, tw, rows_nz); break;
+template <int P, bool SW>
+__device__ __forceinline__ void dif_pass_rt(const AxisDesc& ax, int p, float2* tile, const float2* tw,
+                                            int rows_nz) {
+  const int L = ax.L, Lp = ax.lp[p];
+  const unsigned mg = ax.magic[p];
+  switch (ax.radix[p]) {
+    case 16: dif_pass<16, P, SW>(tile, L, Lp, mg, tw, rows_nz); break;
+    case 8: dif_pass<8, P, SW>(tile, L, Lp, mg, tw, rows_nz); break;
+    case 4: dif_pass<4, P, SW>(tile, L, Lp, mg, tw, rows_nz); break;
+    case 2: dif_pass<2, P, SW>(tile, L, Lp, mg, tw, rows_nz); break;
+    case 5: dif_pass<5, P, SW>(tile, L, Lp, mg, tw, rows_nz); break;
+    case 3: dif_pass<3, P, SW>(tile, L, Lp, mg, tw, rows_nz); break;
     default: break;
   }
 }
 
-template <int P>
-__device__ __forceinline__ void dit_pass_rt(int R, float2* tile, int L, int Lp,
-                                            const float2* __restrict__ tw) {
-  switch (R) {
-    case 16: dit_pass<16, P>(tile, L, Lp, tw); break;
-    case 8: dit_pass<8, P>(tile, L, Lp, tw); break;
-    case 4: dit_pass<4, P>(tile, L, Lp, tw); break;
-    case 2: dit_pass<2, P>(tile, L, Lp, tw); break;
-    case 5: dit_pass<5, P>(tile, L, Lp, tw); break;
-    case 3: dit_pass<3, P>(tile, L, Lp, tw); break;
+template <int P, bool SW>
+__device__ __forceinline__ void dit_pass_rt(const AxisDesc& ax, int p, float2* tile, const float2* tw) {
+  const int L = ax.L, Lp = ax.lp[p];
+  const unsigned mg = ax.magic[p];
+  switch (ax.radix[p]) {
+    case 16: dit_pass<16, P, SW>(tile, L, Lp, mg, tw); break;
+    case 8: dit_pass<8, P, SW>(tile, L, Lp, mg, tw); break;
+    case 4: dit_pass<4, P, SW>(tile, L, Lp, mg, tw); break;
+    case 2: dit_pass<2, P, SW>(tile, L, Lp, mg, tw); break;
+    case 5: dit_pass<5, P, SW>(tile, L, Lp, mg, tw); break;
+    case 3: dit_pass<3, P, SW>(tile, L, Lp, mg, tw); break;
     default: break;
   }
 }
 
 // Full forward transform of the tile (DIF, digit-reversed output).
-template <int P>
-__device__ __forceinline__ void tile_forward(float2* tile, const AxisDesc& ax, int rows_nz) {
+template <int P, bool SW>
+__device__ __forceinline__ void tile_forward(float2* tile, const AxisDesc& ax, const float2* tw, int rows_nz) {
   for (int p = 0; p < ax.npass; ++p) {
-    dif_pass_rt<P>(ax.radix[p], tile, ax.L, ax.lp[p], ax.tw, p == 0 ? rows_nz : ax.L);
+    dif_pass_rt<P, SW>(ax, p, tile, tw, p == 0 ? rows_nz : ax.L);
     __syncthreads();
   }
 }
 
 // Full inverse transform of the tile (DIT, digit-reversed input, natural output, x L).
-template <int P>
-__device__ __forceinline__ void tile_inverse(float2* tile, const AxisDesc& ax) {
+template <int P, bool SW>
+__device__ __forceinline__ void tile_inverse(float2* tile, const AxisDesc& ax, const float2* tw) {
   for (int p = ax.npass - 1; p >= 0; --p) {
-    dit_pass_rt<P>(ax.radix[p], tile, ax.L, ax.lp[p], ax.tw);
+    dit_pass_rt<P, SW>(ax, p, tile, tw);
     __syncthreads();
   }
+}
+
+// Stage the axis twiddle table into shared memory (cp.async; caller waits).
+__device__ __forceinline__ void stage_twiddles(float2* tw_s, const AxisDesc& ax) {
+  for (int i = threadIdx.x; i < ax.L; i += blockDim.x) cp_async8(&tw_s[VP_CHK(i, ax.L, 107)], &ax.tw[i], true);
 }
 
 }  // namespace vp

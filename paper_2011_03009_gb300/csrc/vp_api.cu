@@ -48,6 +48,8 @@ struct vp_plan_s {
   float2* khat = nullptr;
   float2* wsA = nullptr;  // M_x N_y N_z
   float2* wsB = nullptr;  // M_x M_y N_z
+  int* ztiles = nullptr;  // z-sweep tiles: 16 line indices + 4 octant-line indices each
+  long long nztiles = 0;
   unsigned long long bytes = 0;
   bool khat_ready = false;
   bool staged = false;
@@ -134,6 +136,7 @@ void free_plan(vp_plan_s* p) {
   cudaFree(p->khat);
   cudaFree(p->wsA);
   cudaFree(p->wsB);
+  cudaFree(p->ztiles);
   for (auto& r : p->prof) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
@@ -149,7 +152,7 @@ int upload(T** dst, const std::vector<T>& v, unsigned long long* bytes) {
   return VP_OK;
 }
 
-int build_axis_tables(vp_plan_s* p, int a) {
+int build_axis_tables(vp_plan_s* p, int a, std::vector<int>* pos_out) {
   const int L = p->m[a];
   const int np = p->npass[a];
   std::vector<float2> tw(L);
@@ -176,11 +179,40 @@ int build_axis_tables(vp_plan_s* p, int a) {
     pos[f] = pp;
     fold[pp] = std::min(f, L - f);
   }
+  *pos_out = pos;
   int st;
   if ((st = upload(&p->tw[a], tw, &p->bytes)) != VP_OK) return st;
   if ((st = upload(&p->pos[a], pos, &p->bytes)) != VP_OK) return st;
   if ((st = upload(&p->fold[a], fold, &p->bytes)) != VP_OK) return st;
   return VP_OK;
+}
+
+// Tiles of the z sweep: the lines whose (x, y) frequencies fold onto one octant line
+// (f_x in {o_x, M_x - o_x}, f_y in {o_y, M_y - o_y}) form a group of up to four; four
+// groups make a tile of 16 line slots, so each CTA stages only four octant lines of
+// the spectrum.  Line index = p_x M_y + p_y with p the DIF position of the frequency.
+int build_z_tiles(vp_plan_s* p, const std::vector<int>& pos_x, const std::vector<int>& pos_y) {
+  const int Mx = p->m[0], My = p->m[1], Ox = p->oct[0], Oy = p->oct[1];
+  const long long groups = (long long)Ox * Oy;
+  p->nztiles = (groups + 3) / 4;
+  std::vector<int> t((size_t)p->nztiles * 20, -1);
+  long long g = 0;
+  for (int ox = 0; ox < Ox; ++ox) {
+    int fx[2] = {ox, Mx - ox};
+    const int nfx = (ox == 0 || 2 * ox == Mx) ? 1 : 2;
+    for (int oy = 0; oy < Oy; ++oy, ++g) {
+      int fy[2] = {oy, My - oy};
+      const int nfy = (oy == 0 || 2 * oy == My) ? 1 : 2;
+      const long long tile = g / 4;
+      const int slot0 = (int)(g % 4) * 4;
+      int k = 0;
+      for (int i = 0; i < nfx; ++i)
+        for (int j = 0; j < nfy; ++j)
+          t[(size_t)tile * 20 + slot0 + k++] = pos_x[fx[i] % Mx] * My + pos_y[fy[j] % My];
+      t[(size_t)tile * 20 + 16 + (g % 4)] = ox * Oy + oy;
+    }
+  }
+  return upload(&p->ztiles, t, &p->bytes);
 }
 
 AxisDesc axis_desc(const vp_plan_s* p, int a) {
@@ -191,7 +223,12 @@ AxisDesc axis_desc(const vp_plan_s* p, int a) {
   for (int i = 0; i < vp::kMaxPass; ++i) {
     d.radix[i] = p->radix[a][i];
     d.lp[i] = i < d.npass ? lp : 0;
-    if (i < d.npass) lp /= d.radix[i];
+    d.magic[i] = 0;
+    if (i < d.npass) {
+      const unsigned long long s = (unsigned long long)(lp / d.radix[i]);
+      d.magic[i] = s > 1 ? (unsigned)((1ULL << 32) / s + 1) : 0u;
+      lp /= d.radix[i];
+    }
   }
   d.tw = p->tw[a];
   return d;
@@ -256,6 +293,8 @@ int run_sweep(vp_plan_s* p, int which, const float2* f, const float2* const* low
       c.out_rs = (long long)Ny * Nz;
       c.out_os = Nz;
       c.rows_out = Mx;
+      c.in_elems = (long long)Nx * Ny * Nz;
+      c.out_elems = (long long)Mx * Ny * Nz;
       if (lower) {
         c.harmonic = p->harmonic;
         c.cn = (float)p->cn;
@@ -271,6 +310,8 @@ int run_sweep(vp_plan_s* p, int which, const float2* f, const float2* const* low
       c.out_rs = (long long)Ny * Nz;
       c.out_os = Nz;
       c.rows_out = Nx;
+      c.in_elems = (long long)Mx * Ny * Nz;
+      c.out_elems = (long long)Nx * Ny * Nz;
       c.scale = (float)(1.0 / ((double)p->m[0] * p->m[1] * p->m[2]));
       e = vp::launch_col_sweep(c, vp::kInverse, false, s);
     }
@@ -289,6 +330,8 @@ int run_sweep(vp_plan_s* p, int which, const float2* f, const float2* const* low
       c.out_rs = Nz;
       c.out_os = (long long)My * Nz;
       c.rows_out = My;
+      c.in_elems = (long long)Mx * Ny * Nz;
+      c.out_elems = (long long)Mx * My * Nz;
       e = vp::launch_col_sweep(c, vp::kForward, false, s);
     } else {
       c.in = p->wsB;
@@ -299,22 +342,22 @@ int run_sweep(vp_plan_s* p, int which, const float2* f, const float2* const* low
       c.out_rs = Nz;
       c.out_os = (long long)Ny * Nz;
       c.rows_out = Ny;
+      c.in_elems = (long long)Mx * My * Nz;
+      c.out_elems = (long long)Mx * Ny * Nz;
       e = vp::launch_col_sweep(c, vp::kInverse, false, s);
     }
   } else {
     LineSweep l{};
     l.ax = axis_desc(p, 2);
     l.data = p->wsB;
-    l.nlines = (long long)Mx * My;
+    l.nlines = p->nztiles;
     l.ld = Nz;
     l.n_in = Nz;
     l.n_out = Nz;
+    l.data_elems = (long long)Mx * My * Nz;
     l.khat = p->khat;
-    l.My = My;
-    l.Oy = p->oct[1];
     l.Oz = p->oct[2];
-    l.fold_x = p->fold[0];
-    l.fold_y = p->fold[1];
+    l.tiles = p->ztiles;
     l.fold_z = p->fold[2];
     e = vp::launch_line_sweep(l, vp::kConv, s);
   }
@@ -402,7 +445,9 @@ VP_API int vp_plan(const vp_grid* g, int harmonic_n, double f0_hz, const vp_medi
   p->self_im = sc.imag();
 
   int st = VP_OK;
-  for (int a = 0; a < 3 && st == VP_OK; ++a) st = build_axis_tables(p, a);
+  std::vector<int> hpos[3];
+  for (int a = 0; a < 3 && st == VP_OK; ++a) st = build_axis_tables(p, a, &hpos[a]);
+  if (st == VP_OK) st = build_z_tiles(p, hpos[0], hpos[1]);
   const size_t nA = (size_t)m[0] * g->n[1] * g->n[2];
   const size_t nB = (size_t)m[0] * m[1] * g->n[2];
   const size_t nK = (size_t)p->oct[0] * p->oct[1] * p->oct[2];
@@ -467,6 +512,7 @@ VP_API int vp_kernel_fft(vp_plan_t p, vp_stream_t stream) {
     c.n_outer = My;
     c.rows_in = Mx;
     c.rows_out = Mx;
+    c.in_elems = c.out_elems = (long long)total;
     c.scale = 1.0f;
     e = vp::launch_col_sweep(c, vp::kForward, false, s);
   }
@@ -481,6 +527,7 @@ VP_API int vp_kernel_fft(vp_plan_t p, vp_stream_t stream) {
     c.n_outer = Mx;
     c.rows_in = My;
     c.rows_out = My;
+    c.in_elems = c.out_elems = (long long)total;
     c.scale = 1.0f;
     e = vp::launch_col_sweep(c, vp::kForward, false, s);
   }
@@ -492,6 +539,7 @@ VP_API int vp_kernel_fft(vp_plan_t p, vp_stream_t stream) {
     l.ld = Mz;
     l.n_in = Mz;
     l.n_out = Mz;
+    l.data_elems = (long long)total;
     e = vp::launch_line_sweep(l, vp::kForwardOnly, s);
   }
   if (e == cudaSuccess) e = vp::launch_octant_extract(tmp, p->khat, p->m, p->oct, p->pos[0], p->pos[1], p->pos[2], s);

@@ -12,7 +12,7 @@ constexpr int kMaxPass = 8;      // radix passes per axis
 constexpr int kMaxLower = 8;     // lower harmonics fed to one source assembly
 constexpr int kTileB = 16;       // lines per CTA tile in every FFT sweep
 constexpr int kThreads = 256;    // threads per CTA of the FFT sweeps
-constexpr int kMaxL = 1600;      // longest FFT line the shared-memory tile holds
+constexpr int kMaxL = 1536;      // longest FFT line the shared-memory tile holds
 
 // One FFT axis: its length, radix schedule and twiddle table.
 struct AxisDesc {
@@ -20,6 +20,7 @@ struct AxisDesc {
   int npass;
   int radix[kMaxPass];
   int lp[kMaxPass];        // sub-transform length entering pass p (L, L/R0, L/(R0 R1), ...)
+  unsigned magic[kMaxPass];  // floor(2^32 / s_p) + 1 for s_p = lp[p] / radix[p] > 1; 0 when s_p = 1
   const float2* tw;        // L entries, exp(-2 pi i t / L), built in FP64 on the host
 };
 
@@ -33,6 +34,7 @@ struct ColSweep {
   int n_outer;
   int rows_in;    // rows read (rows beyond are zero padding)
   int rows_out;   // rows written
+  long long in_elems, out_elems;  // buffer sizes (elements), for debug-build bounds checks
   float scale;
   AxisDesc ax;
   // source-assembly prologue (first forward sweep fused with Eq. 2.6)
@@ -42,19 +44,23 @@ struct ColSweep {
 };
 
 // Line sweep: FFT along the contiguous axis, 16 lines per CTA.
+// Convolution mode: tile t holds the lines listed in tiles[20 t .. 20 t + 15] (line
+// index or -1) and multiplies lines 4g..4g+3 by octant line tiles[20 t + 16 + g] of the
+// kernel spectrum; each group of four lines are the mirror images (f_x, M_x - f_x) x
+// (f_y, M_y - f_y) of one octant line.  Forward-only mode: tile t holds lines 16t..16t+15.
 struct LineSweep {
   float2* data;
-  long long nlines;
+  long long nlines;     // forward-only mode: number of lines; convolution mode: number of tiles
   long long ld;   // distance between consecutive lines (elements)
   int n_in;       // elements read per line (rest is zero padding up to L)
   int n_out;      // elements written per line
+  long long data_elems;  // buffer size (elements), for debug-build bounds checks
   AxisDesc ax;
   // spectrum multiply (convolution mode)
   const float2* khat;   // octant (Ox, Oy, Oz)
-  int My, Oy, Oz;
-  const int* fold_x;    // position -> folded frequency, per axis
-  const int* fold_y;
-  const int* fold_z;
+  int Oz;
+  const int* tiles;     // 20 ints per tile
+  const int* fold_z;    // z position -> folded frequency
 };
 
 enum SweepDir { kForward = 0, kInverse = 1 };

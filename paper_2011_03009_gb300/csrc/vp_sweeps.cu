@@ -14,138 +14,167 @@ namespace vp {
 
 namespace {
 
-constexpr int kColP = kTileB;       // column tiles: rows of 16 columns, no padding needed
-constexpr int kLineP = kTileB + 1;  // line tiles are written transposed: pad to dodge conflicts
-constexpr size_t kColMax = (size_t)kMaxL * kColP * sizeof(float2);
-constexpr size_t kLineMax = (size_t)kMaxL * kLineP * sizeof(float2);
+constexpr int kColP = kTileB;  // column tiles: rows of 16 columns (row-wise accesses only)
+constexpr int kSrcChunk = 8;   // elements per thread per batch of source-assembly loads
+
+// Shared memory of one column-sweep CTA: twiddles (L) then the tile (16 L).
+__host__ __device__ constexpr size_t col_smem(int L) { return (size_t)L * (1 + kColP) * sizeof(float2); }
+// Shared memory of one line-sweep CTA: the tile (16 L, swizzled), the z fold table
+// (L ints) and four staged octant lines of the spectrum (4 Oz).
+__host__ __device__ constexpr size_t line_smem(int L, int Oz) {
+  return (size_t)L * kTileB * sizeof(float2) + (size_t)((L + 1) & ~1) * sizeof(int) +
+         (size_t)Oz * 4 * sizeof(float2);
+}
 
 template <int DIR, bool SRC>
 __global__ void __launch_bounds__(kThreads) col_sweep_kernel(const ColSweep p) {
-  extern __shared__ float2 tile[];
+  extern __shared__ float2 smem[];
+  const int L = p.ax.L;
+  float2* tw_s = smem;
+  float2* tile = smem + L;
   const int ncb = (p.C + kTileB - 1) / kTileB;
   const int o = blockIdx.x / ncb;
   const int c0 = (blockIdx.x - o * ncb) * kTileB;
-  const int L = p.ax.L;
 
-  // load rows [0, rows_in) of 16 columns; forward sweeps treat the rest as zero
+  stage_twiddles(tw_s, p.ax);
   const int nload = p.rows_in * kTileB;
-  for (int e = threadIdx.x; e < nload; e += blockDim.x) {
-    const int i = e >> 4;
-    const int b = e & (kTileB - 1);
-    const int c = c0 + b;
-    float2 v = make_float2(0.f, 0.f);
-    if (c < p.C) {
-      const long long off = (long long)o * p.in_os + (long long)i * p.in_rs + c;
-      if constexpr (SRC) {
-        // f_n = C_n sum_{m=1}^{n-1} p_m p_{n-m}  (Eq. 2.6)
-        float2 f[kMaxLower];
-        const int nl = p.harmonic - 1;
+  if constexpr (SRC) {
+    // f_n = C_n sum_{m=1}^{n-1} p_m p_{n-m} (Eq. 2.6), summed over the pairs m <= n - m:
+    // each unordered pair appears twice in the sum unless m = n - m.
+    const int n = p.harmonic;
+    for (int e0 = threadIdx.x; e0 < nload; e0 += kSrcChunk * blockDim.x) {
+      float2 acc[kSrcChunk];
+      long long off[kSrcChunk];
+      bool ok[kSrcChunk];
 #pragma unroll
-        for (int m = 0; m < kMaxLower; ++m)
-          if (m < nl) f[m] = __ldg(&p.lower[m][off]);
-        float2 acc = make_float2(0.f, 0.f);
+      for (int j = 0; j < kSrcChunk; ++j) {
+        const int e = e0 + j * blockDim.x;
+        const int c = c0 + (e & (kTileB - 1));
+        ok[j] = e < nload && c < p.C;
+        off[j] = ok[j] ? (long long)o * p.in_os + (long long)(e >> 4) * p.in_rs + c : 0;
+        acc[j] = make_float2(0.f, 0.f);
+      }
+      for (int m = 1; 2 * m <= n; ++m) {
+        const float2* __restrict__ pa = p.lower[m - 1];
+        const float2* __restrict__ pb = p.lower[n - m - 1];
+        const float w = (2 * m == n) ? 1.f : 2.f;
+        float2 a[kSrcChunk], bb[kSrcChunk];
 #pragma unroll
-        for (int m = 1; m <= kMaxLower; ++m) {
-          if (m <= nl) {
-            const float2 a = f[m - 1];
-            float2 bb = a;
-#pragma unroll
-            for (int j = 0; j < kMaxLower; ++j)
-              if (j == p.harmonic - m - 1) bb = f[j];
-            acc = cadd(acc, cmul(a, bb));
-          }
+        for (int j = 0; j < kSrcChunk; ++j) {
+          a[j] = ok[j] ? __ldg(&pa[VP_CHKL(off[j], p.in_elems, 201)]) : make_float2(0.f, 0.f);
+          bb[j] = ok[j] ? __ldg(&pb[VP_CHKL(off[j], p.in_elems, 202)]) : make_float2(0.f, 0.f);
         }
-        v = cscale(acc, p.cn);
-      } else {
-        v = __ldg(&p.in[off]);
+#pragma unroll
+        for (int j = 0; j < kSrcChunk; ++j) acc[j] = cadd(acc[j], cscale(cmul(a[j], bb[j]), w));
+      }
+#pragma unroll
+      for (int j = 0; j < kSrcChunk; ++j) {
+        const int e = e0 + j * blockDim.x;
+        if (e < nload) tile[VP_CHK(e, L * 16, 203)] = cscale(acc[j], p.cn);
       }
     }
-    tile[i * kColP + b] = v;
+  } else {
+    for (int e = threadIdx.x; e < nload; e += blockDim.x) {
+      const int c = c0 + (e & (kTileB - 1));
+      const bool ok = c < p.C;
+      const long long off = ok ? (long long)o * p.in_os + (long long)(e >> 4) * p.in_rs + c : 0;
+      cp_async8(&tile[VP_CHK(e, L * 16, 204)], &p.in[VP_CHKL(off, p.in_elems, 205)], ok);
+    }
   }
+  cp_async_wait_all();
   __syncthreads();
 
-  if (DIR == kForward) tile_forward<kColP>(tile, p.ax, p.rows_in);
-  else tile_inverse<kColP>(tile, p.ax);
+  if (DIR == kForward) tile_forward<kColP, false>(tile, p.ax, tw_s, p.rows_in);
+  else tile_inverse<kColP, false>(tile, p.ax, tw_s);
 
   const int nstore = p.rows_out * kTileB;
   for (int e = threadIdx.x; e < nstore; e += blockDim.x) {
-    const int i = e >> 4;
-    const int b = e & (kTileB - 1);
-    const int c = c0 + b;
+    const int c = c0 + (e & (kTileB - 1));
     if (c < p.C) {
-      const long long off = (long long)o * p.out_os + (long long)i * p.out_rs + c;
-      float2 v = tile[i * kColP + b];
+      const long long off = (long long)o * p.out_os + (long long)(e >> 4) * p.out_rs + c;
+      float2 v = tile[VP_CHK(e, L * 16, 206)];
       if (DIR == kInverse) v = cscale(v, p.scale);
-      p.out[off] = v;
+      p.out[VP_CHKL(off, p.out_elems, 207)] = v;
     }
   }
-  (void)L;
 }
 
-// Lines along the contiguous axis: 16 lines per CTA, loaded coalesced and stored
-// transposed into the tile so that the engine sees the same [row][line] layout.
+// Lines along the contiguous axis: 16 lines per CTA, copied into the swizzled tile so
+// that the engine sees the same [row][line] layout as the column sweeps.
 template <int MODE>
 __global__ void __launch_bounds__(kThreads) line_sweep_kernel(const LineSweep p) {
-  extern __shared__ float2 tile[];
-  __shared__ long long kbase[kTileB];
-  const long long l0 = (long long)blockIdx.x * kTileB;
+  extern __shared__ float2 smem[];
+  __shared__ long long line_of[kTileB];
+  __shared__ int oct_of[4];
   const int L = p.ax.L;
+  float2* tile = smem;
+  int* fz_s = (int*)(smem + (size_t)L * kTileB);
+  float2* ks = (float2*)(fz_s + ((L + 1) & ~1));  // [Oz][4], 8-byte aligned
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nwarps = blockDim.x >> 5;
 
-  if (MODE == kConv && threadIdx.x < kTileB) {
-    const long long l = l0 + threadIdx.x;
-    long long kb = 0;
-    if (l < p.nlines) {
-      const int px = (int)(l / p.My);
-      const int py = (int)(l - (long long)px * p.My);
-      kb = ((long long)p.fold_x[px] * p.Oy + p.fold_y[py]) * p.Oz;
+  if (threadIdx.x < kTileB) {
+    long long l;
+    if (MODE == kConv) {
+      l = p.tiles[20LL * blockIdx.x + threadIdx.x];
+    } else {
+      l = (long long)blockIdx.x * kTileB + threadIdx.x;
+      if (l >= p.nlines) l = -1;
     }
-    kbase[threadIdx.x] = kb;
+    line_of[threadIdx.x] = l;
   }
+  if (MODE == kConv && threadIdx.x < 4) oct_of[threadIdx.x] = p.tiles[20LL * blockIdx.x + 16 + threadIdx.x];
+  __syncthreads();
 
-  const int nload = kTileB * p.n_in;
-  for (int e = threadIdx.x; e < nload; e += blockDim.x) {
-    const int b = e / p.n_in;
-    const int z = e - b * p.n_in;
-    const long long l = l0 + b;
-    float2 v = make_float2(0.f, 0.f);
-    if (l < p.nlines) v = p.data[l * p.ld + z];
-    tile[z * kLineP + b] = v;
+  for (int b = warp; b < kTileB; b += nwarps) {
+    const long long l = line_of[b];
+    const float2* src = p.data + (l < 0 ? 0 : l * p.ld);
+    if (l >= 0) VP_CHKL(l * p.ld + p.n_in - 1, p.data_elems, 301);
+    for (int z = lane; z < p.n_in; z += 32)
+      cp_async8(&tile[VP_CHK((tix<16, true>(z, b)), L * 16, 302)], &src[z], l >= 0);
   }
+  if (MODE == kConv) {
+    for (int i = threadIdx.x; i < L; i += blockDim.x) cp_async4(&fz_s[i], &p.fold_z[i]);
+    for (int g = warp & 3; g < 4; g += 4) {
+      const int oc = oct_of[g];
+      const float2* kl = p.khat + (oc < 0 ? 0 : (long long)oc * p.Oz);
+      for (int oz = (warp >> 2) * 32 + lane; oz < p.Oz; oz += (nwarps >> 2) * 32)
+        cp_async8(&ks[VP_CHK(oz * 4 + g, p.Oz * 4, 303)], &kl[oz], oc >= 0);
+    }
+  }
+  cp_async_wait_all();
   __syncthreads();
 
   if (MODE == kForwardOnly) {
-    tile_forward<kLineP>(tile, p.ax, p.n_in);
+    tile_forward<16, true>(tile, p.ax, p.ax.tw, p.n_in);
   } else {
     // forward passes except the last; the last forward pass, the spectrum multiply and
     // the first inverse pass run on the same registers (the last DIF pass has unit
     // twiddles, and so has the first DIT pass).
     const int P = p.ax.npass;
     for (int q = 0; q < P - 1; ++q) {
-      dif_pass_rt<kLineP>(p.ax.radix[q], tile, L, p.ax.lp[q], p.ax.tw, q == 0 ? p.n_in : L);
+      dif_pass_rt<16, true>(p.ax, q, tile, p.ax.tw, q == 0 ? p.n_in : L);
       __syncthreads();
     }
     const int R = p.ax.radix[P - 1];
     const int nb = (L / R) * kTileB;
-    const float2* __restrict__ kh = p.khat;
-    const int* __restrict__ fz = p.fold_z;
     const int rows_nz = P == 1 ? p.n_in : L;
-#define VP_CONV_CASE(RR)                                                         \
-  case RR: {                                                                     \
-    for (int t = threadIdx.x; t < nb; t += blockDim.x) {                         \
-      const int b = t & (kTileB - 1);                                            \
-      const int base = (t >> 4) * RR;                                            \
-      float2 v[RR];                                                              \
-      _Pragma("unroll") for (int r = 0; r < RR; ++r) {                           \
-        const int row = base + r;                                                \
-        v[r] = row < rows_nz ? tile[row * kLineP + b] : make_float2(0.f, 0.f);   \
-      }                                                                          \
-      dft<RR, false>(v);                                                         \
-      const long long kb = kbase[b];                                             \
-      _Pragma("unroll") for (int r = 0; r < RR; ++r)                             \
-        v[r] = cmul(v[r], __ldg(&kh[kb + __ldg(&fz[base + r])]));                \
-      dft<RR, true>(v);                                                          \
-      _Pragma("unroll") for (int r = 0; r < RR; ++r) tile[(base + r) * kLineP + b] = v[r]; \
-    }                                                                            \
+#define VP_CONV_CASE(RR)                                                               \
+  case RR: {                                                                           \
+    for (int t = threadIdx.x; t < nb; t += blockDim.x) {                               \
+      const int b = t & (kTileB - 1);                                                  \
+      const int base = (t >> 4) * RR;                                                  \
+      float2 v[RR];                                                                    \
+      _Pragma("unroll") for (int r = 0; r < RR; ++r) {                                 \
+        const int row = base + r;                                                      \
+        v[r] = row < rows_nz ? tile[tix<16, true>(row, b)] : make_float2(0.f, 0.f);    \
+      }                                                                                \
+      dft<RR, false>(v);                                                               \
+      _Pragma("unroll") for (int r = 0; r < RR; ++r)                                   \
+        v[r] = cmul(v[r], ks[VP_CHK(fz_s[VP_CHK(base + r, L, 304)] * 4 + (b >> 2), p.Oz * 4, 305)]); \
+      dft<RR, true>(v);                                                                \
+      _Pragma("unroll") for (int r = 0; r < RR; ++r) tile[tix<16, true>(base + r, b)] = v[r]; \
+    }                                                                                  \
   } break;
     switch (R) {
       VP_CONV_CASE(16)
@@ -159,22 +188,25 @@ __global__ void __launch_bounds__(kThreads) line_sweep_kernel(const LineSweep p)
 #undef VP_CONV_CASE
     __syncthreads();
     for (int q = P - 2; q >= 0; --q) {
-      dit_pass_rt<kLineP>(p.ax.radix[q], tile, L, p.ax.lp[q], p.ax.tw);
+      dit_pass_rt<16, true>(p.ax, q, tile, p.ax.tw);
       __syncthreads();
     }
   }
 
-  const int nstore = kTileB * p.n_out;
-  for (int e = threadIdx.x; e < nstore; e += blockDim.x) {
-    const int b = e / p.n_out;
-    const int z = e - b * p.n_out;
-    const long long l = l0 + b;
-    if (l < p.nlines) p.data[l * p.ld + z] = tile[z * kLineP + b];
+  for (int b = warp; b < kTileB; b += nwarps) {
+    const long long l = line_of[b];
+    if (l < 0) continue;
+    float2* dst = p.data + l * p.ld;
+    VP_CHKL(l * p.ld + p.n_out - 1, p.data_elems, 306);
+    for (int z = lane; z < p.n_out; z += 32) dst[z] = tile[VP_CHK((tix<16, true>(z, b)), L * 16, 307)];
   }
 }
 
 // Grant a sweep kernel the largest tile it can be launched with, once per device.
 // Each instantiation (TAG) keeps its own per-device flag.
+constexpr size_t kColMax = col_smem(kMaxL);
+constexpr size_t kLineMax = line_smem(kMaxL, kMaxL / 2 + 1);
+
 template <int TAG, typename K>
 cudaError_t set_smem(K kernel, size_t bytes, size_t max_bytes) {
   static volatile int granted[64] = {0};
@@ -191,7 +223,7 @@ cudaError_t set_smem(K kernel, size_t bytes, size_t max_bytes) {
 }  // namespace
 
 cudaError_t launch_col_sweep(const ColSweep& p, int dir, bool source_prologue, cudaStream_t s) {
-  const size_t smem = (size_t)p.ax.L * kColP * sizeof(float2);
+  const size_t smem = col_smem(p.ax.L);
   const long long ncb = (p.C + kTileB - 1) / kTileB;
   const long long blocks = ncb * p.n_outer;
   if (blocks <= 0) return cudaSuccess;
@@ -214,8 +246,8 @@ cudaError_t launch_col_sweep(const ColSweep& p, int dir, bool source_prologue, c
 }
 
 cudaError_t launch_line_sweep(const LineSweep& p, int mode, cudaStream_t s) {
-  const size_t smem = (size_t)p.ax.L * kLineP * sizeof(float2);
-  const long long blocks = (p.nlines + kTileB - 1) / kTileB;
+  const size_t smem = line_smem(p.ax.L, mode == kConv ? p.Oz : 0);
+  const long long blocks = mode == kConv ? p.nlines : (p.nlines + kTileB - 1) / kTileB;
   if (blocks <= 0) return cudaSuccess;
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
   cudaError_t e;
@@ -232,3 +264,14 @@ cudaError_t launch_line_sweep(const LineSweep& p, int mode, cudaStream_t s) {
 }
 
 }  // namespace vp
+
+#ifdef VP_DEBUG_CHECKS
+extern "C" VP_API int vp_debug_checks(int* out8, int reset) {
+  if (cudaMemcpyFromSymbol(out8, vp::g_vp_debug, 8 * sizeof(int)) != cudaSuccess) return VP_ERR_CUDA;
+  if (reset) {
+    int z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (cudaMemcpyToSymbol(vp::g_vp_debug, z, sizeof(z)) != cudaSuccess) return VP_ERR_CUDA;
+  }
+  return VP_OK;
+}
+#endif
