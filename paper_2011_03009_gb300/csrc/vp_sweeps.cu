@@ -129,7 +129,9 @@ __global__ void __launch_bounds__(kThreads) line_sweep_kernel(const LineSweep p)
   for (int b = warp; b < kTileB; b += nwarps) {
     const long long l = line_of[b];
     const float2* src = p.data + (l < 0 ? 0 : l * p.ld);
+#ifdef VP_DEBUG_CHECKS
     if (l >= 0) VP_CHKL(l * p.ld + p.n_in - 1, p.data_elems, 301);
+#endif
     for (int z = lane; z < p.n_in; z += 32)
       cp_async8(&tile[VP_CHK((tix<16, true>(z, b)), L * 16, 302)], &src[z], l >= 0);
   }
@@ -197,7 +199,9 @@ __global__ void __launch_bounds__(kThreads) line_sweep_kernel(const LineSweep p)
     const long long l = line_of[b];
     if (l < 0) continue;
     float2* dst = p.data + l * p.ld;
+#ifdef VP_DEBUG_CHECKS
     VP_CHKL(l * p.ld + p.n_out - 1, p.data_elems, 306);
+#endif
     for (int z = lane; z < p.n_out; z += 32) dst[z] = tile[VP_CHK((tix<16, true>(z, b)), L * 16, 307)];
   }
 }
