@@ -185,6 +185,34 @@ VP_API int vp_incident_field(const vp_grid* g, const double* points, int n_point
                              double R, double f0_hz, double p0, const vp_medium* m, void* out,
                              vp_stream_t stream);
 
+/* ---- allocation-free volume potential --------------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers that cannot
+ * call cudaMalloc: code running while a stream is captured into a CUDA graph
+ * (cudaMalloc/cudaFree are not capturable, and cudaFree synchronises the device),
+ * applications whose device memory is owned by another allocator that already holds
+ * it, and latency-bound loops that cannot afford the device-wide synchronisation of
+ * cudaMalloc/cudaFree.
+ *
+ * vp_apply_static computes u = V_{k_n}[f] exactly like vp_plan (default embedding and
+ * radix schedule) + vp_kernel_fft + vp_apply, for grids of at most VP_STATIC_MAX_N
+ * voxels per axis, keeping every intermediate in one fixed-size __device__ array inside
+ * libvp.so (about 18.2 MiB, held by every GPU that loads the library until the process
+ * exits).  It calls no cudaMalloc, cudaFree or other allocating routine.  The caller
+ * passes f and u (device pointers, complex64, N voxels each, not aliased); the
+ * kernel spectrum is rebuilt on every call.
+ * - The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call before any
+ *   stream capture.
+ * - Every call on a device shares the array and rewrites everything it later reads,
+ *   so no state carries over between calls; calls whose GPU work overlaps (other
+ *   streams, other host threads) race on the array and must be serialised.
+ * Errors: VP_ERR_ARG (null pointers, n[i] < 1, h <= 0, harmonic < 1, f0 <= 0, c0 <= 0,
+ * rho0 <= 0, alpha0 < 0), VP_ERR_SIZE (an axis longer than VP_STATIC_MAX_N),
+ * VP_ERR_CUDA. */
+#define VP_STATIC_MAX_N 64
+VP_API int vp_apply_static(const vp_grid* g, int harmonic_n, double f0_hz, const vp_medium* m,
+                           const void* f, void* u, vp_stream_t stream);
+
 /* ---- diagnostics ----------------------------------------------------------------- */
 /* Static, NUL-terminated name of a status code. */
 VP_API const char* vp_status_string(int status);

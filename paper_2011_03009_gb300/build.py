@@ -14,7 +14,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libvp.so")
 
-SOURCES = ["vp_api.cu", "vp_sweeps.cu", "vp_kernels.cu"]
+SOURCES = ["vp_api.cu", "vp_sweeps.cu", "vp_kernels.cu", "vp_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -76,6 +76,7 @@ def _load():
         "vp_profile_enable": (I, [P, I]),
         "vp_profile_read": (I, [P, ctypes.POINTER(D), ctypes.POINTER(I), I]),
         "vp_version": (ctypes.c_char_p, []),
+        "vp_apply_static": (I, [ctypes.POINTER(vp_grid), I, D, ctypes.POINTER(vp_medium), P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -234,6 +235,21 @@ def vp_incident_field(grid, points, bowl, medium, out, stream=None):
     _check(lib.vp_incident_field(ctypes.byref(g), ctypes.c_void_p(points.data_ptr()), int(points.shape[0]),
                                  float(bowl.l), float(bowl.R), float(bowl.f0), float(bowl.p0), ctypes.byref(med),
                                  _ptr(out), _stream(stream)), "vp_incident_field")
+
+
+VP_STATIC_MAX_N = 64
+
+
+def vp_apply_static(grid, harmonic: int, f0: float, medium, f, u, stream=None):
+    """u = V_{k_n}[f] without any device allocation (grids up to 64 voxels per axis).
+
+    For callers that cannot allocate device memory (stream capture, memory owned by
+    another allocator); shares one fixed device array across calls, so calls must
+    not overlap on the GPU."""
+    g = grid if isinstance(grid, vp_grid) else grid_of(grid)
+    med = medium if isinstance(medium, vp_medium) else make_medium(medium)
+    _check(lib.vp_apply_static(ctypes.byref(g), int(harmonic), float(f0), ctypes.byref(med), _ptr(f), _ptr(u),
+                               _stream(stream)), "vp_apply_static")
 
 
 def vp_version() -> str:
