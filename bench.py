@@ -35,8 +35,8 @@ L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="nested3", choices=["small", "nested3", "nested5"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -61,7 +61,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, ValueError):
             self.proc = None
@@ -119,6 +119,11 @@ def max_over_ranks(value: float, world: int) -> float:
     return float(t.item())
 
 
+def aggregate_value(voxels: int, steps: int, world: int, total_ms: float) -> float:
+    """Whole-job throughput: voxels of every rank's steps over the slowest rank's time."""
+    return voxels * steps * world / (total_ms / 1e3)
+
+
 def barrier(world: int):
     if world > 1:
         import torch.distributed as dist
@@ -145,6 +150,20 @@ def sweep_bytes(n, m, harmonic, fused_source: bool):
 
 
 SWEEP_NAMES = ["x_forward_source", "y_forward", "z_conv", "y_inverse", "x_inverse"]
+
+
+def kernel_name(sweep: int, m, engine) -> str:
+    """Name of the CUDA kernel that runs one sweep (two-level or radix-pass engine)."""
+    axis = (0, 1, 2, 1, 0)[sweep]
+    L = m[axis]
+    if engine[axis]:
+        if sweep == 2:
+            return f"line2_conv_pipe_kernel (L={L})"
+        kind = ("forward, source" if sweep == 0 else "forward") if sweep < 2 else "inverse"
+        return f"col2_kernel {kind} (L={L})"
+    if sweep == 2:
+        return f"line_sweep_kernel<conv> (L={L})"
+    return f"col_sweep_kernel (L={L})"
 
 
 class GpuWorkload:
@@ -224,11 +243,12 @@ class GpuWorkload:
         out = {}
         for n, p in self.plans.items():
             inf = p.info()
-            out[n] = (tuple(inf.n), tuple(inf.m))
+            out[n] = (tuple(inf.n), tuple(inf.m), tuple(inf.engine))
         return out
 
 
 def run_ours(args, world, rank, local):
+    import numpy as np  # noqa: F401
     import torch
     from paper_2011_03009_gb300 import synth
 
@@ -265,7 +285,7 @@ def run_ours(args, world, rank, local):
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = max_over_ranks(sum(step_ms), world)
     ms_per_step = total_ms / args.steps
-    value = voxels * args.steps * world / (total_ms / 1e3)
+    value = aggregate_value(voxels, args.steps, world, total_ms)
 
     # per-sweep kernel timing (events on the launching stream, inside the timed region)
     geo = gw.plan_geometry()
@@ -273,14 +293,15 @@ def run_ours(args, world, rank, local):
     for n, p in gw.plans.items():
         p.profile_enable(False)
         ms, cnt = p.profile_read(reset=True)
-        nn, mm = geo[n]
+        nn, mm, eng = geo[n]
         fused = n >= 2
         by = sweep_bytes(nn, mm, n, fused)
         for s in range(5):
             if cnt[s] == 0:
                 continue
             per_launch_ms = ms[s] / cnt[s]
-            sweeps.append({"harmonic": n, "sweep": SWEEP_NAMES[s], "n": list(nn), "m": list(mm),
+            sweeps.append({"harmonic": n, "sweep": SWEEP_NAMES[s], "kernel": kernel_name(s, mm, eng),
+                           "n": list(nn), "m": list(mm),
                            "launches": cnt[s], "ms_per_launch": per_launch_ms, "bytes_per_launch": by[s],
                            "gbs": by[s] / (per_launch_ms * 1e-3) / 1e9, "total_ms": ms[s]})
     peaks = {}
@@ -294,8 +315,7 @@ def run_ours(args, world, rank, local):
     dom = max(sweeps, key=lambda r: r["total_ms"]) if sweeps else None
     roofline = None
     if dom:
-        roofline = {"bound": "hbm", "kernel": f"line_sweep_kernel<conv> harmonic {dom['harmonic']}"
-                    if dom["sweep"] == "z_conv" else f"col_sweep_kernel {dom['sweep']} harmonic {dom['harmonic']}",
+        roofline = {"bound": "hbm", "kernel": f"{dom['kernel']}, harmonic {dom['harmonic']}",
                     "achieved": round(dom["gbs"], 1), "peak": hbm_peak, "peak_source": peak_src,
                     "unit": "GB/s", "frac": round(dom["gbs"] / hbm_peak, 4), "traffic": None,
                     "bytes_per_launch": dom["bytes_per_launch"], "ms_per_launch": round(dom["ms_per_launch"], 5)}
@@ -305,7 +325,7 @@ def run_ours(args, world, rank, local):
         rows = [r for r in sweeps if r["harmonic"] == n]
         t = sum(r["ms_per_launch"] for r in rows)
         by = sum(r["bytes_per_launch"] for r in rows)
-        vox = geo[n][0][0] * geo[n][0][1] * geo[n][0][2]
+        vox = int(np.prod(geo[n][0]))
         per_h[str(n)] = {"voxels": vox, "apply_ms": round(t, 4), "voxels_per_s": vox / (t * 1e-3),
                          "model_gbs": round(by / (t * 1e-3) / 1e9, 1), "hbm_frac": round(by / (t * 1e-3) / 1e9 / hbm_peak, 4)}
 
@@ -327,6 +347,7 @@ def run_ours(args, world, rank, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
         "config": {"workload": w.name, "harmonics": ([1] if w.v1_grid is not None else []) + [s.harmonic for s in w.steps],
                    "grids": {str(n): list(geo[n][0]) for n in geo}, "embedding": {str(n): list(geo[n][1]) for n in geo},
+                   "engine": {str(n): list(geo[n][2]) for n in geo},
                    "voxels_per_step": voxels, "bowl_points": w.n_points, "parallelism": f"replicas x{world}",
                    "l2": "flushed between steps (256 MiB write outside the timed events)",
                    "khat_build_ms": round(gw.khat_build_ms, 2)},

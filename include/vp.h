@@ -94,15 +94,21 @@ typedef struct vp_plan_info {
     double self_re, self_im;      /* self-cell integral S(k_n, h)                        */
     unsigned long long workspace_bytes;  /* device bytes held by the plan               */
     int khat_ready;      /* 1 once vp_kernel_fft has been enqueued                       */
+    int engine[3];       /* per axis: 1 two-level register FFT, 0 shared-memory radix passes */
 } vp_plan_info;
 
 /* ---- plans --------------------------------------------------------------------
  * vp_plan: create a plan for harmonic n (>= 1) on grid g (Section 6 algorithm, step 1:
- * one voxel mesh per harmonic).  Computes k_n and C_n, picks the embedding size M
- * (default: smallest even 2^a 3^b 5^c >= 2N on each axis; Section 3.1 needs
- * M >= 2N - 1, Section 6 uses 2N) and its radix schedule, and allocates the plan's
+ * one voxel mesh per harmonic).  Computes k_n and C_n, picks the embedding size M per
+ * axis (Section 3.1 needs M >= 2N - 1, Section 6 uses 2N) and its FFT engine, and
+ * allocates the plan's
  * device workspace (about 8 * (M_x N_y N_z + M_x M_y N_z) bytes) and the storage of
  * the kernel spectrum (8 * prod(M/2 + 1) bytes) on the current device.
+ * Default M: the smallest length >= 2N - 1 compiled for the two-level register engine
+ * (32, 64, 128, 192, 256, 320, 384, 512, 640, 768, 864, 1024, 1200, 1280) when it is at
+ * most a third longer than the smallest even 2^a 3^b 5^c >= 2N, else that 5-smooth
+ * length with the shared-memory radix-pass engine.  An explicit opts->radix schedule
+ * selects the radix-pass engine for that axis.
  * `opts` may be NULL.  `stream` is used only when opts->autotune is set.
  * Errors: VP_ERR_ARG (null pointers, n[i] < 1, h <= 0, harmonic < 1, c0 <= 0,
  * rho0 <= 0, alpha0 < 0, f0 <= 0), VP_ERR_SIZE (M < 2N - 1, or an axis the FFT

@@ -14,7 +14,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libvp.so")
 
-SOURCES = ["vp_api.cu", "vp_sweeps.cu", "vp_kernels.cu", "vp_static.cu"]
+SOURCES = ["vp_api.cu", "vp_sweeps.cu", "vp_kernels.cu", "vp_static.cu", "vp_sweeps2_part0.cu",
+           "vp_sweeps2_part1.cu", "vp_sweeps2_part2.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

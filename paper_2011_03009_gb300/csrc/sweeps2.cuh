@@ -1,0 +1,377 @@
+// Two-level register FFT sweeps (compile-time line length L = A * B).
+//
+// A line x[n], n = B a + b (a < A, b < B), is transformed in two register steps with one
+// shared-memory transpose between them (four-step decomposition):
+//   step 1  thread (line, b):  Y_b[k1] = DFT_A over a of x[B a + b], times w_L^(b k1)
+//   step 2  thread (line, k1): X[k1 + A k2] = DFT_B over b of Y_b[k1]
+// The output is in natural frequency order.  The inverse runs the same two steps in
+// reverse with conjugate twiddles (x L, the 1/(M_x M_y M_z) scale is applied by the
+// last sweep).  Global memory is read and written directly from registers:
+// - column sweeps (strided axis) map the 16 lines of a tile to the 16 lanes of a
+//   half-warp, so every access is one 128-byte row segment;
+// - line sweeps (contiguous axis) map b (or k1) to the lanes, so a warp reads and
+//   writes consecutive elements of one line.
+// The transpose buffer pads each line to an odd pitch so that the 16 lanes of a
+// half-warp never share a bank.
+#pragma once
+
+#include "regfft.cuh"
+
+namespace vp {
+
+constexpr int kLines2 = 16;    // lines per CTA
+constexpr int kThreads2 = 256;
+
+__host__ __device__ constexpr int col2_pitch(int L) { return L + 1; }
+// Resident CTAs per SM the column kernels are compiled for: three while three tiles fit
+// in shared memory (the register cap then is 85 per thread), else one.
+__host__ __device__ constexpr int col2_min_blocks(int L) { return L <= 512 ? 3 : 1; }
+__host__ __device__ constexpr int line2_bpitch(int B) { return B + 1; }
+__host__ __device__ constexpr int line2_pitch(int A, int B) { return A * (B + 1) + 1; }
+
+template <int A, int B, int DIR, bool SRC>
+__global__ void __launch_bounds__(kThreads2, col2_min_blocks(A * B)) col2_kernel(const ColSweep p) {
+  constexpr int L = A * B;
+  constexpr int LP = col2_pitch(L);
+  extern __shared__ float2 S[];
+  const int ncb = (p.C + kLines2 - 1) / kLines2;
+  const int o = blockIdx.x / ncb;
+  const int c0 = (blockIdx.x - o * ncb) * kLines2;
+  const float2* __restrict__ tw = p.ax.tw;
+  const float2 zero = make_float2(0.f, 0.f);
+
+  if constexpr (DIR == kForward) {
+    for (int tau = threadIdx.x; tau < kLines2 * B; tau += blockDim.x) {
+      const int line = tau & (kLines2 - 1);
+      const int b = tau >> 4;
+      const int c = c0 + line;
+      const bool colok = c < p.C;
+      const long long base = (long long)o * p.in_os + c;
+      float2 v[A];
+      if constexpr (SRC) {
+        // f_n = C_n sum_{m=1}^{n-1} p_m p_{n-m} (Eq. 2.6), summed over pairs m <= n - m
+#pragma unroll
+        for (int a = 0; a < A; ++a) v[a] = zero;
+        const int n = p.harmonic;
+        for (int m = 1; 2 * m <= n; ++m) {
+          const float2* __restrict__ pa = p.lower[m - 1];
+          const float2* __restrict__ pb = p.lower[n - m - 1];
+          const float w = ((2 * m == n) ? 1.f : 2.f) * p.cn;
+#pragma unroll
+          for (int a = 0; a < A; ++a) {
+            const int row = B * a + b;
+            if (colok && row < p.rows_in) {
+              const long long off = base + (long long)row * p.in_rs;
+              const float2 x = __ldg(&pa[off]), y = __ldg(&pb[off]);
+              const float2 xy = cmul(x, y);
+              v[a].x = fmaf(w, xy.x, v[a].x);
+              v[a].y = fmaf(w, xy.y, v[a].y);
+            }
+          }
+        }
+      } else {
+#pragma unroll
+        for (int a = 0; a < A; ++a) {
+          const int row = B * a + b;
+          v[a] = (colok && row < p.rows_in) ? __ldg(&p.in[base + (long long)row * p.in_rs]) : zero;
+        }
+      }
+      dft_reg<A, false>(v);
+      float2* s = S + line * LP + b;
+      s[0] = v[0];
+#pragma unroll
+      for (int k1 = 1; k1 < A; ++k1) s[k1 * B] = cmul(v[k1], __ldg(&tw[b * k1]));
+    }
+    __syncthreads();
+    for (int tau = threadIdx.x; tau < kLines2 * A; tau += blockDim.x) {
+      const int line = tau & (kLines2 - 1);
+      const int k1 = tau >> 4;
+      float2 z[B];
+      const float2* s = S + line * LP + k1 * B;
+#pragma unroll
+      for (int b = 0; b < B; ++b) z[b] = s[b];
+      dft_reg<B, false>(z);
+      const int c = c0 + line;
+      if (c < p.C) {
+        const long long base = (long long)o * p.out_os + c;
+#pragma unroll
+        for (int k2 = 0; k2 < B; ++k2) {
+          const int row = k1 + A * k2;
+          if (row < p.rows_out) p.out[base + (long long)row * p.out_rs] = z[k2];
+        }
+      }
+    }
+  } else {
+    for (int tau = threadIdx.x; tau < kLines2 * A; tau += blockDim.x) {
+      const int line = tau & (kLines2 - 1);
+      const int k1 = tau >> 4;
+      const int c = c0 + line;
+      const bool colok = c < p.C;
+      const long long base = (long long)o * p.in_os + c;
+      float2 z[B];
+#pragma unroll
+      for (int k2 = 0; k2 < B; ++k2)
+        z[k2] = colok ? __ldg(&p.in[base + (long long)(k1 + A * k2) * p.in_rs]) : zero;
+      dft_reg<B, true>(z);
+      float2* s = S + line * LP + k1 * B;
+      s[0] = z[0];
+#pragma unroll
+      for (int b = 1; b < B; ++b) s[b] = cmulc(z[b], __ldg(&tw[b * k1]));
+    }
+    __syncthreads();
+    for (int tau = threadIdx.x; tau < kLines2 * B; tau += blockDim.x) {
+      const int line = tau & (kLines2 - 1);
+      const int b = tau >> 4;
+      float2 v[A];
+      const float2* s = S + line * LP + b;
+#pragma unroll
+      for (int k1 = 0; k1 < A; ++k1) v[k1] = s[k1 * B];
+      dft_reg<A, true>(v);
+      const int c = c0 + line;
+      if (c < p.C) {
+        const long long base = (long long)o * p.out_os + c;
+#pragma unroll
+        for (int a = 0; a < A; ++a) {
+          const int row = B * a + b;
+          if (row < p.rows_out) p.out[base + (long long)row * p.out_rs] = cscale(v[a], p.scale);
+        }
+      }
+    }
+  }
+}
+
+template <int A, int B, int MODE>
+__global__ void __launch_bounds__(kThreads2) line2_kernel(const LineSweep p) {
+  constexpr int L = A * B;
+  constexpr int BP = line2_bpitch(B);
+  constexpr int LP = line2_pitch(A, B);
+  extern __shared__ float2 S[];
+  __shared__ long long line_of[kLines2];
+  __shared__ int oct_of[4];
+  const float2* __restrict__ tw = p.ax.tw;
+  const float2 zero = make_float2(0.f, 0.f);
+
+  if (threadIdx.x < kLines2) {
+    long long l;
+    if (MODE == kConv) {
+      l = p.tiles[20LL * blockIdx.x + threadIdx.x];
+    } else {
+      l = (long long)blockIdx.x * kLines2 + threadIdx.x;
+      if (l >= p.nlines) l = -1;
+    }
+    line_of[threadIdx.x] = l;
+  }
+  if (MODE == kConv && threadIdx.x < 4) oct_of[threadIdx.x] = p.tiles[20LL * blockIdx.x + 16 + threadIdx.x];
+  __syncthreads();
+
+  // forward step 1: task (line, b), b fastest across lanes (coalesced along the line)
+  for (int tau = threadIdx.x; tau < kLines2 * B; tau += blockDim.x) {
+    const int line = tau / B;
+    const int b = tau - line * B;
+    const long long l = line_of[line];
+    const float2* src = p.data + (l < 0 ? 0 : l * p.ld);
+    float2 v[A];
+#pragma unroll
+    for (int a = 0; a < A; ++a) {
+      const int n = B * a + b;
+      v[a] = (l >= 0 && n < p.n_in) ? __ldg(&src[n]) : zero;
+    }
+    dft_reg<A, false>(v);
+    float2* s = S + line * LP + b;
+    s[0] = v[0];
+#pragma unroll
+    for (int k1 = 1; k1 < A; ++k1) s[k1 * BP] = cmul(v[k1], __ldg(&tw[b * k1]));
+  }
+  __syncthreads();
+
+  // forward step 2 (+ spectrum multiply and inverse step 2): task (line, k1)
+  for (int tau = threadIdx.x; tau < kLines2 * A; tau += blockDim.x) {
+    const int line = tau / A;
+    const int k1 = tau - line * A;
+    float2 z[B];
+    float2* s = S + line * LP + k1 * BP;
+#pragma unroll
+    for (int b = 0; b < B; ++b) z[b] = s[b];
+    dft_reg<B, false>(z);
+    if constexpr (MODE == kConv) {
+      const int oc = oct_of[line >> 2];
+      if (oc >= 0) {
+        const float2* __restrict__ kl = p.khat + (long long)oc * p.Oz;
+#pragma unroll
+        for (int k2 = 0; k2 < B; ++k2) {
+          const int f = k1 + A * k2;
+          z[k2] = cmul(z[k2], __ldg(&kl[min(f, L - f)]));
+        }
+      }
+      dft_reg<B, true>(z);
+      s[0] = z[0];
+#pragma unroll
+      for (int b = 1; b < B; ++b) s[b] = cmulc(z[b], __ldg(&tw[b * k1]));
+    } else {
+      const long long l = line_of[line];
+      if (l >= 0) {
+        float2* dst = p.data + l * p.ld;
+#pragma unroll
+        for (int k2 = 0; k2 < B; ++k2) {
+          const int f = k1 + A * k2;
+          if (f < p.n_out) dst[f] = z[k2];
+        }
+      }
+    }
+  }
+
+  if constexpr (MODE == kConv) {
+    __syncthreads();
+    // inverse step 1: task (line, b)
+    for (int tau = threadIdx.x; tau < kLines2 * B; tau += blockDim.x) {
+      const int line = tau / B;
+      const int b = tau - line * B;
+      float2 v[A];
+      const float2* s = S + line * LP + b;
+#pragma unroll
+      for (int k1 = 0; k1 < A; ++k1) v[k1] = s[k1 * BP];
+      dft_reg<A, true>(v);
+      const long long l = line_of[line];
+      if (l >= 0) {
+        float2* dst = p.data + l * p.ld;
+#pragma unroll
+        for (int a = 0; a < A; ++a) {
+          const int n = B * a + b;
+          if (n < p.n_out) dst[n] = v[a];
+        }
+      }
+    }
+  }
+}
+
+// Persistent, software-pipelined form of line2_kernel<kConv>: each CTA walks the tiles
+// blockIdx.x, blockIdx.x + gridDim.x, ...  The 16 input lines of the next tile are
+// copied into a staging buffer with cp.async while the current tile runs its forward
+// step 2, spectrum multiply and inverse step 2; the next tile's four octant lines of
+// the spectrum are copied while the current tile runs its inverse step 1.  The
+// twiddle table is staged once.  The compute phases then touch only registers and
+// shared memory.
+// Shared memory: transpose buffer (16 x line2_pitch), staging buffer (16 x ni),
+// spectrum lines (4 x Oz), twiddles (L).
+__host__ __device__ constexpr int conv_stage_pitch(int n_in) { return n_in | 1; }  // odd: lanes = lines
+__host__ __device__ constexpr size_t conv_pipe_smem(int A, int B, int n_in, int Oz) {
+  return ((size_t)kLines2 * line2_pitch(A, B) + (size_t)kLines2 * conv_stage_pitch(n_in) + (size_t)4 * Oz +
+          (size_t)A * B) *
+         sizeof(float2);
+}
+
+template <int A, int B>
+__global__ void __launch_bounds__(kThreads2) line2_conv_pipe_kernel(const LineSweep p) {
+  constexpr int L = A * B;
+  constexpr int BP = line2_bpitch(B);
+  constexpr int LP = line2_pitch(A, B);
+  extern __shared__ float2 S[];
+  const int NI = conv_stage_pitch(p.n_in);
+  float2* I = S + kLines2 * LP;
+  float2* K = I + kLines2 * NI;  // [4][Oz]
+  float2* T = K + 4 * p.Oz;      // twiddles
+  __shared__ long long line_of[2][kLines2];
+  __shared__ int oct_of[2][4];
+  const float2 zero = make_float2(0.f, 0.f);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long ntiles = p.nlines;
+
+  auto fetch_lines = [&](long long t, int slot) {
+    for (int b = warp; b < kLines2; b += kThreads2 / 32) {
+      const long long l = p.tiles[20LL * t + b];
+      const float2* src = p.data + (l < 0 ? 0 : l * p.ld);
+      for (int n = lane; n < p.n_in; n += 32) cp_async8(&I[b * NI + n], &src[n], l >= 0);
+    }
+    if (threadIdx.x < kLines2) line_of[slot][threadIdx.x] = p.tiles[20LL * t + threadIdx.x];
+    if (threadIdx.x < 4) oct_of[slot][threadIdx.x] = p.tiles[20LL * t + 16 + threadIdx.x];
+  };
+  auto fetch_spectrum = [&](long long t) {
+    const int g = warp & 3;
+    const int oc = p.tiles[20LL * t + 16 + g];
+    const float2* kl = p.khat + (oc < 0 ? 0 : (long long)oc * p.Oz);
+    for (int i = (warp >> 2) * 32 + lane; i < p.Oz; i += (kThreads2 / 128) * 32)
+      cp_async8(&K[g * p.Oz + i], &kl[i], oc >= 0);
+  };
+
+  for (int i = threadIdx.x; i < L; i += blockDim.x) cp_async8(&T[i], &p.ax.tw[i], true);
+  long long t = blockIdx.x;
+  if (t < ntiles) {
+    fetch_lines(t, 0);
+    fetch_spectrum(t);
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  for (int it = 0; t < ntiles; t += gridDim.x, ++it) {
+    const int cur = it & 1;
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    __syncthreads();
+    // forward step 1 from the staging buffer; the 16 lanes of a half-warp hold the 16
+    // lines (odd staging pitch), so every twiddle read is a broadcast
+    for (int tau = threadIdx.x; tau < kLines2 * B; tau += blockDim.x) {
+      const int line = tau & (kLines2 - 1);
+      const int b = tau >> 4;
+      const float2* src = I + line * NI;
+      float2 v[A];
+#pragma unroll
+      for (int a = 0; a < A; ++a) {
+        const int n = B * a + b;
+        v[a] = n < p.n_in ? src[n] : zero;
+      }
+      dft_reg<A, false>(v);
+      float2* s = S + line * LP + b;
+      s[0] = v[0];
+#pragma unroll
+      for (int k1 = 1; k1 < A; ++k1) s[k1 * BP] = cmul(v[k1], T[b * k1]);
+    }
+    __syncthreads();
+    const long long tn = t + gridDim.x;
+    if (tn < ntiles) fetch_lines(tn, cur ^ 1);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    // forward step 2, spectrum multiply, inverse step 2 (lanes = lines again)
+    for (int tau = threadIdx.x; tau < kLines2 * A; tau += blockDim.x) {
+      const int line = tau & (kLines2 - 1);
+      const int k1 = tau >> 4;
+      float2 z[B];
+      float2* s = S + line * LP + k1 * BP;
+#pragma unroll
+      for (int b = 0; b < B; ++b) z[b] = s[b];
+      dft_reg<B, false>(z);
+      if (oct_of[cur][line >> 2] >= 0) {
+        const float2* kl = K + (line >> 2) * p.Oz;
+#pragma unroll
+        for (int k2 = 0; k2 < B; ++k2) {
+          const int f = k1 + A * k2;
+          z[k2] = cmul(z[k2], kl[min(f, L - f)]);
+        }
+      }
+      dft_reg<B, true>(z);
+      s[0] = z[0];
+#pragma unroll
+      for (int b = 1; b < B; ++b) s[b] = cmulc(z[b], T[b * k1]);
+    }
+    __syncthreads();
+    if (tn < ntiles) fetch_spectrum(tn);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    // inverse step 1 and store
+    for (int tau = threadIdx.x; tau < kLines2 * B; tau += blockDim.x) {
+      const int line = tau / B;
+      const int b = tau - line * B;
+      float2 v[A];
+      const float2* s = S + line * LP + b;
+#pragma unroll
+      for (int k1 = 0; k1 < A; ++k1) v[k1] = s[k1 * BP];
+      dft_reg<A, true>(v);
+      const long long l = line_of[cur][line];
+      if (l >= 0) {
+        float2* dst = p.data + l * p.ld;
+#pragma unroll
+        for (int a = 0; a < A; ++a) {
+          const int n = B * a + b;
+          if (n < p.n_out) dst[n] = v[a];
+        }
+      }
+    }
+  }
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+}  // namespace vp

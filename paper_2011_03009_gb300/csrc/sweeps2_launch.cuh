@@ -1,0 +1,110 @@
+// Launchers of the two-level sweep kernels for the sizes of one part of kFastSizes.
+// Included by vp_sweeps2_part{0,1,2}.cu with VP_PART defined.
+#pragma once
+
+#include "sweeps2.cuh"
+
+namespace vp {
+namespace {
+
+template <typename K>
+cudaError_t grant_smem(K kernel, size_t bytes, volatile int* granted) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (bytes <= 48 * 1024 || granted[dev]) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) granted[dev] = 1;
+  return e;
+}
+
+template <int A, int B, int DIR, bool SRC>
+cudaError_t col2_launch(const ColSweep& p, cudaStream_t s) {
+  static volatile int granted[64] = {0};
+  const size_t smem = (size_t)kLines2 * col2_pitch(A * B) * sizeof(float2);
+  const long long ncb = (p.C + kLines2 - 1) / kLines2;
+  const long long blocks = ncb * p.n_outer;
+  if (blocks <= 0) return cudaSuccess;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  auto k = col2_kernel<A, B, DIR, SRC>;
+  cudaError_t e = grant_smem(k, smem, granted);
+  if (e != cudaSuccess) return e;
+  k<<<(unsigned)blocks, kThreads2, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+template <int A, int B, int MODE>
+cudaError_t line2_launch(const LineSweep& p, cudaStream_t s) {
+  static volatile int granted[64] = {0};
+  const size_t smem = (size_t)kLines2 * line2_pitch(A, B) * sizeof(float2);
+  const long long blocks = MODE == kConv ? p.nlines : (p.nlines + kLines2 - 1) / kLines2;
+  if (blocks <= 0) return cudaSuccess;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  auto k = line2_kernel<A, B, MODE>;
+  cudaError_t e = grant_smem(k, smem, granted);
+  if (e != cudaSuccess) return e;
+  k<<<(unsigned)blocks, kThreads2, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+template <int A, int B>
+cudaError_t col2_dispatch(const ColSweep& p, int dir, bool src, cudaStream_t s) {
+  if (dir == kForward && src) return col2_launch<A, B, kForward, true>(p, s);
+  if (dir == kForward) return col2_launch<A, B, kForward, false>(p, s);
+  return col2_launch<A, B, kInverse, false>(p, s);
+}
+
+// Persistent pipelined convolution sweep: one CTA per resident slot, tiles strided.
+template <int A, int B>
+cudaError_t line2_conv_pipe_launch(const LineSweep& p, cudaStream_t s, bool* used) {
+  static volatile int granted[64] = {0};
+  static int slots[64] = {0};
+  *used = false;
+  const size_t smem = conv_pipe_smem(A, B, p.n_in, p.Oz);
+  if (smem > 200 * 1024) return cudaSuccess;  // too large to pipeline: caller falls back
+  if (p.nlines <= 0) {
+    *used = true;
+    return cudaSuccess;
+  }
+  auto k = line2_conv_pipe_kernel<A, B>;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!granted[dev]) {
+    // the staging buffer depends on n_in: grant the largest pipelined size once
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    granted[dev] = 1;
+  }
+  int per_sm = 0, sms = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads2, smem);
+  if (e != cudaSuccess) return e;
+  if (!slots[dev]) {
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    slots[dev] = sms;
+  }
+  sms = slots[dev];
+  if (per_sm < 1) return cudaSuccess;
+  long long grid = (long long)per_sm * sms;
+  if (grid > p.nlines) grid = p.nlines;
+  k<<<(unsigned)grid, kThreads2, smem, s>>>(p);
+  *used = true;
+  return cudaGetLastError();
+}
+
+template <int A, int B>
+cudaError_t line2_dispatch(const LineSweep& p, int mode, cudaStream_t s) {
+  if (mode == kConv) {
+    bool used = false;
+    cudaError_t e = line2_conv_pipe_launch<A, B>(p, s, &used);
+    if (e != cudaSuccess || used) return e;
+    return line2_launch<A, B, kConv>(p, s);
+  }
+  return line2_launch<A, B, kForwardOnly>(p, s);
+}
+
+}  // namespace
+}  // namespace vp

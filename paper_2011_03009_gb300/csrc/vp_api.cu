@@ -42,6 +42,7 @@ struct vp_plan_s {
   int oct[3] = {0, 0, 0};
   int radix[3][vp::kMaxPass] = {};
   int npass[3] = {0, 0, 0};
+  int fast[3] = {0, 0, 0};  // axis handled by the two-level register engine
   float2* tw[3] = {nullptr, nullptr, nullptr};
   int* pos[3] = {nullptr, nullptr, nullptr};   // frequency -> position after the DIF passes
   int* fold[3] = {nullptr, nullptr, nullptr};  // position -> min(f, M - f)
@@ -97,10 +98,30 @@ bool smooth5(int v) {
   return v == 1;
 }
 
-int default_m(int n) {
+int smooth_m(int n) {
   int m = 2 * n;
   while (!smooth5(m)) m += 2;
   return m;
+}
+
+bool fast_size(int L) {
+  for (int i = 0; i < vp::kNumFastSizes; ++i)
+    if (vp::kFastSizes[i].L == L) return true;
+  return false;
+}
+
+// Default embedding: the smallest length >= 2N - 1 of the two-level engine when it is
+// at most a third longer than the smallest even 5-smooth length >= 2N (fewer
+// instructions per element outweigh the extra padding), else that 5-smooth length.
+int default_m(int n) {
+  const int sm = smooth_m(n);
+  int best = 0;
+  for (int i = 0; i < vp::kNumFastSizes; ++i) {
+    const int L = vp::kFastSizes[i].L;
+    if (L >= 2 * n - 1 && (best == 0 || L < best)) best = L;
+  }
+  if (best != 0 && 3 * best <= 4 * sm) return best;
+  return sm;
 }
 
 // Default radix schedule: as few passes as possible, radix <= 16, power-of-two bits
@@ -170,11 +191,15 @@ int build_axis_tables(vp_plan_s* p, int a, std::vector<int>* pos_out) {
   }
   std::vector<int> pos(L), fold(L);
   for (int pp = 0; pp < L; ++pp) {
-    int f = 0, mul = 1;
-    for (int i = 0; i < np; ++i) {
-      const int q = (pp / stride[i]) % p->radix[a][i];
-      f += q * mul;
-      mul *= p->radix[a][i];
+    int f = pp;  // the two-level engine keeps natural order
+    if (!p->fast[a]) {
+      f = 0;
+      int mul = 1;
+      for (int i = 0; i < np; ++i) {
+        const int q = (pp / stride[i]) % p->radix[a][i];
+        f += q * mul;
+        mul *= p->radix[a][i];
+      }
     }
     pos[f] = pp;
     fold[pp] = std::min(f, L - f);
@@ -218,6 +243,7 @@ int build_z_tiles(vp_plan_s* p, const std::vector<int>& pos_x, const std::vector
 AxisDesc axis_desc(const vp_plan_s* p, int a) {
   AxisDesc d{};
   d.L = p->m[a];
+  d.fast = p->fast[a];
   d.npass = p->npass[a];
   int lp = d.L;
   for (int i = 0; i < vp::kMaxPass; ++i) {
@@ -300,7 +326,7 @@ int run_sweep(vp_plan_s* p, int which, const float2* f, const float2* const* low
         c.cn = (float)p->cn;
         for (int i = 0; i < p->harmonic - 1; ++i) c.lower[i] = lower[i];
       }
-      e = vp::launch_col_sweep(c, vp::kForward, lower != nullptr, s);
+      e = vp::launch_col_any(c, vp::kForward, lower != nullptr, s);
     } else {
       c.in = p->wsA;
       c.in_rs = (long long)Ny * Nz;
@@ -313,7 +339,7 @@ int run_sweep(vp_plan_s* p, int which, const float2* f, const float2* const* low
       c.in_elems = (long long)Mx * Ny * Nz;
       c.out_elems = (long long)Nx * Ny * Nz;
       c.scale = (float)(1.0 / ((double)p->m[0] * p->m[1] * p->m[2]));
-      e = vp::launch_col_sweep(c, vp::kInverse, false, s);
+      e = vp::launch_col_any(c, vp::kInverse, false, s);
     }
   } else if (which == 1 || which == 3) {
     ColSweep c{};
@@ -332,7 +358,7 @@ int run_sweep(vp_plan_s* p, int which, const float2* f, const float2* const* low
       c.rows_out = My;
       c.in_elems = (long long)Mx * Ny * Nz;
       c.out_elems = (long long)Mx * My * Nz;
-      e = vp::launch_col_sweep(c, vp::kForward, false, s);
+      e = vp::launch_col_any(c, vp::kForward, false, s);
     } else {
       c.in = p->wsB;
       c.in_rs = Nz;
@@ -344,7 +370,7 @@ int run_sweep(vp_plan_s* p, int which, const float2* f, const float2* const* low
       c.rows_out = Ny;
       c.in_elems = (long long)Mx * My * Nz;
       c.out_elems = (long long)Mx * Ny * Nz;
-      e = vp::launch_col_sweep(c, vp::kInverse, false, s);
+      e = vp::launch_col_any(c, vp::kInverse, false, s);
     }
   } else {
     LineSweep l{};
@@ -359,7 +385,7 @@ int run_sweep(vp_plan_s* p, int which, const float2* f, const float2* const* low
     l.Oz = p->oct[2];
     l.tiles = p->ztiles;
     l.fold_z = p->fold[2];
-    e = vp::launch_line_sweep(l, vp::kConv, s);
+    e = vp::launch_line_any(l, vp::kConv, s);
   }
   if (e != cudaSuccess) return cuda_status(e);
   return prof_end(rec, s);
@@ -395,12 +421,13 @@ VP_API int vp_plan(const vp_grid* g, int harmonic_n, double f0_hz, const vp_medi
     return VP_ERR_ARG;
   if (harmonic_n - 1 > vp::kMaxLower) return VP_ERR_UNSUPPORTED;
   // sizes and schedules are validated before any device work
-  int m[3], radix[3][vp::kMaxPass], npass[3];
+  int m[3], radix[3][vp::kMaxPass], npass[3], fast[3];
   for (int a = 0; a < 3; ++a) {
     const int N = g->n[a];
     if (N > vp::kMaxL) return VP_ERR_SIZE;
     m[a] = (opts && opts->m[a] > 0) ? opts->m[a] : default_m(N);
     if (m[a] < 2 * N - 1 || m[a] > vp::kMaxL) return VP_ERR_SIZE;
+    fast[a] = 0;
     if (opts && opts->radix[a][0] != 0) {
       int prod = 1, np = 0;
       for (int i = 0; i < vp::kMaxPass && opts->radix[a][i] != 0; ++i) {
@@ -414,6 +441,7 @@ VP_API int vp_plan(const vp_grid* g, int harmonic_n, double f0_hz, const vp_medi
     } else {
       npass[a] = default_schedule(m[a], radix[a]);
       if (npass[a] == 0) return VP_ERR_SIZE;
+      fast[a] = fast_size(m[a]) ? 1 : 0;
     }
   }
   vp_plan_s* p = new (std::nothrow) vp_plan_s();
@@ -429,6 +457,7 @@ VP_API int vp_plan(const vp_grid* g, int harmonic_n, double f0_hz, const vp_medi
     p->m[a] = m[a];
     p->oct[a] = m[a] / 2 + 1;
     p->npass[a] = npass[a];
+    p->fast[a] = fast[a];
     for (int i = 0; i < vp::kMaxPass; ++i) p->radix[a][i] = radix[a][i];
   }
   p->h = g->h;
@@ -489,6 +518,7 @@ VP_API int vp_plan_get_info(vp_plan_t p, vp_plan_info* info) {
   info->self_im = p->self_im;
   info->workspace_bytes = p->bytes;
   info->khat_ready = p->khat_ready ? 1 : 0;
+  for (int a = 0; a < 3; ++a) info->engine[a] = p->fast[a];
   return VP_OK;
 }
 
@@ -514,7 +544,7 @@ VP_API int vp_kernel_fft(vp_plan_t p, vp_stream_t stream) {
     c.rows_out = Mx;
     c.in_elems = c.out_elems = (long long)total;
     c.scale = 1.0f;
-    e = vp::launch_col_sweep(c, vp::kForward, false, s);
+    e = vp::launch_col_any(c, vp::kForward, false, s);
   }
   if (e == cudaSuccess) {
     ColSweep c{};  // y, in place
@@ -529,7 +559,7 @@ VP_API int vp_kernel_fft(vp_plan_t p, vp_stream_t stream) {
     c.rows_out = My;
     c.in_elems = c.out_elems = (long long)total;
     c.scale = 1.0f;
-    e = vp::launch_col_sweep(c, vp::kForward, false, s);
+    e = vp::launch_col_any(c, vp::kForward, false, s);
   }
   if (e == cudaSuccess) {
     LineSweep l{};
@@ -540,7 +570,7 @@ VP_API int vp_kernel_fft(vp_plan_t p, vp_stream_t stream) {
     l.n_in = Mz;
     l.n_out = Mz;
     l.data_elems = (long long)total;
-    e = vp::launch_line_sweep(l, vp::kForwardOnly, s);
+    e = vp::launch_line_any(l, vp::kForwardOnly, s);
   }
   if (e == cudaSuccess) e = vp::launch_octant_extract(tmp, p->khat, p->m, p->oct, p->pos[0], p->pos[1], p->pos[2], s);
   cudaError_t e2 = cudaFreeAsync(tmp, s);
@@ -610,6 +640,9 @@ VP_API int vp_restrict_to_nested_box(const vp_grid* src, const void* src_field, 
   for (int ax = 0; ax < 3; ++ax) {
     a[ax] = (dst->origin[ax] - src->origin[ax]) / src->h;
     b[ax] = dst->h / src->h;
+    // positions are carried in 64-bit fixed point with 40 fractional bits
+    if (std::fabs(a[ax]) + std::fabs(b[ax]) * (double)dst->n[ax] > 4.0e6) return VP_ERR_ARG;
+    if (dst->n[0] > 65535 || dst->n[1] > 65535) return VP_ERR_UNSUPPORTED;
     const double t0 = a[ax];
     const double t1 = std::fma((double)(dst->n[ax] - 1), b[ax], a[ax]);
     const double lo = std::min(t0, t1), hi = std::max(t0, t1);

@@ -14,9 +14,22 @@ constexpr int kTileB = 16;       // lines per CTA tile in every FFT sweep
 constexpr int kThreads = 256;    // threads per CTA of the FFT sweeps
 constexpr int kMaxL = 1536;      // longest FFT line the shared-memory tile holds
 
+// Line lengths with a compile-time two-level register engine (L = A * B, see
+// sweeps2.cuh), split into three groups compiled as separate translation units.
+struct FastSize {
+  int L, A, B, part;
+};
+constexpr FastSize kFastSizes[] = {
+    {32, 4, 8, 0},     {64, 8, 8, 0},     {128, 8, 16, 0},   {192, 12, 16, 0},  {256, 16, 16, 0},
+    {320, 16, 20, 1},  {384, 16, 24, 1},  {512, 16, 32, 1},  {640, 20, 32, 1},  {768, 24, 32, 2},
+    {864, 27, 32, 2},  {1024, 32, 32, 2}, {1200, 30, 40, 2}, {1280, 32, 40, 2},
+};
+constexpr int kNumFastSizes = sizeof(kFastSizes) / sizeof(kFastSizes[0]);
+
 // One FFT axis: its length, radix schedule and twiddle table.
 struct AxisDesc {
   int L;
+  int fast;  // 1: two-level register engine (natural order), 0: shared-memory radix passes
   int npass;
   int radix[kMaxPass];
   int lp[kMaxPass];        // sub-transform length entering pass p (L, L/R0, L/(R0 R1), ...)
@@ -69,6 +82,16 @@ enum LineMode { kConv = 0, kForwardOnly = 1 };
 // Launchers (vp_sweeps.cu).  Return a cudaError_t.
 cudaError_t launch_col_sweep(const ColSweep& p, int dir, bool source_prologue, cudaStream_t s);
 cudaError_t launch_line_sweep(const LineSweep& p, int mode, cudaStream_t s);
+// Two-level engine (vp_sweeps2_part*.cu); cudaErrorNotSupported if L is not in the part.
+cudaError_t launch_col2_part0(const ColSweep& p, int dir, bool src, cudaStream_t s);
+cudaError_t launch_col2_part1(const ColSweep& p, int dir, bool src, cudaStream_t s);
+cudaError_t launch_col2_part2(const ColSweep& p, int dir, bool src, cudaStream_t s);
+cudaError_t launch_line2_part0(const LineSweep& p, int mode, cudaStream_t s);
+cudaError_t launch_line2_part1(const LineSweep& p, int mode, cudaStream_t s);
+cudaError_t launch_line2_part2(const LineSweep& p, int mode, cudaStream_t s);
+// Dispatch on p.ax.fast: two-level engine or shared-memory radix passes.
+cudaError_t launch_col_any(const ColSweep& p, int dir, bool src, cudaStream_t s);
+cudaError_t launch_line_any(const LineSweep& p, int mode, cudaStream_t s);
 
 // Other kernels (vp_kernels.cu).
 cudaError_t launch_kernel_lattice(float2* out, const int n[3], const int m[3], double h,

@@ -120,68 +120,69 @@ __global__ void source_kernel(LowerPtrs lo, int harmonic, float cn, float2* __re
   }
 }
 
-struct AxisMap { double a, b; int n; };
+// Target position along one axis in source-voxel units, t = a + i b, held in 64-bit
+// fixed point with kFixBits fractional bits: T = A + i B exactly, with A and B the
+// host-rounded a 2^kFixBits and b 2^kFixBits (error below 2^-kFixBits per unit of i).
+constexpr int kFixBits = 40;
 
-__device__ __forceinline__ bool axis_weights(const AxisMap& m, int i, int& i0, float& w) {
-  const double t = fma((double)i, m.b, m.a);
-  const double tol = 1e-9;
-  const bool inside = t >= -tol && t <= (double)(m.n - 1) + tol;
+struct AxisFix { long long A, B; int n; };
+
+__device__ __forceinline__ bool axis_weights(const AxisFix& m, int i, int& i0, float& w) {
+  const long long T = m.A + (long long)i * m.B;
+  const long long tol = 1100;  // 1e-9 voxel in fixed point
+  const bool inside = T >= -tol && T <= ((long long)(m.n - 1) << kFixBits) + tol;
   if (m.n == 1) {
     i0 = 0;
     w = 0.f;
     return inside;
   }
-  double fl = floor(t);
-  if (fl < 0.0) fl = 0.0;
-  if (fl > (double)(m.n - 2)) fl = (double)(m.n - 2);
+  long long fl = T >> kFixBits;  // floor (arithmetic shift)
+  if (fl < 0) fl = 0;
+  if (fl > m.n - 2) fl = m.n - 2;
   i0 = (int)fl;
-  double wd = t - fl;
-  if (wd < 0.0) wd = 0.0;
-  if (wd > 1.0) wd = 1.0;
-  w = (float)wd;
+  float wf = (float)(T - (fl << kFixBits)) * (1.0f / (float)(1LL << kFixBits));
+  w = fminf(fmaxf(wf, 0.f), 1.f);
   return inside;
 }
 
-__global__ void restrict_kernel(const float2* __restrict__ src, int snx, int sny, int snz,
-                                float2* __restrict__ dst, int dnx, int dny, int dnz, AxisMap mx,
-                                AxisMap my, AxisMap mz, int zero_outside) {
-  const long long total = (long long)dnx * dny * dnz;
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int iz = (int)(idx % dnz);
-    const long long r1 = idx / dnz;
-    const int iy = (int)(r1 % dny);
-    const int ix = (int)(r1 / dny);
-    int x0, y0, z0;
-    float wx, wy, wz;
-    bool in = axis_weights(mx, ix, x0, wx);
-    in &= axis_weights(my, iy, y0, wy);
-    in &= axis_weights(mz, iz, z0, wz);
-    if (!in && zero_outside) {
-      dst[idx] = make_float2(0.f, 0.f);
-      continue;
-    }
-    const int x1 = snx > 1 ? x0 + 1 : x0;
-    const int y1 = sny > 1 ? y0 + 1 : y0;
-    const int z1 = snz > 1 ? z0 + 1 : z0;
-    const long long sy = snz, sx = (long long)sny * snz;
-    const float2 c000 = __ldg(&src[x0 * sx + y0 * sy + z0]);
-    const float2 c001 = __ldg(&src[x0 * sx + y0 * sy + z1]);
-    const float2 c010 = __ldg(&src[x0 * sx + y1 * sy + z0]);
-    const float2 c011 = __ldg(&src[x0 * sx + y1 * sy + z1]);
-    const float2 c100 = __ldg(&src[x1 * sx + y0 * sy + z0]);
-    const float2 c101 = __ldg(&src[x1 * sx + y0 * sy + z1]);
-    const float2 c110 = __ldg(&src[x1 * sx + y1 * sy + z0]);
-    const float2 c111 = __ldg(&src[x1 * sx + y1 * sy + z1]);
-    const float uz = 1.f - wz, uy = 1.f - wy, ux = 1.f - wx;
-    float2 c00 = make_float2(uz * c000.x + wz * c001.x, uz * c000.y + wz * c001.y);
-    float2 c01 = make_float2(uz * c010.x + wz * c011.x, uz * c010.y + wz * c011.y);
-    float2 c10 = make_float2(uz * c100.x + wz * c101.x, uz * c100.y + wz * c101.y);
-    float2 c11 = make_float2(uz * c110.x + wz * c111.x, uz * c110.y + wz * c111.y);
-    float2 c0 = make_float2(uy * c00.x + wy * c01.x, uy * c00.y + wy * c01.y);
-    float2 c1 = make_float2(uy * c10.x + wy * c11.x, uy * c10.y + wy * c11.y);
-    dst[idx] = make_float2(ux * c0.x + wx * c1.x, ux * c0.y + wx * c1.y);
+// One CTA row of 128 targets along z at fixed (x, y) = (blockIdx.z, blockIdx.y).
+__global__ void __launch_bounds__(128) restrict_kernel(const float2* __restrict__ src, int snx, int sny, int snz,
+                                                       float2* __restrict__ dst, int dnx, int dny, int dnz,
+                                                       AxisFix mx, AxisFix my, AxisFix mz, int zero_outside) {
+  const int iz = blockIdx.x * blockDim.x + threadIdx.x;
+  const int iy = blockIdx.y;
+  const int ix = blockIdx.z;
+  if (iz >= dnz) return;
+  const long long idx = ((long long)ix * dny + iy) * dnz + iz;
+  int x0, y0, z0;
+  float wx, wy, wz;
+  bool in = axis_weights(mx, ix, x0, wx);
+  in &= axis_weights(my, iy, y0, wy);
+  in &= axis_weights(mz, iz, z0, wz);
+  if (!in && zero_outside) {
+    dst[idx] = make_float2(0.f, 0.f);
+    return;
   }
+  const int x1 = snx > 1 ? x0 + 1 : x0;
+  const int y1 = sny > 1 ? y0 + 1 : y0;
+  const int z1 = snz > 1 ? z0 + 1 : z0;
+  const long long sy = snz, sx = (long long)sny * snz;
+  const float2 c000 = __ldg(&src[x0 * sx + y0 * sy + z0]);
+  const float2 c001 = __ldg(&src[x0 * sx + y0 * sy + z1]);
+  const float2 c010 = __ldg(&src[x0 * sx + y1 * sy + z0]);
+  const float2 c011 = __ldg(&src[x0 * sx + y1 * sy + z1]);
+  const float2 c100 = __ldg(&src[x1 * sx + y0 * sy + z0]);
+  const float2 c101 = __ldg(&src[x1 * sx + y0 * sy + z1]);
+  const float2 c110 = __ldg(&src[x1 * sx + y1 * sy + z0]);
+  const float2 c111 = __ldg(&src[x1 * sx + y1 * sy + z1]);
+  const float uz = 1.f - wz, uy = 1.f - wy, ux = 1.f - wx;
+  const float2 c00 = make_float2(uz * c000.x + wz * c001.x, uz * c000.y + wz * c001.y);
+  const float2 c01 = make_float2(uz * c010.x + wz * c011.x, uz * c010.y + wz * c011.y);
+  const float2 c10 = make_float2(uz * c100.x + wz * c101.x, uz * c100.y + wz * c101.y);
+  const float2 c11 = make_float2(uz * c110.x + wz * c111.x, uz * c110.y + wz * c111.y);
+  const float2 c0 = make_float2(uy * c00.x + wy * c01.x, uy * c00.y + wy * c01.y);
+  const float2 c1 = make_float2(uy * c10.x + wy * c11.x, uy * c10.y + wy * c11.y);
+  dst[idx] = make_float2(ux * c0.x + wx * c1.x, ux * c0.y + wx * c1.y);
 }
 
 constexpr int kIncBlock = 256;
@@ -278,10 +279,16 @@ cudaError_t launch_source_assemble(const float2* const* lower, int harmonic, flo
 
 cudaError_t launch_restrict(const float2* src, const int ns[3], float2* dst, const int nd[3],
                             const double a[3], const double b[3], int zero_outside, cudaStream_t s) {
-  const long long total = (long long)nd[0] * nd[1] * nd[2];
-  AxisMap mx{a[0], b[0], ns[0]}, my{a[1], b[1], ns[1]}, mz{a[2], b[2], ns[2]};
-  restrict_kernel<<<grid_for(total, 256), 256, 0, s>>>(src, ns[0], ns[1], ns[2], dst, nd[0], nd[1], nd[2], mx,
-                                                        my, mz, zero_outside);
+  if (nd[1] > 65535 || nd[0] > 65535) return cudaErrorInvalidConfiguration;
+  AxisFix m[3];
+  for (int i = 0; i < 3; ++i) {
+    m[i].A = llround(a[i] * (double)(1LL << kFixBits));
+    m[i].B = llround(b[i] * (double)(1LL << kFixBits));
+    m[i].n = ns[i];
+  }
+  const dim3 grid((unsigned)((nd[2] + 127) / 128), (unsigned)nd[1], (unsigned)nd[0]);
+  restrict_kernel<<<grid, 128, 0, s>>>(src, ns[0], ns[1], ns[2], dst, nd[0], nd[1], nd[2], m[0], m[1], m[2],
+                                        zero_outside);
   return cudaGetLastError();
 }
 

@@ -269,6 +269,26 @@ cudaError_t launch_line_sweep(const LineSweep& p, int mode, cudaStream_t s) {
 
 }  // namespace vp
 
+namespace vp {
+
+cudaError_t launch_col_any(const ColSweep& p, int dir, bool src, cudaStream_t s) {
+  if (!p.ax.fast) return launch_col_sweep(p, dir, src, s);
+  cudaError_t e = launch_col2_part0(p, dir, src, s);
+  if (e == cudaErrorNotSupported) e = launch_col2_part1(p, dir, src, s);
+  if (e == cudaErrorNotSupported) e = launch_col2_part2(p, dir, src, s);
+  return e;
+}
+
+cudaError_t launch_line_any(const LineSweep& p, int mode, cudaStream_t s) {
+  if (!p.ax.fast) return launch_line_sweep(p, mode, s);
+  cudaError_t e = launch_line2_part0(p, mode, s);
+  if (e == cudaErrorNotSupported) e = launch_line2_part1(p, mode, s);
+  if (e == cudaErrorNotSupported) e = launch_line2_part2(p, mode, s);
+  return e;
+}
+
+}  // namespace vp
+
 #ifdef VP_DEBUG_CHECKS
 extern "C" VP_API int vp_debug_checks(int* out8, int reset) {
   if (cudaMemcpyFromSymbol(out8, vp::g_vp_debug, 8 * sizeof(int)) != cudaSuccess) return VP_ERR_CUDA;

@@ -50,7 +50,7 @@ class vp_plan_info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int * 3), ("m", ctypes.c_int * 3), ("radix", (ctypes.c_int * MAX_PASS) * 3),
                 ("k_re", ctypes.c_double), ("k_im", ctypes.c_double), ("c_n", ctypes.c_double),
                 ("self_re", ctypes.c_double), ("self_im", ctypes.c_double),
-                ("workspace_bytes", ctypes.c_ulonglong), ("khat_ready", ctypes.c_int)]
+                ("workspace_bytes", ctypes.c_ulonglong), ("khat_ready", ctypes.c_int), ("engine", ctypes.c_int * 3)]
 
 
 def _load():

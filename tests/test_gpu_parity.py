@@ -223,3 +223,62 @@ def test_small_workload_end_to_end(vp):
     bf = potential.apply_bruteforce(f, g.h, k2, targets=tg)
     sel = got[tg[:, 0], tg[:, 1], tg[:, 2]]
     assert np.linalg.norm(sel - bf) <= REL_L2 * np.linalg.norm(bf) * 3
+
+
+FAST_SIZES = [32, 64, 128, 192, 256, 320, 384, 512, 640, 768, 864, 1024, 1200, 1280]
+
+
+@pytest.mark.parametrize("L", FAST_SIZES)
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_two_level_engine_every_size_and_axis(vp, L, axis):
+    """Each compiled two-level length on each sweep type (x column, y column, z line),
+    with a ragged N = L/2 - 1 along that axis and radix-pass axes elsewhere."""
+    n = [5, 6, 7]
+    n[axis] = L // 2 - 1
+    m = [0, 0, 0]
+    m[axis] = L
+    g = grid(tuple(n), h=5e-5)
+    k = physics.wavenumber(2, 1.1e6, synth.WATER)
+    f = synth.random_field(tuple(n), seed=L + axis)
+    plan = vp.vp_plan(g, 2, 1.1e6, synth.WATER, m=m)
+    assert plan.info().engine[axis] == 1
+    vp.vp_kernel_fft(plan)
+    u = torch.empty(tuple(n), dtype=torch.complex64, device="cuda")
+    vp.vp_apply(plan, dev(f), u)
+    got = host(u)
+    plan.close()
+    ref = potential.apply_fft(f, g.h, k)
+    assert rel_l2(got, ref) <= REL_L2
+
+
+@pytest.mark.parametrize("harmonic", [2, 4, 5])
+def test_fused_source_on_two_level_engine(vp, harmonic):
+    n = (60, 31, 64)  # M = 128 (two-level), 64 (two-level), 128 (two-level)
+    g = grid(n, h=6e-5)
+    lower = [synth.random_field(n, seed=200 + m) for m in range(1, harmonic)]
+    plan = vp.vp_plan(g, harmonic, 1.1e6, synth.WATER)
+    assert list(plan.info().engine) == [1, 1, 1]
+    vp.vp_kernel_fft(plan)
+    u = torch.empty(n, dtype=torch.complex64, device="cuda")
+    plan.source_assemble([dev(x) for x in lower])
+    plan.apply(None, u)
+    got = host(u)
+    plan.close()
+    ref = cascade.harmonic(harmonic, lower, g.h, 1.1e6, synth.WATER)
+    assert rel_l2(got, ref) <= REL_L2
+
+
+def test_two_level_kernel_spectrum_octant(vp):
+    n = (64, 96, 40)  # M = 128, 192, 80 -> 128, 192 two-level; 80 radix passes
+    g = grid(n, h=8e-5)
+    plan = vp.vp_plan(g, 3, 1.1e6, synth.WATER)
+    inf = plan.info()
+    m = tuple(inf.m)
+    o = tuple(v // 2 + 1 for v in m)
+    vp.vp_kernel_fft(plan)
+    buf = torch.empty(o, dtype=torch.complex64, device="cuda")
+    plan.kernel_spectrum_get(buf)
+    got = host(buf)
+    plan.close()
+    full = potential.kernel_spectrum(n, g.h, physics.wavenumber(3, 1.1e6, synth.WATER), m)
+    assert rel_l2(got, full[: o[0], : o[1], : o[2]]) <= 1e-6
