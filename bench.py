@@ -38,7 +38,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="nested3", choices=["small", "nested3", "nested5"])
+    ap.add_argument("--workload", default="nested3", choices=["small", "nested3", "nested5", "batch64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--check", action="store_true", help="per-harmonic rel-L2 vs the FP64 oracle (slow)")
@@ -150,6 +150,35 @@ def sweep_bytes(n, m, harmonic, fused_source: bool):
 
 
 SWEEP_NAMES = ["x_forward_source", "y_forward", "z_conv", "y_inverse", "x_inverse"]
+
+
+def csrc_digest() -> str:
+    """Short digest of the CUDA sources; a stored ncu traffic figure is used only while it matches."""
+    import hashlib
+    d = os.path.join(ROOT, "paper_2011_03009_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")):
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(f.encode() + b"\0" + fh.read())
+    return h.hexdigest()[:12]
+
+
+def stored_traffic(kernel: str):
+    """DRAM bytes per launch (read + write) of `kernel` from profiles/dram_traffic.txt, or None.
+
+    Each line: <kernel label with spaces replaced by _> <csrc digest> <read bytes> <write bytes>.
+    """
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    key, dig = kernel.replace(" ", "_"), csrc_digest()
+    with open(path) as fh:
+        for line in fh:
+            f = line.split()
+            if len(f) == 4 and not line.startswith("#") and f[0] == key and f[1] == dig:
+                return int(float(f[2])) + int(float(f[3]))
+    return None
 
 
 def kernel_name(sweep: int, m, engine) -> str:
@@ -317,7 +346,7 @@ def run_ours(args, world, rank, local):
     if dom:
         roofline = {"bound": "hbm", "kernel": f"{dom['kernel']}, harmonic {dom['harmonic']}",
                     "achieved": round(dom["gbs"], 1), "peak": hbm_peak, "peak_source": peak_src,
-                    "unit": "GB/s", "frac": round(dom["gbs"] / hbm_peak, 4), "traffic": None,
+                    "unit": "GB/s", "frac": round(dom["gbs"] / hbm_peak, 4), "traffic": stored_traffic(dom["kernel"]),
                     "bytes_per_launch": dom["bytes_per_launch"], "ms_per_launch": round(dom["ms_per_launch"], 5)}
     # whole-apply model bytes ((25 + n) words per voxel for M = 2N) per harmonic
     per_h = {}
@@ -481,6 +510,120 @@ def run_reference(args, world, rank):
     print(json.dumps(line))
 
 
+# --------------------------------------------------------------------------- batched workload
+
+def run_batch(args, world, rank, local):
+    """64 seeded transducer configurations x harmonics 1-3 on uneven nested grids:
+    a loop of single-instance calls versus grouped batched launches replayed from a
+    CUDA graph.  Metric: harmonic fields per second."""
+    import torch
+    from paper_2011_03009_gb300 import synth
+    from paper_2011_03009_gb300 import vp
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    count = 64
+    inst = synth.draw_batch_instances(count, seed=4)
+    c64 = torch.complex64
+    n_points = 512  # bowl points per instance (input generator only)
+    items = []
+    t0 = time.perf_counter()
+    for i, b in enumerate(inst):
+        pts = torch.from_numpy(synth.sample_bowl_points(b.bowl, n_points, 4000 + i)).to(dev)
+        g1, g2, g3 = b.grids
+        it = {"grids": b.grids, "bowl": b.bowl}
+        it["p1_g1"] = torch.empty(g1.n, dtype=c64, device=dev)
+        it["p1_g2"] = torch.empty(g2.n, dtype=c64, device=dev)
+        vp.vp_incident_field(g1, pts, b.bowl, synth.WATER, it["p1_g1"])
+        vp.vp_incident_field(g2, pts, b.bowl, synth.WATER, it["p1_g2"])
+        it["plans"] = [vp.vp_plan(g, n, b.bowl.f0, synth.WATER, autotune=True) for n, g in ((1, g1), (2, g2), (3, g3))]
+        for p in it["plans"]:
+            p.kernel_fft()
+        it["u"] = [torch.empty(g.n, dtype=c64, device=dev) for g in (g1, g2, g3)]
+        it["r"] = [torch.empty(g3.n, dtype=c64, device=dev) for _ in range(2)]
+        items.append(it)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+
+    def restrict_all():
+        for it in items:
+            g1, g2, g3 = it["grids"]
+            vp.vp_restrict_to_nested_box(g2, it["p1_g2"], g3, it["r"][0])
+            vp.vp_restrict_to_nested_box(g2, it["u"][1], g3, it["r"][1])
+
+    def plain_step():
+        for it in items:
+            p1, p2, p3 = it["plans"]
+            g1, g2, g3 = it["grids"]
+            p1.apply(it["p1_g1"], it["u"][0])
+            p2.source_assemble([it["p1_g2"]])
+            p2.apply(None, it["u"][1])
+            vp.vp_restrict_to_nested_box(g2, it["p1_g2"], g3, it["r"][0])
+            vp.vp_restrict_to_nested_box(g2, it["u"][1], g3, it["r"][1])
+            p3.source_assemble([it["r"][0], it["r"][1]])
+            p3.apply(None, it["u"][2])
+
+    b1 = vp.Batch([it["plans"][0] for it in items], [it["u"][0] for it in items], fs=[it["p1_g1"] for it in items])
+    b2 = vp.Batch([it["plans"][1] for it in items], [it["u"][1] for it in items],
+                  lowers=[[it["p1_g2"]] for it in items])
+    b3 = vp.Batch([it["plans"][2] for it in items], [it["u"][2] for it in items],
+                  lowers=[[it["r"][0], it["r"][1]] for it in items])
+
+    def batched_step():
+        b1.run()
+        b2.run()
+        restrict_all()
+        b3.run()
+
+    def timeit(fn, reps):
+        for _ in range(max(3, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        z.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(z) / reps
+
+    reps = max(3, min(args.steps, 20))
+    ms_plain = timeit(plain_step, reps)
+    ms_batched = timeit(batched_step, reps)
+    # graph of the batched step
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        batched_step()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        batched_step()
+    ms_graph = timeit(graph.replay, reps)
+    graph_p = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph_p):
+        plain_step()
+    ms_plain_graph = timeit(graph_p.replay, reps)
+    fields = 3 * count
+    groups = {"h1": len(set(tuple(it["plans"][0].info().m) for it in items)),
+              "h2": len(set(tuple(it["plans"][1].info().m) for it in items)),
+              "h3": len(set(tuple(it["plans"][2].info().m) for it in items))}
+    voxels = sum(g.voxels for it in items for g in it["grids"])
+    line = {"metric": "fields/s", "value": fields / (ms_graph / 1e3), "unit": "fields/s", "n_gpus": 1,
+            "steps": reps, "warmup": max(3, args.warmup), "ms_per_step": ms_graph, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+            "config": {"workload": "batch64_h1-3_uneven_96-256cube", "instances": count, "fields_per_step": fields,
+                       "voxels_per_step": voxels, "bowl_points": n_points, "embedding_groups": groups,
+                       "setup_s": round(setup_s, 2)},
+            "plain_loop": {"fields_per_s": fields / (ms_plain / 1e3), "ms_per_step": ms_plain},
+            "plain_loop_graph": {"fields_per_s": fields / (ms_plain_graph / 1e3), "ms_per_step": ms_plain_graph},
+            "batched": {"fields_per_s": fields / (ms_batched / 1e3), "ms_per_step": ms_batched},
+            "batched_graph": {"fields_per_s": fields / (ms_graph / 1e3), "ms_per_step": ms_graph},
+            "voxel_potentials_per_s": voxels / (ms_graph / 1e3)}
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     world, rank, local = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), \
@@ -489,7 +632,10 @@ def main():
         run_reference(args, world, rank)
         return
     world, rank, local = dist_init(args)
-    run_ours(args, world, rank, local)
+    if args.workload == "batch64":
+        run_batch(args, world, rank, local)
+    else:
+        run_ours(args, world, rank, local)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -82,7 +82,9 @@ typedef struct vp_plan_opts {
     int m[3];           /* embedding size per axis; 0 = smallest even 5-smooth >= 2N     */
     int radix[3][8];    /* radix schedule per axis (product must equal M); 0-terminated,
                            all zero = default schedule                                    */
-    int autotune;       /* nonzero: time candidate schedules at plan time on `stream`   */
+    int autotune;       /* nonzero and no m / radix given: time the default embedding
+                           against the smallest even 5-smooth one (three applications
+                           each, on `stream`) and keep the faster; cached per grid shape */
 } vp_plan_opts;
 
 typedef struct vp_plan_info {
@@ -190,6 +192,28 @@ VP_API int vp_restrict_to_nested_box(const vp_grid* src, const void* src_field, 
 VP_API int vp_incident_field(const vp_grid* g, const double* points, int n_points, double l,
                              double R, double f0_hz, double p0, const vp_medium* m, void* out,
                              vp_stream_t stream);
+
+/* ---- batched evaluation -------------------------------------------------------------
+ * Many independent evaluations (e.g. many transducer configurations, each with its own
+ * nested grids) bound once and run together.  Item i computes u[i] = V_{k_n}[f_i] with
+ * plans[i]: f_i = f[i] when f != NULL and f[i] != NULL, otherwise the source of Eq. 2.6
+ * assembled from lower[i * 8 + 0 .. i * 8 + n - 2] (p_1 .. p_{n-1} on the plan's grid;
+ * rows of 8 pointers).  Items whose plans share the embedding size on every axis, run
+ * the two-level engine on every axis and agree on f vs source form one group; each
+ * group runs as one launch per FFT sweep over all its items (each CTA finds its item
+ * in a per-sweep offset table), so a batch of uneven grids needs a handful of
+ * launches instead of five per item.  Other items run one plan at a time.  All
+ * pointers are device pointers bound at creation; vp_batch_run recomputes from their
+ * current contents, so a stream capture of vp_batch_run replays correctly.  A plan may
+ * appear at most once per batch (items share nothing but read-only inputs); kernel
+ * spectra must be built (vp_kernel_fft) before vp_batch_run.
+ * Errors: VP_ERR_ARG (count < 1, null plan or output, a plan listed twice, a missing
+ * source field), VP_ERR_STATE (spectrum not built), VP_ERR_NOMEM, VP_ERR_CUDA. */
+typedef struct vp_batch_s* vp_batch_t;
+VP_API int vp_batch_create(int count, const vp_plan_t* plans, const void* const* f, const void* const* lower,
+                           void* const* u, vp_batch_t* out);
+VP_API int vp_batch_run(vp_batch_t b, vp_stream_t stream);
+VP_API int vp_batch_destroy(vp_batch_t b);
 
 /* ---- allocation-free volume potential --------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers that cannot

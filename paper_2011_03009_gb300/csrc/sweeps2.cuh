@@ -29,14 +29,14 @@ __host__ __device__ constexpr int col2_min_blocks(int L) { return L <= 512 ? 3 :
 __host__ __device__ constexpr int line2_bpitch(int B) { return B + 1; }
 __host__ __device__ constexpr int line2_pitch(int A, int B) { return A * (B + 1) + 1; }
 
+// One 16-column tile (tile index `tile` of p's n_outer x ceil(C/16) tiles).
 template <int A, int B, int DIR, bool SRC>
-__global__ void __launch_bounds__(kThreads2, col2_min_blocks(A * B)) col2_kernel(const ColSweep p) {
+__device__ __forceinline__ void col2_tile(const ColSweep& p, int tile, float2* S) {
   constexpr int L = A * B;
   constexpr int LP = col2_pitch(L);
-  extern __shared__ float2 S[];
   const int ncb = (p.C + kLines2 - 1) / kLines2;
-  const int o = blockIdx.x / ncb;
-  const int c0 = (blockIdx.x - o * ncb) * kLines2;
+  const int o = tile / ncb;
+  const int c0 = (tile - o * ncb) * kLines2;
   const float2* __restrict__ tw = p.ax.tw;
   const float2 zero = make_float2(0.f, 0.f);
 
@@ -140,12 +140,48 @@ __global__ void __launch_bounds__(kThreads2, col2_min_blocks(A * B)) col2_kernel
   }
 }
 
+template <int A, int B, int DIR, bool SRC>
+__global__ void __launch_bounds__(kThreads2, col2_min_blocks(A * B)) col2_kernel(const ColSweep p) {
+  extern __shared__ float2 S[];
+  col2_tile<A, B, DIR, SRC>(p, blockIdx.x, S);
+}
+
+// Batched form: the parameters of up to kMaxBatch plans travel in the kernel's own
+// parameter block (constant bank), with offsets[i] the first CTA (or tile) of plan i;
+// CTA b finds its plan by a binary search over the constant-bank offsets.
+template <typename T>
+__device__ __forceinline__ int batch_owner(const BatchParams<T>& bp, int b) {
+  int lo = 0, hi = bp.count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (bp.offsets[mid] <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <typename T>
+__device__ __forceinline__ void copy_params(T* dst, const T* src) {
+  static_assert(sizeof(T) % 4 == 0, "parameter blocks are word-sized");
+  const int* s = (const int*)src;
+  int* d = (int*)dst;
+  for (int i = threadIdx.x; i < (int)(sizeof(T) / 4); i += blockDim.x) d[i] = __ldg(&s[i]);
+}
+
+template <int A, int B, int DIR, bool SRC>
+__global__ void __launch_bounds__(kThreads2, col2_min_blocks(A * B))
+    col2_batch_kernel(const __grid_constant__ BatchParams<ColSweep> bp) {
+  extern __shared__ float2 S[];
+  const int owner = batch_owner(bp, blockIdx.x);
+  col2_tile<A, B, DIR, SRC>(bp.item[owner], blockIdx.x - bp.offsets[owner], S);
+}
+
+// One tile of 16 lines (conv: tile `tile` of the tile list; forward: lines 16 tile ..).
 template <int A, int B, int MODE>
-__global__ void __launch_bounds__(kThreads2) line2_kernel(const LineSweep p) {
+__device__ __forceinline__ void line2_tile(const LineSweep& p, long long tile, float2* S) {
   constexpr int L = A * B;
   constexpr int BP = line2_bpitch(B);
   constexpr int LP = line2_pitch(A, B);
-  extern __shared__ float2 S[];
   __shared__ long long line_of[kLines2];
   __shared__ int oct_of[4];
   const float2* __restrict__ tw = p.ax.tw;
@@ -154,14 +190,14 @@ __global__ void __launch_bounds__(kThreads2) line2_kernel(const LineSweep p) {
   if (threadIdx.x < kLines2) {
     long long l;
     if (MODE == kConv) {
-      l = p.tiles[20LL * blockIdx.x + threadIdx.x];
+      l = p.tiles[20LL * tile + threadIdx.x];
     } else {
-      l = (long long)blockIdx.x * kLines2 + threadIdx.x;
+      l = tile * kLines2 + threadIdx.x;
       if (l >= p.nlines) l = -1;
     }
     line_of[threadIdx.x] = l;
   }
-  if (MODE == kConv && threadIdx.x < 4) oct_of[threadIdx.x] = p.tiles[20LL * blockIdx.x + 16 + threadIdx.x];
+  if (MODE == kConv && threadIdx.x < 4) oct_of[threadIdx.x] = p.tiles[20LL * tile + 16 + threadIdx.x];
   __syncthreads();
 
   // forward step 1: task (line, b), b fastest across lanes (coalesced along the line)
@@ -244,6 +280,19 @@ __global__ void __launch_bounds__(kThreads2) line2_kernel(const LineSweep p) {
   }
 }
 
+template <int A, int B, int MODE>
+__global__ void __launch_bounds__(kThreads2) line2_kernel(const LineSweep p) {
+  extern __shared__ float2 S[];
+  line2_tile<A, B, MODE>(p, blockIdx.x, S);
+}
+
+template <int A, int B>
+__global__ void __launch_bounds__(kThreads2) line2_batch_kernel(const __grid_constant__ BatchParams<LineSweep> bp) {
+  extern __shared__ float2 S[];
+  const int owner = batch_owner(bp, blockIdx.x);
+  line2_tile<A, B, kConv>(bp.item[owner], blockIdx.x - bp.offsets[owner], S);
+}
+
 // Persistent, software-pipelined form of line2_kernel<kConv>: each CTA walks the tiles
 // blockIdx.x, blockIdx.x + gridDim.x, ...  The 16 input lines of the next tile are
 // copied into a staging buffer with cp.async while the current tile runs its forward
@@ -260,37 +309,64 @@ __host__ __device__ constexpr size_t conv_pipe_smem(int A, int B, int n_in, int 
          sizeof(float2);
 }
 
-template <int A, int B>
-__global__ void __launch_bounds__(kThreads2) line2_conv_pipe_kernel(const LineSweep p) {
+// p is a __grid_constant__ parameter, so &p is one address valid in every thread.
+// BATCH = false: the tiles of plan p.  BATCH = true: the tiles of every plan of a group,
+// numbered consecutively (plan i owns [offsets[i], offsets[i + 1])), all with the same
+// line length L and spectrum octant length; ni is the staging pitch for the longest
+// input line.
+template <int A, int B, bool BATCH>
+__global__ void __launch_bounds__(kThreads2)
+    line2_conv_pipe_kernel(const __grid_constant__ LineSweep p, const __grid_constant__ BatchParams<LineSweep> bp,
+                           long long ntiles, int NI) {
   constexpr int L = A * B;
   constexpr int BP = line2_bpitch(B);
   constexpr int LP = line2_pitch(A, B);
   extern __shared__ float2 S[];
-  const int NI = conv_stage_pitch(p.n_in);
+  const int Oz = p.Oz;  // shared by every plan of a batch group
   float2* I = S + kLines2 * LP;
   float2* K = I + kLines2 * NI;  // [4][Oz]
-  float2* T = K + 4 * p.Oz;      // twiddles
+  float2* T = K + 4 * Oz;        // twiddles
   __shared__ long long line_of[2][kLines2];
   __shared__ int oct_of[2][4];
+  __shared__ const LineSweep* plan_of[2];
   const float2 zero = make_float2(0.f, 0.f);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long ntiles = p.nlines;
 
-  auto fetch_lines = [&](long long t, int slot) {
-    for (int b = warp; b < kLines2; b += kThreads2 / 32) {
-      const long long l = p.tiles[20LL * t + b];
-      const float2* src = p.data + (l < 0 ? 0 : l * p.ld);
-      for (int n = lane; n < p.n_in; n += 32) cp_async8(&I[b * NI + n], &src[n], l >= 0);
+  // plan and local tile index of global tile t
+  auto resolve = [&](long long t, long long& local) -> const LineSweep* {
+    if constexpr (BATCH) {
+      const int i = batch_owner(bp, (int)t);
+      local = t - bp.offsets[i];
+      return &bp.item[i];
+    } else {
+      local = t;
+      return &p;
     }
-    if (threadIdx.x < kLines2) line_of[slot][threadIdx.x] = p.tiles[20LL * t + threadIdx.x];
-    if (threadIdx.x < 4) oct_of[slot][threadIdx.x] = p.tiles[20LL * t + 16 + threadIdx.x];
+  };
+  auto fetch_lines = [&](long long t, int slot) {
+    long long lt = 0;
+    const LineSweep* q = resolve(t, lt);
+    const int* tiles = q->tiles;
+    const float2* data = q->data;
+    const long long ld = q->ld;
+    const int n_in = q->n_in;
+    for (int b = warp; b < kLines2; b += kThreads2 / 32) {
+      const long long l = tiles[20LL * lt + b];
+      const float2* src = data + (l < 0 ? 0 : l * ld);
+      for (int n = lane; n < NI; n += 32) cp_async8(&I[b * NI + n], &src[n < n_in ? n : 0], l >= 0 && n < n_in);
+    }
+    if (threadIdx.x < kLines2) line_of[slot][threadIdx.x] = tiles[20LL * lt + threadIdx.x];
+    if (threadIdx.x < 4) oct_of[slot][threadIdx.x] = tiles[20LL * lt + 16 + threadIdx.x];
+    if (threadIdx.x == 0) plan_of[slot] = q;
   };
   auto fetch_spectrum = [&](long long t) {
+    long long lt = 0;
+    const LineSweep* q = resolve(t, lt);
     const int g = warp & 3;
-    const int oc = p.tiles[20LL * t + 16 + g];
-    const float2* kl = p.khat + (oc < 0 ? 0 : (long long)oc * p.Oz);
-    for (int i = (warp >> 2) * 32 + lane; i < p.Oz; i += (kThreads2 / 128) * 32)
-      cp_async8(&K[g * p.Oz + i], &kl[i], oc >= 0);
+    const int oc = q->tiles[20LL * lt + 16 + g];
+    const float2* kl = q->khat + (oc < 0 ? 0 : (long long)oc * Oz);
+    for (int i = (warp >> 2) * 32 + lane; i < Oz; i += (kThreads2 / 128) * 32)
+      cp_async8(&K[g * Oz + i], &kl[i], oc >= 0);
   };
 
   for (int i = threadIdx.x; i < L; i += blockDim.x) cp_async8(&T[i], &p.ax.tw[i], true);
@@ -304,6 +380,10 @@ __global__ void __launch_bounds__(kThreads2) line2_conv_pipe_kernel(const LineSw
     const int cur = it & 1;
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
+    const LineSweep* q = plan_of[cur];
+    const int n_out = q->n_out;
+    float2* const data = q->data;
+    const long long ld = q->ld;
     // forward step 1 from the staging buffer; the 16 lanes of a half-warp hold the 16
     // lines (odd staging pitch), so every twiddle read is a broadcast
     for (int tau = threadIdx.x; tau < kLines2 * B; tau += blockDim.x) {
@@ -314,7 +394,7 @@ __global__ void __launch_bounds__(kThreads2) line2_conv_pipe_kernel(const LineSw
 #pragma unroll
       for (int a = 0; a < A; ++a) {
         const int n = B * a + b;
-        v[a] = n < p.n_in ? src[n] : zero;
+        v[a] = n < NI ? src[n] : zero;  // the staging buffer holds zeros past n_in
       }
       dft_reg<A, false>(v);
       float2* s = S + line * LP + b;
@@ -336,7 +416,7 @@ __global__ void __launch_bounds__(kThreads2) line2_conv_pipe_kernel(const LineSw
       for (int b = 0; b < B; ++b) z[b] = s[b];
       dft_reg<B, false>(z);
       if (oct_of[cur][line >> 2] >= 0) {
-        const float2* kl = K + (line >> 2) * p.Oz;
+        const float2* kl = K + (line >> 2) * Oz;
 #pragma unroll
         for (int k2 = 0; k2 < B; ++k2) {
           const int f = k1 + A * k2;
@@ -362,11 +442,11 @@ __global__ void __launch_bounds__(kThreads2) line2_conv_pipe_kernel(const LineSw
       dft_reg<A, true>(v);
       const long long l = line_of[cur][line];
       if (l >= 0) {
-        float2* dst = p.data + l * p.ld;
+        float2* dst = data + l * ld;
 #pragma unroll
         for (int a = 0; a < A; ++a) {
           const int n = B * a + b;
-          if (n < p.n_out) dst[n] = v[a];
+          if (n < n_out) dst[n] = v[a];
         }
       }
     }

@@ -56,41 +56,52 @@ cudaError_t col2_dispatch(const ColSweep& p, int dir, bool src, cudaStream_t s) 
 }
 
 // Persistent pipelined convolution sweep: one CTA per resident slot, tiles strided.
-template <int A, int B>
-cudaError_t line2_conv_pipe_launch(const LineSweep& p, cudaStream_t s, bool* used) {
-  static volatile int granted[64] = {0};
-  static int slots[64] = {0};
-  *used = false;
-  const size_t smem = conv_pipe_smem(A, B, p.n_in, p.Oz);
-  if (smem > 200 * 1024) return cudaSuccess;  // too large to pipeline: caller falls back
-  if (p.nlines <= 0) {
-    *used = true;
-    return cudaSuccess;
-  }
-  auto k = line2_conv_pipe_kernel<A, B>;
+// Resident CTAs per SM for a given shared-memory size, cached per (device, size).
+template <typename K>
+cudaError_t resident_slots(K kernel, size_t smem, volatile int* granted, int* grid_out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   if (!granted[dev]) {
     // the staging buffer depends on n_in: grant the largest pipelined size once
-    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
     granted[dev] = 1;
   }
-  int per_sm = 0, sms = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads2, smem);
-  if (e != cudaSuccess) return e;
-  if (!slots[dev]) {
-    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  static int sms[64] = {0};
+  if (!sms[dev]) {
+    int v = 0;
+    e = cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    slots[dev] = sms;
+    sms[dev] = v;
   }
-  sms = slots[dev];
-  if (per_sm < 1) return cudaSuccess;
-  long long grid = (long long)per_sm * sms;
-  if (grid > p.nlines) grid = p.nlines;
-  k<<<(unsigned)grid, kThreads2, smem, s>>>(p);
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads2, smem);
+  if (e != cudaSuccess) return e;
+  *grid_out = per_sm * sms[dev];
+  return cudaSuccess;
+}
+
+template <int A, int B>
+cudaError_t line2_conv_pipe_launch(const LineSweep& p, cudaStream_t s, bool* used) {
+  static volatile int granted[64] = {0};
+  *used = false;
+  const int ni = conv_stage_pitch(p.n_in);
+  const size_t smem = conv_pipe_smem(A, B, p.n_in, p.Oz);
+  if (smem > 200 * 1024) return cudaSuccess;  // too large to pipeline: caller falls back
+  if (p.nlines <= 0) {
+    *used = true;
+    return cudaSuccess;
+  }
+  auto k = line2_conv_pipe_kernel<A, B, false>;
+  int grid = 0;
+  cudaError_t e = resident_slots(k, smem, granted, &grid);
+  if (e != cudaSuccess) return e;
+  if (grid < 1) return cudaSuccess;
+  if (grid > p.nlines) grid = (int)p.nlines;
+  static BatchParams<LineSweep> none{};  // unused by the single-plan form
+  k<<<(unsigned)grid, kThreads2, smem, s>>>(p, none, p.nlines, ni);
   *used = true;
   return cudaGetLastError();
 }
@@ -104,6 +115,54 @@ cudaError_t line2_dispatch(const LineSweep& p, int mode, cudaStream_t s) {
     return line2_launch<A, B, kConv>(p, s);
   }
   return line2_launch<A, B, kForwardOnly>(p, s);
+}
+
+template <int A, int B, int DIR, bool SRC>
+cudaError_t col2_batch_launch(const BatchParams<ColSweep>& bp, int total, cudaStream_t s) {
+  static volatile int granted[64] = {0};
+  const size_t smem = (size_t)kLines2 * col2_pitch(A * B) * sizeof(float2);
+  if (total <= 0) return cudaSuccess;
+  auto k = col2_batch_kernel<A, B, DIR, SRC>;
+  cudaError_t e = grant_smem(k, smem, granted);
+  if (e != cudaSuccess) return e;
+  k<<<(unsigned)total, kThreads2, smem, s>>>(bp);
+  return cudaGetLastError();
+}
+
+template <int A, int B>
+cudaError_t col2_batch_dispatch(const BatchParams<ColSweep>& bp, int total, int dir, bool src, cudaStream_t s) {
+  if (dir == kForward && src) return col2_batch_launch<A, B, kForward, true>(bp, total, s);
+  if (dir == kForward) return col2_batch_launch<A, B, kForward, false>(bp, total, s);
+  return col2_batch_launch<A, B, kInverse, false>(bp, total, s);
+}
+
+// Batched z sweep: the pipelined persistent kernel over every tile of the group when
+// its shared memory fits, else one CTA per tile.  first: any plan of the group (for the
+// shared twiddle table and octant length); ni_max: longest input line of the group.
+template <int A, int B>
+cudaError_t line2_batch_dispatch(const LineSweep& first, int ni_max, const BatchParams<LineSweep>& bp, int total,
+                                 cudaStream_t s) {
+  if (total <= 0) return cudaSuccess;
+  const size_t psmem = conv_pipe_smem(A, B, ni_max, first.Oz);
+  if (psmem <= 200 * 1024) {
+    static volatile int pgranted[64] = {0};
+    auto k = line2_conv_pipe_kernel<A, B, true>;
+    int grid = 0;
+    cudaError_t e = resident_slots(k, psmem, pgranted, &grid);
+    if (e != cudaSuccess) return e;
+    if (grid >= 1) {
+      if (grid > total) grid = total;
+      k<<<(unsigned)grid, kThreads2, psmem, s>>>(first, bp, total, conv_stage_pitch(ni_max));
+      return cudaGetLastError();
+    }
+  }
+  static volatile int granted[64] = {0};
+  const size_t smem = (size_t)kLines2 * line2_pitch(A, B) * sizeof(float2);
+  auto k = line2_batch_kernel<A, B>;
+  cudaError_t e = grant_smem(k, smem, granted);
+  if (e != cudaSuccess) return e;
+  k<<<(unsigned)total, kThreads2, smem, s>>>(bp);
+  return cudaGetLastError();
 }
 
 }  // namespace

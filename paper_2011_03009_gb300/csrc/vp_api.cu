@@ -8,6 +8,10 @@
 #include <complex>
 #include <cstdlib>
 #include <cstring>
+#include <array>
+#include <map>
+#include <memory>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -295,21 +299,17 @@ int prof_end(ProfRec* r, cudaStream_t s) {
   return VP_OK;
 }
 
-// The five sweeps; sweep 1 either loads f or assembles the source.
-int run_sweep(vp_plan_s* p, int which, const float2* f, const float2* const* lower, float2* u,
-              cudaStream_t s) {
+// Parameters of column sweep `which` (0 x forward, 1 y forward, 3 y inverse, 4 x
+// inverse); sweep 0 reads f, or assembles the source from lower when lower != NULL.
+ColSweep col_params(const vp_plan_s* p, int which, const float2* f, const float2* const* lower, float2* u) {
   const int Nx = p->n[0], Ny = p->n[1], Nz = p->n[2];
   const int Mx = p->m[0], My = p->m[1];
-  ProfRec* rec = nullptr;
-  int st = prof_begin(p, which, s, &rec);
-  if (st != VP_OK) return st;
-  cudaError_t e = cudaSuccess;
+  ColSweep c{};
+  c.scale = 1.0f;
+  c.C = Nz;
   if (which == 0 || which == 4) {
-    ColSweep c{};
     c.ax = axis_desc(p, 0);
-    c.C = Nz;
     c.n_outer = Ny;
-    c.scale = 1.0f;
     if (which == 0) {
       c.in = f;
       c.in_rs = (long long)Ny * Nz;
@@ -326,7 +326,6 @@ int run_sweep(vp_plan_s* p, int which, const float2* f, const float2* const* low
         c.cn = (float)p->cn;
         for (int i = 0; i < p->harmonic - 1; ++i) c.lower[i] = lower[i];
       }
-      e = vp::launch_col_any(c, vp::kForward, lower != nullptr, s);
     } else {
       c.in = p->wsA;
       c.in_rs = (long long)Ny * Nz;
@@ -339,14 +338,10 @@ int run_sweep(vp_plan_s* p, int which, const float2* f, const float2* const* low
       c.in_elems = (long long)Mx * Ny * Nz;
       c.out_elems = (long long)Nx * Ny * Nz;
       c.scale = (float)(1.0 / ((double)p->m[0] * p->m[1] * p->m[2]));
-      e = vp::launch_col_any(c, vp::kInverse, false, s);
     }
-  } else if (which == 1 || which == 3) {
-    ColSweep c{};
+  } else {
     c.ax = axis_desc(p, 1);
-    c.C = Nz;
     c.n_outer = Mx;
-    c.scale = 1.0f;
     if (which == 1) {
       c.in = p->wsA;
       c.in_rs = Nz;
@@ -358,7 +353,6 @@ int run_sweep(vp_plan_s* p, int which, const float2* f, const float2* const* low
       c.rows_out = My;
       c.in_elems = (long long)Mx * Ny * Nz;
       c.out_elems = (long long)Mx * My * Nz;
-      e = vp::launch_col_any(c, vp::kForward, false, s);
     } else {
       c.in = p->wsB;
       c.in_rs = Nz;
@@ -370,26 +364,149 @@ int run_sweep(vp_plan_s* p, int which, const float2* f, const float2* const* low
       c.rows_out = Ny;
       c.in_elems = (long long)Mx * My * Nz;
       c.out_elems = (long long)Mx * Ny * Nz;
-      e = vp::launch_col_any(c, vp::kInverse, false, s);
     }
+  }
+  return c;
+}
+
+// Parameters of the z sweep (forward FFT, spectrum multiply, inverse FFT).
+LineSweep line_params(const vp_plan_s* p) {
+  LineSweep l{};
+  l.ax = axis_desc(p, 2);
+  l.data = p->wsB;
+  l.nlines = p->nztiles;
+  l.ld = p->n[2];
+  l.n_in = p->n[2];
+  l.n_out = p->n[2];
+  l.data_elems = (long long)p->m[0] * p->m[1] * p->n[2];
+  l.khat = p->khat;
+  l.Oz = p->oct[2];
+  l.tiles = p->ztiles;
+  l.fold_z = p->fold[2];
+  return l;
+}
+
+// The five sweeps; sweep 1 either loads f or assembles the source.
+int run_sweep(vp_plan_s* p, int which, const float2* f, const float2* const* lower, float2* u,
+              cudaStream_t s) {
+  ProfRec* rec = nullptr;
+  int st = prof_begin(p, which, s, &rec);
+  if (st != VP_OK) return st;
+  cudaError_t e;
+  if (which == 2) {
+    e = vp::launch_line_any(line_params(p), vp::kConv, s);
   } else {
-    LineSweep l{};
-    l.ax = axis_desc(p, 2);
-    l.data = p->wsB;
-    l.nlines = p->nztiles;
-    l.ld = Nz;
-    l.n_in = Nz;
-    l.n_out = Nz;
-    l.data_elems = (long long)Mx * My * Nz;
-    l.khat = p->khat;
-    l.Oz = p->oct[2];
-    l.tiles = p->ztiles;
-    l.fold_z = p->fold[2];
-    e = vp::launch_line_any(l, vp::kConv, s);
+    const ColSweep c = col_params(p, which, f, lower, u);
+    e = vp::launch_col_any(c, which <= 1 ? vp::kForward : vp::kInverse, which == 0 && lower != nullptr, s);
   }
   if (e != cudaSuccess) return cuda_status(e);
   return prof_end(rec, s);
 }
+
+// ---- autotuner: embedding size per grid shape -----------------------------------------
+// Candidates: the default (two-level engine where its menu allows) and the smallest even
+// 5-smooth size per axis (radix-pass engine unless that size is on the menu).  Each is
+// timed over three applications on the caller's stream; the winner is cached per grid
+// shape for the life of the process.
+
+std::mutex g_tune_mu;
+std::map<std::array<int, 3>, std::array<int, 3>> g_tune_cache;
+
+// ---- batched evaluation ------------------------------------------------------------
+
+cudaError_t col2_batch(int L, const vp::BatchParams<ColSweep>& bp, int total, int dir, bool src, cudaStream_t s) {
+  cudaError_t e = vp::launch_col2_batch_part0(L, bp, total, dir, src, s);
+  if (e == cudaErrorNotSupported) e = vp::launch_col2_batch_part1(L, bp, total, dir, src, s);
+  if (e == cudaErrorNotSupported) e = vp::launch_col2_batch_part2(L, bp, total, dir, src, s);
+  return e;
+}
+
+cudaError_t line2_batch(int L, const LineSweep& first, int ni_max, const vp::BatchParams<LineSweep>& bp, int total,
+                        cudaStream_t s) {
+  cudaError_t e = vp::launch_line2_batch_part0(L, first, ni_max, bp, total, s);
+  if (e == cudaErrorNotSupported) e = vp::launch_line2_batch_part1(L, first, ni_max, bp, total, s);
+  if (e == cudaErrorNotSupported) e = vp::launch_line2_batch_part2(L, first, ni_max, bp, total, s);
+  return e;
+}
+
+// Items of one group share the embedding sizes, run the two-level engine on every
+// axis and agree on whether sweep 1 assembles a source: one launch per sweep for each
+// chunk of at most kMaxBatch items, whose parameters ride in the kernel parameter block.
+struct BatchChunk {
+  vp::BatchParams<ColSweep> col[4];  // sweeps 0, 1, 3, 4
+  vp::BatchParams<LineSweep> line;
+  int total[5] = {0, 0, 0, 0, 0};
+  LineSweep first{};  // any item's z-sweep parameters (shared twiddle table, octant length)
+  int ni_max = 0;     // longest z input line of the chunk
+};
+
+struct BatchGroup {
+  int m[3] = {0, 0, 0};
+  bool src = false;
+  std::vector<int> items;
+  std::vector<std::unique_ptr<BatchChunk>> chunks;
+};
+
+}  // namespace
+
+struct vp_batch_s {
+  int count = 0;
+  std::vector<vp_plan_t> plans;
+  std::vector<const void*> f;
+  std::vector<std::vector<const void*>> lower;
+  std::vector<void*> u;
+  std::vector<BatchGroup> groups;
+  std::vector<int> singles;  // items evaluated one plan at a time
+};
+
+namespace {
+
+void free_batch(vp_batch_s* b) { delete b; }
+
+long long col_ctas(const ColSweep& c) { return (long long)((c.C + 15) / 16) * c.n_outer; }
+
+int build_group(vp_batch_s* b, BatchGroup& g) {
+  const int sweeps[4] = {0, 1, 3, 4};
+  const int n_all = (int)g.items.size();
+  for (int c0 = 0; c0 < n_all; c0 += vp::kMaxBatch) {
+    const int n = std::min(vp::kMaxBatch, n_all - c0);
+    std::unique_ptr<BatchChunk> ch(new (std::nothrow) BatchChunk());
+    if (!ch) return VP_ERR_NOMEM;
+    std::memset(ch.get(), 0, sizeof(BatchChunk));
+    long long acc[5] = {0, 0, 0, 0, 0};
+    for (int q = 0; q < 4; ++q) ch->col[q].count = n;
+    ch->line.count = n;
+    for (int j = 0; j < n; ++j) {
+      const int i = g.items[c0 + j];
+      vp_plan_s* p = b->plans[i];
+      const float2* lo[vp::kMaxLower] = {};
+      for (size_t k = 0; k < b->lower[i].size(); ++k) lo[k] = (const float2*)b->lower[i][k];
+      for (int q = 0; q < 4; ++q) {
+        const ColSweep c = col_params(p, sweeps[q], (const float2*)b->f[i], g.src ? lo : nullptr, (float2*)b->u[i]);
+        ch->col[q].item[j] = c;
+        const int w = q < 2 ? q : q + 1;
+        ch->col[q].offsets[j] = (int)acc[w];
+        acc[w] += col_ctas(c);
+      }
+      const LineSweep l = line_params(p);
+      ch->line.item[j] = l;
+      ch->line.offsets[j] = (int)acc[2];
+      acc[2] += l.nlines;
+      ch->ni_max = std::max(ch->ni_max, l.n_in);
+      if (j == 0) ch->first = l;
+    }
+    for (int w = 0; w < 5; ++w) {
+      if (acc[w] > 0x7fffffffLL) return VP_ERR_SIZE;
+      ch->total[w] = (int)acc[w];
+    }
+    for (int q = 0; q < 4; ++q) ch->col[q].offsets[n] = ch->total[q < 2 ? q : q + 1];
+    ch->line.offsets[n] = ch->total[2];
+    g.chunks.push_back(std::move(ch));
+  }
+  return VP_OK;
+}
+
+int autotune_m(const vp_grid* g, double f0, const vp_medium* med, cudaStream_t s, int* best_m);
 
 }  // namespace
 
@@ -420,6 +537,30 @@ VP_API int vp_plan(const vp_grid* g, int harmonic_n, double f0_hz, const vp_medi
       !std::isfinite(f0_hz))
     return VP_ERR_ARG;
   if (harmonic_n - 1 > vp::kMaxLower) return VP_ERR_UNSUPPORTED;
+  if (opts && opts->autotune) {
+    bool explicit_choice = false;
+    for (int a = 0; a < 3; ++a) explicit_choice |= opts->m[a] != 0 || opts->radix[a][0] != 0;
+    if (!explicit_choice) {
+      vp_plan_opts o{};
+      const std::array<int, 3> key = {g->n[0], g->n[1], g->n[2]};
+      bool cached = false;
+      {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+          for (int a = 0; a < 3; ++a) o.m[a] = it->second[a];
+          cached = true;
+        }
+      }
+      if (!cached) {
+        const int st = autotune_m(g, f0_hz, med, (cudaStream_t)stream, o.m);
+        if (st != VP_OK) return st;
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = {o.m[0], o.m[1], o.m[2]};
+      }
+      return vp_plan(g, harmonic_n, f0_hz, med, &o, stream, out);
+    }
+  }
   // sizes and schedules are validated before any device work
   int m[3], radix[3][vp::kMaxPass], npass[3], fast[3];
   for (int a = 0; a < 3; ++a) {
@@ -670,6 +811,101 @@ VP_API int vp_incident_field(const vp_grid* g, const double* points, int n_point
   return cuda_status(e);
 }
 
+VP_API int vp_batch_create(int count, const vp_plan_t* plans, const void* const* f, const void* const* lower,
+                           void* const* u, vp_batch_t* out) {
+  if (out) *out = nullptr;
+  if (!out || count < 1 || !plans || !u) return VP_ERR_ARG;
+  vp_batch_s* b = new (std::nothrow) vp_batch_s();
+  if (!b) return VP_ERR_NOMEM;
+  b->count = count;
+  b->plans.assign(plans, plans + count);
+  b->f.resize(count, nullptr);
+  b->lower.resize(count);
+  b->u.assign(u, u + count);
+  for (int i = 0; i < count; ++i) {
+    vp_plan_s* p = plans[i];
+    bool bad = !p || !u[i];
+    for (int j = 0; j < i && !bad; ++j) bad = plans[j] == p;  // one workspace per plan
+    const void* fi = f ? f[i] : nullptr;
+    if (!bad && !fi) {
+      if (!lower || p->harmonic < 2) bad = true;
+      for (int k = 0; !bad && k < p->harmonic - 1; ++k) {
+        const void* q = lower[(size_t)i * vp::kMaxLower + k];
+        if (!q) bad = true;
+        else b->lower[i].push_back(q);
+      }
+    }
+    if (bad) {
+      free_batch(b);
+      return VP_ERR_ARG;
+    }
+    b->f[i] = fi;
+  }
+  for (int i = 0; i < count; ++i) {
+    vp_plan_s* p = plans[i];
+    const bool all_fast = p->fast[0] && p->fast[1] && p->fast[2];
+    if (!all_fast) {
+      b->singles.push_back(i);
+      continue;
+    }
+    const bool src = b->f[i] == nullptr;
+    BatchGroup* g = nullptr;
+    for (auto& h : b->groups)
+      if (h.m[0] == p->m[0] && h.m[1] == p->m[1] && h.m[2] == p->m[2] && h.src == src) g = &h;
+    if (!g) {
+      b->groups.emplace_back();
+      g = &b->groups.back();
+      for (int a = 0; a < 3; ++a) g->m[a] = p->m[a];
+      g->src = src;
+    }
+    g->items.push_back(i);
+  }
+  for (auto& g : b->groups) {
+    const int st = build_group(b, g);
+    if (st != VP_OK) {
+      free_batch(b);
+      return st;
+    }
+  }
+  *out = b;
+  return VP_OK;
+}
+
+VP_API int vp_batch_run(vp_batch_t b, vp_stream_t stream) {
+  if (!b) return VP_ERR_ARG;
+  for (int i = 0; i < b->count; ++i)
+    if (!b->plans[i]->khat_ready) return VP_ERR_STATE;
+  cudaStream_t s = (cudaStream_t)stream;
+  for (auto& g : b->groups) {
+    for (auto& chp : g.chunks) {
+      const BatchChunk& ch = *chp;
+      cudaError_t e = col2_batch(g.m[0], ch.col[0], ch.total[0], vp::kForward, g.src, s);
+      if (e == cudaSuccess) e = col2_batch(g.m[1], ch.col[1], ch.total[1], vp::kForward, false, s);
+      if (e == cudaSuccess) e = line2_batch(g.m[2], ch.first, ch.ni_max, ch.line, ch.total[2], s);
+      if (e == cudaSuccess) e = col2_batch(g.m[1], ch.col[2], ch.total[3], vp::kInverse, false, s);
+      if (e == cudaSuccess) e = col2_batch(g.m[0], ch.col[3], ch.total[4], vp::kInverse, false, s);
+      if (e != cudaSuccess) return cuda_status(e);
+    }
+  }
+  for (int i : b->singles) {
+    vp_plan_s* p = b->plans[i];
+    int st;
+    if (b->f[i]) {
+      st = vp_apply(p, b->f[i], b->u[i], stream);
+    } else {
+      st = vp_source_assemble(p, b->lower[i].data(), (int)b->lower[i].size(), 0, nullptr, stream);
+      if (st == VP_OK) st = vp_apply(p, nullptr, b->u[i], stream);
+    }
+    if (st != VP_OK) return st;
+  }
+  return VP_OK;
+}
+
+VP_API int vp_batch_destroy(vp_batch_t b) {
+  free_batch(b);
+  return VP_OK;
+}
+
 VP_API int vp_profile_enable(vp_plan_t p, int on) {
   if (!p) return VP_ERR_ARG;
   p->prof_on = on != 0;
@@ -699,3 +935,54 @@ VP_API int vp_profile_read(vp_plan_t p, double ms[5], int count[5], int reset) {
 }
 
 }  // extern "C"
+
+namespace {
+
+int autotune_m(const vp_grid* g, double f0, const vp_medium* med, cudaStream_t s, int* best_m) {
+  int cand[2][3];
+  for (int a = 0; a < 3; ++a) {
+    cand[0][a] = default_m(g->n[a]);
+    cand[1][a] = smooth_m(g->n[a]);
+    best_m[a] = cand[0][a];
+  }
+  const bool same = cand[0][0] == cand[1][0] && cand[0][1] == cand[1][1] && cand[0][2] == cand[1][2];
+  if (same) return VP_OK;
+  const size_t nv = (size_t)g->n[0] * g->n[1] * g->n[2];
+  float2* f = nullptr;
+  float2* u = nullptr;
+  VP_TRY_CUDA(cudaMallocAsync((void**)&f, nv * sizeof(float2), s));
+  cudaError_t e = cudaMallocAsync((void**)&u, nv * sizeof(float2), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(f, 0, nv * sizeof(float2), s);
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&t1);
+  float best = 1e30f;
+  for (int c = 0; c < 2 && e == cudaSuccess; ++c) {
+    vp_plan_opts o{};
+    for (int a = 0; a < 3; ++a) o.m[a] = cand[c][a];
+    vp_plan_t p = nullptr;
+    if (vp_plan(g, 1, f0, med, &o, s, &p) != VP_OK) continue;
+    p->khat_ready = true;  // timing only: the spectrum's values do not change the work
+    e = cudaMemsetAsync(p->khat, 0, (size_t)p->oct[0] * p->oct[1] * p->oct[2] * sizeof(float2), s);
+    float ms = 0.f;
+    for (int r = 0; r < 4 && e == cudaSuccess; ++r) {
+      if (r == 1) e = cudaEventRecord(t0, s);
+      if (e == cudaSuccess && vp_apply(p, f, u, s) != VP_OK) e = cudaErrorUnknown;
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(t1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+    vp_destroy(p);
+    if (e == cudaSuccess && ms < best) {
+      best = ms;
+      for (int a = 0; a < 3; ++a) best_m[a] = cand[c][a];
+    }
+  }
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
+  cudaFreeAsync(f, s);
+  if (u) cudaFreeAsync(u, s);
+  return e == cudaSuccess ? VP_OK : cuda_status(e);
+}
+
+}  // namespace

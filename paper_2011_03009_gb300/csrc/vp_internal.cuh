@@ -89,6 +89,27 @@ cudaError_t launch_col2_part2(const ColSweep& p, int dir, bool src, cudaStream_t
 cudaError_t launch_line2_part0(const LineSweep& p, int mode, cudaStream_t s);
 cudaError_t launch_line2_part1(const LineSweep& p, int mode, cudaStream_t s);
 cudaError_t launch_line2_part2(const LineSweep& p, int mode, cudaStream_t s);
+// Batched two-level sweeps: the parameters of up to kMaxBatch plans (and the first
+// CTA of each, offsets[i]) in the kernel parameter block.
+constexpr int kMaxBatch = 64;
+template <typename T>
+struct BatchParams {
+  int count;
+  int offsets[kMaxBatch + 1];
+  T item[kMaxBatch];
+};
+cudaError_t launch_col2_batch_part0(int L, const BatchParams<ColSweep>& bp, int total, int dir, bool src,
+                                    cudaStream_t s);
+cudaError_t launch_col2_batch_part1(int L, const BatchParams<ColSweep>& bp, int total, int dir, bool src,
+                                    cudaStream_t s);
+cudaError_t launch_col2_batch_part2(int L, const BatchParams<ColSweep>& bp, int total, int dir, bool src,
+                                    cudaStream_t s);
+cudaError_t launch_line2_batch_part0(int L, const LineSweep& first, int ni_max, const BatchParams<LineSweep>& bp,
+                                     int total, cudaStream_t s);
+cudaError_t launch_line2_batch_part1(int L, const LineSweep& first, int ni_max, const BatchParams<LineSweep>& bp,
+                                     int total, cudaStream_t s);
+cudaError_t launch_line2_batch_part2(int L, const LineSweep& first, int ni_max, const BatchParams<LineSweep>& bp,
+                                     int total, cudaStream_t s);
 // Dispatch on p.ax.fast: two-level engine or shared-memory radix passes.
 cudaError_t launch_col_any(const ColSweep& p, int dir, bool src, cudaStream_t s);
 cudaError_t launch_line_any(const LineSweep& p, int mode, cudaStream_t s);

@@ -226,7 +226,7 @@ def draw_batch_instances(count: int, seed: int, nmin: int = 96, nmax: int = 256,
         extent = math.inf
         for n in range(1, harmonics + 1):
             h = wavelength(WATER.c0, f0, n) / 6
-            hi = min(nmax, int(math.floor(extent / h)))
+            hi = nmax if math.isinf(extent) else min(nmax, int(math.floor(extent / h)))
             lo = min(nmin, hi)
             nv = int(rng.integers(lo, hi + 1))
             extent = nv * h

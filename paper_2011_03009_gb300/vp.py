@@ -25,6 +25,7 @@ VP_ERR_TIMEOUT = -7
 VP_ERR_UNSUPPORTED = -8
 VP_RESTRICT_ZERO_OUTSIDE = 1
 MAX_PASS = 8
+MAX_LOWER = 8
 
 
 class VpError(RuntimeError):
@@ -77,6 +78,10 @@ def _load():
         "vp_profile_read": (I, [P, ctypes.POINTER(D), ctypes.POINTER(I), I]),
         "vp_version": (ctypes.c_char_p, []),
         "vp_apply_static": (I, [ctypes.POINTER(vp_grid), I, D, ctypes.POINTER(vp_medium), P, P, P]),
+        "vp_batch_create": (I, [I, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P),
+                                ctypes.POINTER(P)]),
+        "vp_batch_run": (I, [P, P]),
+        "vp_batch_destroy": (I, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -190,6 +195,43 @@ class Plan:
     def close(self):
         if self._h and self._h.value:
             lib.vp_destroy(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """vp_batch_t: items (plan, f or lower fields, u) bound once, run with grouped launches."""
+
+    def __init__(self, plans, us, fs=None, lowers=None):
+        count = len(plans)
+        self._keep = (list(plans), list(us), fs, lowers)  # keep tensors and plans alive
+        P = ctypes.c_void_p
+        pa = (P * count)(*[p._h.value for p in plans])
+        ua = (P * count)(*[_ptr(t).value for t in us])
+        fa = None
+        if fs is not None:
+            fa = (P * count)(*[(_ptr(t).value if t is not None else None) for t in fs])
+        la = None
+        if lowers is not None:
+            flat = []
+            for i in range(count):
+                row = list(lowers[i] or [])
+                flat += [_ptr(t).value for t in row] + [None] * (MAX_LOWER - len(row))
+            la = (P * (count * MAX_LOWER))(*flat)
+        self._h = P(0)
+        _check(lib.vp_batch_create(count, pa, fa, la, ua, ctypes.byref(self._h)), "vp_batch_create")
+
+    def run(self, stream=None):
+        _check(lib.vp_batch_run(self._h, _stream(stream)), "vp_batch_run")
+
+    def close(self):
+        if self._h and self._h.value:
+            lib.vp_batch_destroy(self._h)
             self._h = ctypes.c_void_p(0)
 
     def __del__(self):
