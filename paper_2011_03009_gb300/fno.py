@@ -1,0 +1,306 @@
+"""Fourier-neural-operator surrogate for harmonics 2..5 (binding, training, data).
+
+Every step runs in libvp.so's kernels (include/vp_fno.h): the forward and backward
+passes on BF16 tensor cores, the loss and Adam.  This module only allocates device
+buffers (torch), orders the calls and generates training data with the plain
+volume-potential path (include/vp.h), which also judges the surrogate's error.
+
+Data: each sample is one seeded bowl configuration.  Harmonic n lives on an N^3 grid
+at lambda_n / 6 centred on the focus (equal voxel counts, domains shrinking with the
+wavelength); p1 is evaluated on the grid of harmonic 2 and on the focal box (the grid
+of harmonic 5); p_n = V_{k_n}[f_n] with lower harmonics restricted from their own
+grids; the targets are p2..p5 restricted to the box.  With s = max |p1| on the box,
+the network sees q1 = p1 / s and predicts q_n = p_n / (s^n kappa_n), where kappa_n is a
+fixed per-harmonic scale taken from the training set.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import math
+import time
+from typing import List, Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import synth
+from . import vp as _vp
+
+lib = _vp.lib
+P = ctypes.c_void_p
+
+
+class vp_fno_desc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("width", ctypes.c_int), ("hidden", ctypes.c_int), ("layers", ctypes.c_int),
+                ("modes", ctypes.c_int * 3)]
+
+
+_sig = {
+    "vp_fno_param_count": (ctypes.c_longlong, [ctypes.POINTER(vp_fno_desc)]),
+    "vp_fno_param_offsets": (ctypes.c_int, [ctypes.POINTER(vp_fno_desc), ctypes.POINTER(ctypes.c_longlong)]),
+    "vp_fno_workspace_bytes": (ctypes.c_longlong, [ctypes.POINTER(vp_fno_desc)]),
+    "vp_fno_forward": (ctypes.c_int, [ctypes.POINTER(vp_fno_desc), P, P, P, P, P, P]),
+    "vp_fno_loss": (ctypes.c_int, [ctypes.POINTER(vp_fno_desc), P, P, P, P]),
+    "vp_fno_backward": (ctypes.c_int, [ctypes.POINTER(vp_fno_desc), P, P, P, P, P, P, P]),
+    "vp_fno_adam": (ctypes.c_int, [ctypes.c_longlong, P, P, P, P, P, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                   ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, P]),
+    "vp_fno_to_bf16": (ctypes.c_int, [ctypes.c_longlong, P, P, P]),
+}
+for _n, (_r, _a) in _sig.items():
+    _f = getattr(lib, _n)
+    _f.restype = _r
+    _f.argtypes = _a
+
+
+def _check(st, where):
+    if st != 0:
+        raise _vp.VpError(st, where)
+
+
+def _p(t) -> P:
+    return P(t.data_ptr()) if t is not None else P(0)
+
+
+def _s(stream=None) -> P:
+    stream = stream or torch.cuda.current_stream()
+    return P(int(stream.cuda_stream))
+
+
+@dataclasses.dataclass(frozen=True)
+class FnoConfig:
+    n: int = 64
+    width: int = 48
+    hidden: int = 128
+    layers: int = 4
+    modes: tuple = (16, 16, 8)
+
+    def desc(self) -> vp_fno_desc:
+        d = vp_fno_desc()
+        d.n, d.width, d.hidden, d.layers = self.n, self.width, self.hidden, self.layers
+        for i in range(3):
+            d.modes[i] = int(self.modes[i])
+        return d
+
+
+class Fno:
+    """Parameters (FP32 master + BF16 copy), Adam state and workspace of one surrogate."""
+
+    def __init__(self, cfg: FnoConfig, seed: int = 0, device="cuda"):
+        self.cfg = cfg
+        self.d = cfg.desc()
+        n = lib.vp_fno_param_count(ctypes.byref(self.d))
+        if n < 0:
+            raise ValueError(f"invalid FNO configuration {cfg}")
+        self.count = int(n)
+        offs = (ctypes.c_longlong * (3 * cfg.layers + 7))()
+        _check(lib.vp_fno_param_offsets(ctypes.byref(self.d), offs), "vp_fno_param_offsets")
+        self.offsets = list(offs)
+        self.device = torch.device(device)
+        self.params = torch.zeros(self.count, dtype=torch.float32, device=self.device)
+        self.params_bf16 = torch.zeros(self.count, dtype=torch.bfloat16, device=self.device)
+        self.grads = torch.zeros_like(self.params)
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.step_count = 0
+        wsb = lib.vp_fno_workspace_bytes(ctypes.byref(self.d))
+        self.ws = torch.empty(int(wsb), dtype=torch.uint8, device=self.device)
+        self.sums = torch.zeros(8, dtype=torch.float32, device=self.device)
+        self.kappa = torch.ones(4, dtype=torch.float64)
+        self.set_params(self.init_params(seed))
+
+    # ---- parameter layout -----------------------------------------------------------
+    def slices(self):
+        o, L = self.offsets, self.cfg.layers
+        names = ["P", "bP"]
+        for l in range(L):
+            names += [f"R{l}", f"W{l}", f"b{l}"]
+        names += ["Q1", "bQ1", "Q2", "bQ2"]
+        return {nm: (o[i], o[i + 1]) for i, nm in enumerate(names)}
+
+    def init_params(self, seed: int) -> np.ndarray:
+        rng = np.random.default_rng(seed)
+        c = self.cfg
+        W, H = c.width, c.hidden
+        mx, my, mz = c.modes
+        flat = np.zeros(self.count, dtype=np.float64)
+        sl = self.slices()
+
+        def put(nm, arr):
+            a, b = sl[nm]
+            flat[a:b] = np.asarray(arr, dtype=np.float64).ravel()
+
+        put("P", rng.standard_normal((2, W)) / math.sqrt(2))
+        for l in range(c.layers):
+            put(f"R{l}", rng.standard_normal((mx, my, mz, W, W, 2)) / W)
+            put(f"W{l}", rng.standard_normal((W, W)) / math.sqrt(W))
+        put("Q1", rng.standard_normal((W, H)) / math.sqrt(W))
+        put("Q2", rng.standard_normal((H, 8)) / math.sqrt(H))
+        return flat
+
+    def set_params(self, flat: np.ndarray):
+        self.params.copy_(torch.from_numpy(np.asarray(flat, dtype=np.float32)))
+        _check(lib.vp_fno_to_bf16(self.count, _p(self.params), _p(self.params_bf16), _s()), "vp_fno_to_bf16")
+
+    def unpack(self, flat: np.ndarray) -> dict:
+        """Flat parameters -> dict in the oracle's naming (R complex)."""
+        c = self.cfg
+        sl = self.slices()
+        W, H = c.width, c.hidden
+        mx, my, mz = c.modes
+        g = lambda nm: flat[sl[nm][0]:sl[nm][1]]
+        out = {"P": g("P").reshape(2, W), "bP": g("bP").copy(), "R": [], "W": [], "b": [],
+               "Q1": g("Q1").reshape(W, H), "bQ1": g("bQ1").copy(), "Q2": g("Q2").reshape(H, 8),
+               "bQ2": g("bQ2").copy()}
+        for l in range(c.layers):
+            r = g(f"R{l}").reshape(mx, my, mz, W, W, 2)
+            out["R"].append(r[..., 0] + 1j * r[..., 1])
+            out["W"].append(g(f"W{l}").reshape(W, W))
+            out["b"].append(g(f"b{l}").copy())
+        return out
+
+    # ---- passes ---------------------------------------------------------------------
+    def forward(self, x: torch.Tensor, y: Optional[torch.Tensor] = None):
+        _check(lib.vp_fno_forward(ctypes.byref(self.d), _p(self.params), _p(self.params_bf16), _p(x), _p(y),
+                                  _p(self.ws), _s()), "vp_fno_forward")
+
+    def loss(self, target: torch.Tensor) -> torch.Tensor:
+        _check(lib.vp_fno_loss(ctypes.byref(self.d), _p(target), _p(self.sums), _p(self.ws), _s()), "vp_fno_loss")
+        return self.sums
+
+    def backward(self, x: torch.Tensor, target: torch.Tensor):
+        _check(lib.vp_fno_backward(ctypes.byref(self.d), _p(self.params), _p(self.params_bf16), _p(x), _p(target),
+                                   _p(self.grads), _p(self.ws), _s()), "vp_fno_backward")
+
+    def adam(self, lr: float, grad_scale: float = 1.0, b1=0.9, b2=0.999, eps=1e-8):
+        self.step_count += 1
+        c1 = 1 - b1 ** self.step_count
+        c2 = 1 - b2 ** self.step_count
+        _check(lib.vp_fno_adam(self.count, _p(self.params), _p(self.params_bf16), _p(self.grads), _p(self.m),
+                               _p(self.v), lr, b1, b2, eps, c1, c2, grad_scale, _s()), "vp_fno_adam")
+
+    def train_epoch(self, xs: Sequence[torch.Tensor], ts: Sequence[torch.Tensor], lr: float, batch: int,
+                    order: np.ndarray) -> float:
+        total = torch.zeros((), dtype=torch.float64, device=self.device)
+        for s0 in range(0, len(order), batch):
+            self.grads.zero_()
+            idx = order[s0:s0 + batch]
+            for i in idx:
+                self.forward(xs[i])
+                sums = self.loss(ts[i])
+                total += (sums[:4] / sums[4:]).mean().double()
+                self.backward(xs[i], ts[i])
+            self.adam(lr, grad_scale=1.0 / len(idx))
+        return float(total.item()) / len(order)
+
+    def predict(self, x: torch.Tensor, y: torch.Tensor):
+        self.forward(x, y)
+
+    def rel_l2(self, x: torch.Tensor, t: torch.Tensor) -> np.ndarray:
+        """Relative L2 error per harmonic (n = 2..5) of the prediction for one sample."""
+        self.forward(x)
+        s = self.loss(t).double().cpu().numpy()
+        return np.sqrt(s[:4] / s[4:])
+
+    def state(self) -> dict:
+        return {"cfg": dataclasses.asdict(self.cfg), "params": self.params.cpu(), "m": self.m.cpu(),
+                "v": self.v.cpu(), "step": self.step_count, "kappa": self.kappa.clone()}
+
+    def load_state(self, st: dict):
+        self.params.copy_(st["params"].to(self.device))
+        self.m.copy_(st["m"].to(self.device))
+        self.v.copy_(st["v"].to(self.device))
+        self.step_count = int(st["step"])
+        self.kappa = st["kappa"].clone()
+        _check(lib.vp_fno_to_bf16(self.count, _p(self.params), _p(self.params_bf16), _s()), "vp_fno_to_bf16")
+
+
+# ---- training data from the plain volume-potential path -----------------------------
+
+def harmonic_grids(bowl: synth.Bowl, n: int, medium=synth.WATER):
+    """N^3 grids at lambda_h / 6 centred on the focus for h = 2..5 (the box is h = 5)."""
+    return {h: synth.focus_grid(bowl, (n, n, n), h, medium) for h in range(2, 6)}
+
+
+class PlainCascade:
+    """Harmonics 2..5 of one bowl on the focal box by the plain GPU path (the judge)."""
+
+    def __init__(self, n: int, n_points: int = 512, medium=synth.WATER, device="cuda"):
+        self.n, self.n_points, self.medium, self.device = n, n_points, medium, torch.device(device)
+        c64 = torch.complex64
+        shape = (n, n, n)
+        self.f = {h: torch.empty(shape, dtype=c64, device=self.device) for h in range(1, 6)}
+        self.p1_box = torch.empty(shape, dtype=c64, device=self.device)
+        self.r = [torch.empty(shape, dtype=c64, device=self.device) for _ in range(4)]
+        self.box = {h: torch.empty(shape, dtype=c64, device=self.device) for h in range(2, 6)}
+
+    def run(self, bowl: synth.Bowl, seed: int):
+        """Returns (p1 on the box, {h: p_h on the box}) as complex64 CUDA tensors."""
+        vp, n = _vp, self.n
+        g = harmonic_grids(bowl, n, self.medium)
+        pts = torch.from_numpy(synth.sample_bowl_points(bowl, self.n_points, seed)).to(self.device)
+        vp.vp_incident_field(g[2], pts, bowl, self.medium, self.f[1])
+        vp.vp_incident_field(g[5], pts, bowl, self.medium, self.p1_box)
+        home = {1: g[2]}
+        for h in range(2, 6):
+            plan = vp.vp_plan(g[h], h, bowl.f0, self.medium)
+            plan.kernel_fft()
+            lower = []
+            for m in range(1, h):
+                if home[m] is g[h]:
+                    lower.append(self.f[m])
+                else:
+                    vp.vp_restrict_to_nested_box(home[m], self.f[m], g[h], self.r[m - 1])
+                    lower.append(self.r[m - 1])
+            plan.source_assemble(lower)
+            plan.apply(None, self.f[h])
+            home[h] = g[h]
+            plan.close()
+        for h in range(2, 6):
+            if h == 5:
+                self.box[h].copy_(self.f[5])
+            else:
+                vp.vp_restrict_to_nested_box(g[h], self.f[h], g[5], self.box[h])
+        return self.p1_box, self.box
+
+
+def draw_bowls(count: int, seed: int) -> List[synth.Bowl]:
+    """Seeded bowls (focal length 8-15 cm, aperture 3-7.5 cm, 0.8-1.5 MHz, 0.5-3 MPa)."""
+    return [b.bowl for b in synth.draw_batch_instances(count, seed, harmonics=1)]
+
+
+def encode(p1: torch.Tensor, harm: dict, kappa=None):
+    """(x, target, s): normalised network input and target for one sample."""
+    s = float(p1.abs().max().item())
+    x = torch.view_as_real(p1 / s).reshape(-1, 2).float().contiguous()
+    tg = []
+    for h in range(2, 6):
+        k = 1.0 if kappa is None else float(kappa[h - 2])
+        tg.append(torch.view_as_real(harm[h] / (s ** h * k)).reshape(-1, 2))
+    t = torch.cat(tg, dim=1).float().contiguous()
+    return x, t, s
+
+
+def make_dataset(count: int, seed: int, n: int, n_points: int = 512, kappa=None):
+    """Generate `count` samples; returns (xs, ts, scales, kappa, seconds)."""
+    casc = PlainCascade(n, n_points)
+    bowls = draw_bowls(count, seed)
+    raw = []
+    t0 = time.perf_counter()
+    for i, b in enumerate(bowls):
+        p1, harm = casc.run(b, seed * 100003 + i)
+        s = float(p1.abs().max().item())
+        raw.append((p1.clone(), {h: harm[h].clone() for h in harm}, s))
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    if kappa is None:
+        mags = np.array([[float((r[1][h] / r[2] ** h).abs().pow(2).mean().sqrt().item()) for h in range(2, 6)]
+                         for r in raw])
+        kappa = torch.from_numpy(np.median(mags, axis=0))
+    xs, ts, ss = [], [], []
+    for p1, harm, s in raw:
+        x, t, _ = encode(p1, harm, kappa)
+        xs.append(x)
+        ts.append(t)
+        ss.append(s)
+    return xs, ts, ss, kappa, sec
