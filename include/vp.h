@@ -124,6 +124,18 @@ VP_API int vp_plan(const vp_grid* g, int harmonic_n, double f0_hz, const vp_medi
  * first (pending work that uses the plan completes).  NULL is accepted. */
 VP_API int vp_destroy(vp_plan_t p);
 
+/* Point an existing plan at another grid of the same voxel counts, harmonic, f0 and
+ * medium (new spacing, origin, k_n, C_n and self cell), keeping its embedding size,
+ * FFT schedule, tables and device workspace: a sequence of problems with equal N
+ * (e.g. one instance after another at 6 voxels per wavelength) then needs no device
+ * allocation.  The kernel spectrum becomes stale: call vp_kernel_fft before the next
+ * vp_apply, and vp_source_assemble again.  Host-only; work already enqueued on the
+ * plan keeps the state it was enqueued with only when it runs on the stream the next
+ * vp_kernel_fft uses.  A batch created from the plan before the call refuses to run
+ * afterwards (VP_ERR_STATE): create it again.  Errors: VP_ERR_ARG (as vp_plan), VP_ERR_UNSUPPORTED (harmonic
+ * > 9), VP_ERR_SIZE (g->n differs from the plan's). */
+VP_API int vp_plan_retarget(vp_plan_t p, const vp_grid* g, int harmonic_n, double f0_hz, const vp_medium* m);
+
 /* Fill *info.  Errors: VP_ERR_ARG. */
 VP_API int vp_plan_get_info(vp_plan_t p, vp_plan_info* info);
 

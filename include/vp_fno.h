@@ -9,9 +9,11 @@
  * n = 2..5), and p_n = s^n q_n exactly undoes the scaling.
  *
  * Architecture (Fourier neural operator, L layers, width W, projection width H):
- *   h0 = x P + bP                                            (2 -> W)
+ *   h0 = phi(x) P + bP                                       (10 -> W)
  *   t_l = K_l(h_l) + h_l W_l + b_l,  h_{l+1} = GELU(t_l) for l < L-1, else t_l
  *   y = GELU(h_L Q1 + bQ1) Q2 + bQ2                          (W -> H -> 8)
+ * phi(x) = (Re, Im of q^k, k = 1..5) with q = x0 + i x1: since p_n grows like p1^n times
+ * a slowly varying envelope, the lift sees the powers of the normalised fundamental.
  * K_l: real 3-D DFT of each channel, keep kx in the lowest modes[0] (half non-negative,
  * half negative), ky likewise with modes[1], kz in [0, modes[2]); multiply every kept
  * mode by a complex W x W matrix R_l; inverse real DFT with the remaining modes zero
@@ -29,7 +31,7 @@
  * P, bP, (R_l, W_l, b_l) for each layer, Q1, bQ1, Q2, bQ2 and the total count.
  * R_l is [mx][my][mz][W][W][2] (kept modes in kx-slot, ky-slot, kz order; slot j < m/2
  * is frequency j, else N - m + j; complex as Re, Im); W_l is [W][W] (in, out); P is
- * [2][W]; Q1 is [W][H]; Q2 is [H][8].
+ * [10][W] (feature rows in phi's order); Q1 is [W][H]; Q2 is [H][8].
  * All pointers are device pointers; every call is asynchronous on `stream`.
  */
 #ifndef VP_FNO_H
@@ -42,6 +44,8 @@ extern "C" {
 #endif
 
 #define VP_FNO_MAX_LAYERS 8
+#define VP_FNO_POWERS 5                 /* powers of q in the input features */
+#define VP_FNO_IN (2 * VP_FNO_POWERS)   /* input features per voxel          */
 
 typedef struct vp_fno_desc {
     int n;          /* box voxels per axis, 4..256                         */
@@ -66,6 +70,13 @@ VP_API long long vp_fno_workspace_bytes(const vp_fno_desc* d);
  * activations in ws for vp_fno_loss / vp_fno_backward.  Errors: VP_ERR_ARG, VP_ERR_CUDA. */
 VP_API int vp_fno_forward(const vp_fno_desc* d, const float* params, const void* params_bf16, const float* x,
                           float* y, void* ws, vp_stream_t stream);
+
+/* Inference: y (FP32 [N^3][8], required) from x, the same function as vp_fno_forward but
+ * keeping no activations (vp_fno_loss / vp_fno_backward must not follow it) and with the
+ * projection fused into one kernel.  ws as for vp_fno_forward.
+ * Errors: VP_ERR_ARG, VP_ERR_CUDA. */
+VP_API int vp_fno_infer(const vp_fno_desc* d, const float* params, const void* params_bf16, const float* x,
+                        float* y, void* ws, vp_stream_t stream);
 
 /* Loss of the last forward pass against target: sums8[n] = ||y_n - q_n||^2 and
  * sums8[4 + n] = ||q_n||^2, n = 0..3 (device FP32[8], may be NULL; the sums are also

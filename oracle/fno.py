@@ -5,8 +5,9 @@ real channels: Re, Im) to the normalised harmonics q_n = p_n / s^n, n = 2..5 (ei
 channels).  The cascade makes p_n homogeneous of degree n in p1 (Eq. 2.6), so the
 scale s = max |p1| factors out exactly and the network only learns the shape.
 
-Architecture (a standard Fourier neural operator):
-  h0 = x P + bP                                            lift 2 -> W
+Architecture (a Fourier neural operator with power features at the input):
+  phi(x) = (Re q, Im q, Re q^2, Im q^2, ..., Re q^5, Im q^5),  q = x0 + i x1
+  h0 = phi(x) P + bP                                       lift 10 -> W
   t_l = SpecConv_l(h_l) + h_l W_l + b_l,  h_{l+1} = GELU(t_l) for l < L-1, else t_l
   y = GELU(h_L Q1 + bQ1) Q2 + bQ2                          project W -> H -> 8
 SpecConv: real 3-D FFT (rfftn over x, y, z), keep kx, ky in the lowest mx, my (half
@@ -46,9 +47,22 @@ def spectral_conv(h: np.ndarray, R: np.ndarray, modes) -> np.ndarray:
     return np.fft.irfftn(full, s=(N, N, N), axes=(0, 1, 2))
 
 
+POWERS = 5
+
+
+def features(x: np.ndarray) -> np.ndarray:
+    """(..., 2) real pairs -> (..., 10): Re and Im of q^k, k = 1..5, q = x0 + i x1."""
+    q = x[..., 0] + 1j * x[..., 1]
+    out = []
+    for k in range(1, POWERS + 1):
+        qk = q ** k
+        out += [qk.real, qk.imag]
+    return np.stack(out, axis=-1)
+
+
 def forward(params: dict, x: np.ndarray, modes) -> np.ndarray:
     """x: (N, N, N, 2) -> (N, N, N, 8)."""
-    h = x @ params["P"] + params["bP"]
+    h = features(x) @ params["P"] + params["bP"]
     L = len(params["R"])
     for l in range(L):
         t = spectral_conv(h, params["R"][l], modes) + h @ params["W"][l] + params["b"][l]
@@ -77,7 +91,7 @@ def init_params(N: int, width: int, hidden: int, layers: int, modes, seed: int) 
         return rng.standard_normal(shape) * scale
 
     return {
-        "P": nrm(2, W, scale=1.0 / math.sqrt(2)), "bP": np.zeros(W),
+        "P": nrm(2 * POWERS, W, scale=1.0 / math.sqrt(2 * POWERS)), "bP": np.zeros(W),
         "R": [(nrm(mx, my, mz, W, W, scale=1.0 / W) + 1j * nrm(mx, my, mz, W, W, scale=1.0 / W))
               for _ in range(layers)],
         "W": [nrm(W, W, scale=1.0 / math.sqrt(W)) for _ in range(layers)],

@@ -58,6 +58,7 @@ struct vp_plan_s {
   unsigned long long bytes = 0;
   bool khat_ready = false;
   bool staged = false;
+  unsigned long long generation = 0;  // bumped by vp_plan_retarget
   bool prof_on = false;
   std::vector<ProfRec> prof;
   size_t prof_used = 0;
@@ -452,6 +453,7 @@ struct BatchGroup {
 struct vp_batch_s {
   int count = 0;
   std::vector<vp_plan_t> plans;
+  std::vector<unsigned long long> generation;  // of each plan when the batch was built
   std::vector<const void*> f;
   std::vector<std::vector<const void*>> lower;
   std::vector<void*> u;
@@ -509,6 +511,59 @@ int build_group(vp_batch_s* b, BatchGroup& g) {
 int autotune_m(const vp_grid* g, double f0, const vp_medium* med, cudaStream_t s, int* best_m);
 
 }  // namespace
+
+// Physics of a plan: spacing, origin, k_n = 2 pi n f0 / c0 + i alpha(n f0) (Section 2),
+// C_n of Eq. 2.6 with the minus sign of Eq. 3.2 folded in, and the self-cell integral of
+// Eq. 3.9.  Marks the kernel spectrum stale.
+static void set_physics(vp_plan_s* p, const vp_grid* g, int harmonic_n, double f0_hz, const vp_medium* med) {
+  for (int a = 0; a < 3; ++a) p->origin[a] = g->origin[a];
+  p->h = g->h;
+  p->harmonic = harmonic_n;
+  p->f0 = f0_hz;
+  p->med = *med;
+  const double f = harmonic_n * f0_hz;
+  p->kr = 2.0 * kPi * f / med->c0;
+  p->ki = attenuation(f, *med);
+  const double omega = 2.0 * kPi * f0_hz;
+  p->cn = -med->beta * omega * omega * harmonic_n * harmonic_n / (2.0 * med->rho0 * std::pow(med->c0, 4));
+  const std::complex<double> sc = self_cell_host({p->kr, p->ki}, p->h);
+  p->self_re = sc.real();
+  p->self_im = sc.imag();
+  p->khat_ready = false;
+  p->staged = false;
+}
+
+// Stream-ordered pool of this library for the kernel-spectrum scratch cube (8 M^3
+// bytes per vp_kernel_fft).  Freed blocks up to kScratchKeep bytes stay reserved across
+// synchronisations, so a sequence of vp_kernel_fft calls of one size maps device memory
+// once; larger cubes go back to the driver at the next synchronisation.  Null if the
+// device has no memory-pool support (the default pool is used then).
+constexpr unsigned long long kScratchKeep = 2ULL << 30;
+
+static cudaMemPool_t scratch_pool(int dev) {
+  static std::mutex mu;
+  static std::map<int, cudaMemPool_t> pools;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = pools.find(dev);
+  if (it != pools.end()) return it->second;
+  cudaMemPool_t pool = nullptr;
+  int supported = 0;
+  if (cudaDeviceGetAttribute(&supported, cudaDevAttrMemoryPoolsSupported, dev) == cudaSuccess && supported) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    if (cudaMemPoolCreate(&pool, &props) == cudaSuccess) {
+      unsigned long long keep = kScratchKeep;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    } else {
+      pool = nullptr;
+      cudaGetLastError();
+    }
+  }
+  pools[dev] = pool;
+  return pool;
+}
 
 extern "C" {
 
@@ -601,18 +656,7 @@ VP_API int vp_plan(const vp_grid* g, int harmonic_n, double f0_hz, const vp_medi
     p->fast[a] = fast[a];
     for (int i = 0; i < vp::kMaxPass; ++i) p->radix[a][i] = radix[a][i];
   }
-  p->h = g->h;
-  p->harmonic = harmonic_n;
-  p->f0 = f0_hz;
-  p->med = *med;
-  const double f = harmonic_n * f0_hz;
-  p->kr = 2.0 * kPi * f / med->c0;
-  p->ki = attenuation(f, *med);
-  const double omega = 2.0 * kPi * f0_hz;
-  p->cn = -med->beta * omega * omega * harmonic_n * harmonic_n / (2.0 * med->rho0 * std::pow(med->c0, 4));
-  const std::complex<double> sc = self_cell_host({p->kr, p->ki}, p->h);
-  p->self_re = sc.real();
-  p->self_im = sc.imag();
+  set_physics(p, g, harmonic_n, f0_hz, med);
 
   int st = VP_OK;
   std::vector<int> hpos[3];
@@ -644,6 +688,17 @@ VP_API int vp_destroy(vp_plan_t p) {
   return cuda_status(e);
 }
 
+VP_API int vp_plan_retarget(vp_plan_t p, const vp_grid* g, int harmonic_n, double f0_hz, const vp_medium* med) {
+  if (!p || !grid_ok(g) || !medium_ok(med) || harmonic_n < 1 || !(f0_hz > 0) || !std::isfinite(f0_hz))
+    return VP_ERR_ARG;
+  if (harmonic_n - 1 > vp::kMaxLower) return VP_ERR_UNSUPPORTED;
+  for (int a = 0; a < 3; ++a)
+    if (g->n[a] != p->n[a]) return VP_ERR_SIZE;
+  set_physics(p, g, harmonic_n, f0_hz, med);
+  ++p->generation;
+  return VP_OK;
+}
+
 VP_API int vp_plan_get_info(vp_plan_t p, vp_plan_info* info) {
   if (!p || !info) return VP_ERR_ARG;
   std::memset(info, 0, sizeof(*info));
@@ -670,7 +725,12 @@ VP_API int vp_kernel_fft(vp_plan_t p, vp_stream_t stream) {
   const int Mx = p->m[0], My = p->m[1], Mz = p->m[2];
   const size_t total = (size_t)Mx * My * Mz;
   float2* tmp = nullptr;
-  VP_TRY_CUDA(cudaMallocAsync((void**)&tmp, total * sizeof(float2), s));
+  cudaMemPool_t pool = scratch_pool(p->dev);
+  if (pool) {
+    VP_TRY_CUDA(cudaMallocFromPoolAsync((void**)&tmp, total * sizeof(float2), pool, s));
+  } else {
+    VP_TRY_CUDA(cudaMallocAsync((void**)&tmp, total * sizeof(float2), s));
+  }
   cudaError_t e = vp::launch_kernel_lattice(tmp, p->n, p->m, p->h, p->kr, p->ki, s);
   if (e == cudaSuccess) {
     ColSweep c{};  // x, in place over the full cube
@@ -819,6 +879,7 @@ VP_API int vp_batch_create(int count, const vp_plan_t* plans, const void* const*
   if (!b) return VP_ERR_NOMEM;
   b->count = count;
   b->plans.assign(plans, plans + count);
+  for (int i = 0; i < count; ++i) b->generation.push_back(plans[i]->generation);
   b->f.resize(count, nullptr);
   b->lower.resize(count);
   b->u.assign(u, u + count);
@@ -874,7 +935,7 @@ VP_API int vp_batch_create(int count, const vp_plan_t* plans, const void* const*
 VP_API int vp_batch_run(vp_batch_t b, vp_stream_t stream) {
   if (!b) return VP_ERR_ARG;
   for (int i = 0; i < b->count; ++i)
-    if (!b->plans[i]->khat_ready) return VP_ERR_STATE;
+    if (!b->plans[i]->khat_ready || b->plans[i]->generation != b->generation[i]) return VP_ERR_STATE;
   cudaStream_t s = (cudaStream_t)stream;
   for (auto& g : b->groups) {
     for (auto& chp : g.chunks) {

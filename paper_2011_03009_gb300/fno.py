@@ -29,6 +29,7 @@ from . import vp as _vp
 
 lib = _vp.lib
 P = ctypes.c_void_p
+N_IN = 10  # input features per voxel (VP_FNO_IN): Re, Im of q^1..q^5
 
 
 class vp_fno_desc(ctypes.Structure):
@@ -41,6 +42,7 @@ _sig = {
     "vp_fno_param_offsets": (ctypes.c_int, [ctypes.POINTER(vp_fno_desc), ctypes.POINTER(ctypes.c_longlong)]),
     "vp_fno_workspace_bytes": (ctypes.c_longlong, [ctypes.POINTER(vp_fno_desc)]),
     "vp_fno_forward": (ctypes.c_int, [ctypes.POINTER(vp_fno_desc), P, P, P, P, P, P]),
+    "vp_fno_infer": (ctypes.c_int, [ctypes.POINTER(vp_fno_desc), P, P, P, P, P, P]),
     "vp_fno_loss": (ctypes.c_int, [ctypes.POINTER(vp_fno_desc), P, P, P, P]),
     "vp_fno_backward": (ctypes.c_int, [ctypes.POINTER(vp_fno_desc), P, P, P, P, P, P, P]),
     "vp_fno_adam": (ctypes.c_int, [ctypes.c_longlong, P, P, P, P, P, ctypes.c_float, ctypes.c_float, ctypes.c_float,
@@ -130,7 +132,7 @@ class Fno:
             a, b = sl[nm]
             flat[a:b] = np.asarray(arr, dtype=np.float64).ravel()
 
-        put("P", rng.standard_normal((2, W)) / math.sqrt(2))
+        put("P", rng.standard_normal((N_IN, W)) / math.sqrt(N_IN))
         for l in range(c.layers):
             put(f"R{l}", rng.standard_normal((mx, my, mz, W, W, 2)) / W)
             put(f"W{l}", rng.standard_normal((W, W)) / math.sqrt(W))
@@ -149,7 +151,7 @@ class Fno:
         W, H = c.width, c.hidden
         mx, my, mz = c.modes
         g = lambda nm: flat[sl[nm][0]:sl[nm][1]]
-        out = {"P": g("P").reshape(2, W), "bP": g("bP").copy(), "R": [], "W": [], "b": [],
+        out = {"P": g("P").reshape(N_IN, W), "bP": g("bP").copy(), "R": [], "W": [], "b": [],
                "Q1": g("Q1").reshape(W, H), "bQ1": g("bQ1").copy(), "Q2": g("Q2").reshape(H, 8),
                "bQ2": g("bQ2").copy()}
         for l in range(c.layers):
@@ -193,8 +195,13 @@ class Fno:
             self.adam(lr, grad_scale=1.0 / len(idx))
         return float(total.item()) / len(order)
 
+    def infer(self, x: torch.Tensor, y: torch.Tensor):
+        """Inference only (no activations kept): y [N^3][8] from x [N^3][2]."""
+        _check(lib.vp_fno_infer(ctypes.byref(self.d), _p(self.params), _p(self.params_bf16), _p(x), _p(y),
+                                _p(self.ws), _s()), "vp_fno_infer")
+
     def predict(self, x: torch.Tensor, y: torch.Tensor):
-        self.forward(x, y)
+        self.infer(x, y)
 
     def rel_l2(self, x: torch.Tensor, t: torch.Tensor) -> np.ndarray:
         """Relative L2 error per harmonic (n = 2..5) of the prediction for one sample."""
@@ -233,17 +240,32 @@ class PlainCascade:
         self.p1_box = torch.empty(shape, dtype=c64, device=self.device)
         self.r = [torch.empty(shape, dtype=c64, device=self.device) for _ in range(4)]
         self.box = {h: torch.empty(shape, dtype=c64, device=self.device) for h in range(2, 6)}
+        self.plans = {}   # one plan per harmonic, re-targeted per instance (equal N)
 
     def run(self, bowl: synth.Bowl, seed: int):
         """Returns (p1 on the box, {h: p_h on the box}) as complex64 CUDA tensors."""
-        vp, n = _vp, self.n
-        g = harmonic_grids(bowl, n, self.medium)
+        self.incident(bowl, seed)
+        return self.p1_box, self.harmonics(bowl)
+
+    def incident(self, bowl: synth.Bowl, seed: int):
+        """p1 (Eq. 3.10) on the grid of harmonic 2 and on the box, from seeded bowl points."""
+        vp = _vp
+        g = harmonic_grids(bowl, self.n, self.medium)
         pts = torch.from_numpy(synth.sample_bowl_points(bowl, self.n_points, seed)).to(self.device)
         vp.vp_incident_field(g[2], pts, bowl, self.medium, self.f[1])
         vp.vp_incident_field(g[5], pts, bowl, self.medium, self.p1_box)
+
+    def harmonics(self, bowl: synth.Bowl):
+        """p2..p5 restricted to the box, from the p1 fields of the last incident() call."""
+        vp = _vp
+        g = harmonic_grids(bowl, self.n, self.medium)
         home = {1: g[2]}
         for h in range(2, 6):
-            plan = vp.vp_plan(g[h], h, bowl.f0, self.medium)
+            plan = self.plans.get(h)
+            if plan is None:
+                plan = self.plans[h] = vp.vp_plan(g[h], h, bowl.f0, self.medium)
+            else:
+                plan.retarget(g[h], h, bowl.f0, self.medium)
             plan.kernel_fft()
             lower = []
             for m in range(1, h):
@@ -255,13 +277,12 @@ class PlainCascade:
             plan.source_assemble(lower)
             plan.apply(None, self.f[h])
             home[h] = g[h]
-            plan.close()
         for h in range(2, 6):
             if h == 5:
                 self.box[h].copy_(self.f[5])
             else:
                 vp.vp_restrict_to_nested_box(g[h], self.f[h], g[5], self.box[h])
-        return self.p1_box, self.box
+        return self.box
 
 
 def draw_bowls(count: int, seed: int) -> List[synth.Bowl]:
@@ -276,31 +297,42 @@ def encode(p1: torch.Tensor, harm: dict, kappa=None):
     tg = []
     for h in range(2, 6):
         k = 1.0 if kappa is None else float(kappa[h - 2])
-        tg.append(torch.view_as_real(harm[h] / (s ** h * k)).reshape(-1, 2))
+        # p_h / s^h is ~1e-27 Pa^(1-h): scale in complex128, store the O(1) result in FP32
+        q = harm[h].to(torch.complex128) / (s ** h * k)
+        tg.append(torch.view_as_real(q.to(torch.complex64)).reshape(-1, 2))
     t = torch.cat(tg, dim=1).float().contiguous()
     return x, t, s
 
 
-def make_dataset(count: int, seed: int, n: int, n_points: int = 512, kappa=None):
-    """Generate `count` samples; returns (xs, ts, scales, kappa, seconds)."""
+def make_dataset(count: int, seed: int, n: int, n_points: int = 512, kappa=None, kappa_samples: int = 16):
+    """Generate `count` samples; returns (xs, ts, scales, kappa, seconds).  Without a
+    given kappa it is the per-harmonic median RMS of p_n / s^n over the first
+    `kappa_samples` samples; samples are encoded as they are made (one copy in memory)."""
     casc = PlainCascade(n, n_points)
     bowls = draw_bowls(count, seed)
-    raw = []
+    xs, ts, ss, pending = [], [], [], []
     t0 = time.perf_counter()
     for i, b in enumerate(bowls):
         p1, harm = casc.run(b, seed * 100003 + i)
         s = float(p1.abs().max().item())
-        raw.append((p1.clone(), {h: harm[h].clone() for h in harm}, s))
-    torch.cuda.synchronize()
-    sec = time.perf_counter() - t0
-    if kappa is None:
-        mags = np.array([[float((r[1][h] / r[2] ** h).abs().pow(2).mean().sqrt().item()) for h in range(2, 6)]
-                         for r in raw])
-        kappa = torch.from_numpy(np.median(mags, axis=0))
-    xs, ts, ss = [], [], []
-    for p1, harm, s in raw:
+        if kappa is None:
+            pending.append((p1.clone(), {h: harm[h].clone() for h in harm}, s))
+            if len(pending) < min(kappa_samples, count):
+                continue
+            mags = np.array([[float((r[1][h].to(torch.complex128) / r[2] ** h).abs().pow(2).mean().sqrt().item())
+                              for h in range(2, 6)] for r in pending])
+            kappa = torch.from_numpy(np.median(mags, axis=0))
+            for q1, hq, sq in pending:
+                x, t, _ = encode(q1, hq, kappa)
+                xs.append(x)
+                ts.append(t)
+                ss.append(sq)
+            pending = []
+            continue
         x, t, _ = encode(p1, harm, kappa)
         xs.append(x)
         ts.append(t)
         ss.append(s)
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
     return xs, ts, ss, kappa, sec

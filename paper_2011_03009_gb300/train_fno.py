@@ -1,0 +1,127 @@
+"""Train and evaluate the FNO surrogate of harmonics 2..5 on fields from the plain path.
+
+    python -m paper_2011_03009_gb300.train_fno --n 128 --train 2000 --test 200 --epochs 15 \
+        --json results.json [--checkpoint fno.pt]
+
+Training set: seeded bowls (seed 5: focal length 8-15 cm, aperture 3-7.5 cm, 0.8-1.5 MHz,
+0.5-3 MPa); held-out set: seed 6.  Each sample's targets are p2..p5 from the plain
+volume-potential cascade (PlainCascade), its input p1 on the focal box.  Prints one JSON
+line (and writes it to --json) with the held-out relative L2 error per harmonic, the
+fraction of held-out samples whose worst harmonic exceeds the threshold (those fall back
+to the plain path) and the measured times per field of every stage.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import sys
+import time
+
+import numpy as np
+import torch
+
+from . import fno as F
+
+
+def _time_ms(fn, reps: int) -> float:
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    fn(0)
+    torch.cuda.synchronize()
+    a.record()
+    for i in range(reps):
+        fn(i)
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def stage_times(model: F.Fno, casc: F.PlainCascade, bowls, reps: int = 8) -> dict:
+    """Per-field device times (ms): incident field on one N^3 grid, the plain cascade
+    from p1 (kernel spectra, restrictions, sources, potentials), surrogate inference."""
+    n = casc.n
+    x = torch.zeros((n ** 3, 2), dtype=torch.float32, device="cuda")
+    y = torch.empty((n ** 3, 8), dtype=torch.float32, device="cuda")
+    casc.incident(bowls[0], 0)
+    t_inc = _time_ms(lambda i: casc.incident(bowls[i % len(bowls)], i), reps) / 2.0  # two grids per call
+    t_harm = _time_ms(lambda i: casc.harmonics(bowls[i % len(bowls)]), reps)
+    t_inf = _time_ms(lambda i: model.infer(x, y), reps)
+    return {"incident_ms_per_grid": t_inc, "plain_cascade_ms": t_harm, "surrogate_infer_ms": t_inf}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--width", type=int, default=48)
+    ap.add_argument("--hidden", type=int, default=128)
+    ap.add_argument("--layers", type=int, default=4)
+    ap.add_argument("--modes", type=int, nargs=3, default=None)
+    ap.add_argument("--train", type=int, default=2000)
+    ap.add_argument("--test", type=int, default=200)
+    ap.add_argument("--epochs", type=int, default=15)
+    ap.add_argument("--batch", type=int, default=4)
+    ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--points", type=int, default=512)
+    ap.add_argument("--threshold", type=float, default=1e-2)
+    ap.add_argument("--json", default=None)
+    ap.add_argument("--checkpoint", default=None)
+    a = ap.parse_args(argv)
+    torch.cuda.set_device(0)
+    modes = tuple(a.modes) if a.modes else (a.n // 4, a.n // 4, a.n // 8)
+    cfg = F.FnoConfig(n=a.n, width=a.width, hidden=a.hidden, layers=a.layers, modes=modes)
+    model = F.Fno(cfg, seed=0)
+    t0 = time.perf_counter()
+    xs, ts, _, kappa, t_gen = F.make_dataset(a.train, 5, a.n, a.points)
+    model.kappa = kappa
+    xv, tv, _, _, t_gen2 = F.make_dataset(a.test, 6, a.n, a.points, kappa)
+    print(f"data {a.train}+{a.test} samples in {time.perf_counter() - t0:.1f}s", file=sys.stderr, flush=True)
+    rng = np.random.default_rng(1)
+    history = []
+    t0 = time.perf_counter()
+    for ep in range(a.epochs):
+        lr = a.lr * 0.5 * (1 + math.cos(math.pi * ep / max(1, a.epochs)))  # cosine schedule
+        loss = model.train_epoch(xs, ts, lr, a.batch, rng.permutation(a.train))
+        history.append(loss)
+        print(f"epoch {ep} loss {loss:.4e} lr {lr:.2e} {time.perf_counter() - t0:.1f}s", file=sys.stderr, flush=True)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    if a.checkpoint:
+        torch.save(model.state(), a.checkpoint)
+    train_err = np.array([model.rel_l2(x, t) for x, t in zip(xs[:a.test], ts[:a.test])])
+    errs = np.array([model.rel_l2(x, t) for x, t in zip(xv, tv)])
+    worst = errs.max(axis=1)
+    del xs, ts
+    casc = F.PlainCascade(a.n, a.points)
+    times = stage_times(model, casc, F.draw_bowls(8, 7))
+    fb = float(np.mean(worst > a.threshold))
+    inc, harm, inf = times["incident_ms_per_grid"], times["plain_cascade_ms"], times["surrogate_infer_ms"]
+    res = {
+        "n": a.n, "width": a.width, "hidden": a.hidden, "layers": a.layers, "modes": list(modes),
+        "train": a.train, "test": a.test, "epochs": a.epochs, "batch": a.batch, "params": model.count,
+        "loss_history": history,
+        "heldout_rel_l2_median": np.median(errs, axis=0).tolist(),
+        "heldout_rel_l2_mean": errs.mean(axis=0).tolist(),
+        "heldout_rel_l2_p90": np.quantile(errs, 0.9, axis=0).tolist(),
+        "train_rel_l2_mean": train_err.mean(axis=0).tolist(),
+        "threshold": a.threshold, "fallback_rate": fb,
+        "data_gen_s": t_gen + t_gen2, "train_s": t_train,
+        **times,
+        # fields/s from p1 already on the device (the cascade vs the surrogate), and with
+        # the incident field included (plain: p1 on the grid of harmonic 2; surrogate: p1
+        # on the box, plus the whole plain path again for the fallback share)
+        "fields_per_s_from_p1": {"plain": 1e3 / harm, "surrogate": 1e3 / inf,
+                                 "surrogate_with_fallback": 1e3 / (inf + fb * harm)},
+        "fields_per_s_with_incident": {"plain": 1e3 / (inc + harm), "surrogate": 1e3 / (inc + inf),
+                                       "surrogate_with_fallback": 1e3 / (inc + inf + fb * (inc + harm))},
+    }
+    line = json.dumps(res)
+    print(line, flush=True)
+    if a.json:
+        with open(a.json, "w") as f:
+            f.write(line + "\n")
+    return model, res
+
+
+if __name__ == "__main__":
+    main()

@@ -65,6 +65,7 @@ def _load():
         "vp_plan": (I, [ctypes.POINTER(vp_grid), I, D, ctypes.POINTER(vp_medium), ctypes.POINTER(vp_plan_opts), P,
                         ctypes.POINTER(P)]),
         "vp_destroy": (I, [P]),
+        "vp_plan_retarget": (I, [P, ctypes.POINTER(vp_grid), I, D, ctypes.POINTER(vp_medium)]),
         "vp_plan_get_info": (I, [P, ctypes.POINTER(vp_plan_info)]),
         "vp_kernel_fft": (I, [P, P]),
         "vp_kernel_spectrum_get": (I, [P, P, P]),
@@ -160,6 +161,14 @@ class Plan:
                          _stream(stream) if autotune else ctypes.c_void_p(0), ctypes.byref(self._h))
         _check(st, "vp_plan")
         self.n = tuple(int(v) for v in g.n)
+
+    def retarget(self, grid, harmonic: int, f0: float, medium):
+        """vp_plan_retarget: same voxel counts, new spacing/origin/harmonic/f0/medium."""
+        g = grid if isinstance(grid, vp_grid) else grid_of(grid)
+        med = medium if isinstance(medium, vp_medium) else make_medium(medium)
+        _check(lib.vp_plan_retarget(self._h, ctypes.byref(g), int(harmonic), float(f0), ctypes.byref(med)),
+               "vp_plan_retarget")
+        self.grid, self._g, self.harmonic = grid, g, int(harmonic)
 
     def info(self) -> vp_plan_info:
         inf = vp_plan_info()

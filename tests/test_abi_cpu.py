@@ -7,13 +7,16 @@ import re
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "vp.h")
+INCLUDE = os.path.join(ROOT, "include")
+HEADERS = sorted(os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h"))
 
 
 def _declared_functions():
-    text = open(HEADER).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"VP_API\s+[\w\s\*]+?\b(vp_\w+)\s*\(", text)))
+    names = set()
+    for h in HEADERS:
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names.update(re.findall(r"VP_API\s+[\w\s\*]+?\b(vp_\w+)\s*\(", text))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
@@ -27,7 +30,9 @@ def vp():
 def test_header_declares_the_boundary():
     names = _declared_functions()
     for required in ("vp_plan", "vp_kernel_fft", "vp_source_assemble", "vp_apply",
-                     "vp_restrict_to_nested_box", "vp_destroy", "vp_status_string"):
+                     "vp_restrict_to_nested_box", "vp_destroy", "vp_status_string",
+                     "vp_batch_create", "vp_batch_run", "vp_apply_static",
+                     "vp_fno_forward", "vp_fno_backward", "vp_fno_adam"):
         assert required in names
 
 
@@ -96,6 +101,8 @@ def test_other_calls_reject_bad_arguments_on_the_host(vp):
     assert vp.lib.vp_apply(None, None, P(16), None) == vp.VP_ERR_ARG
     assert vp.lib.vp_source_assemble(None, None, 1, 0, None, None) == vp.VP_ERR_ARG
     assert vp.lib.vp_destroy(None) == vp.VP_OK
+    g8 = vp.make_grid((8, 8, 8), (0, 0, 0), 1e-4)
+    assert vp.lib.vp_plan_retarget(None, ctypes.byref(g8), 2, 1e6, ctypes.byref(_medium(vp))) == vp.VP_ERR_ARG
     assert vp.lib.vp_profile_enable(None, 1) == vp.VP_ERR_ARG
     src = vp.make_grid((5, 5, 5), (0.0, 0.0, 0.0), 1e-3)
     dst_out = vp.make_grid((3, 3, 3), (0.0, 0.0, 0.0031), 1e-3)
@@ -110,3 +117,30 @@ def test_other_calls_reject_bad_arguments_on_the_host(vp):
                                     None) == vp.VP_ERR_ARG
     assert vp.lib.vp_incident_field(ctypes.byref(src), P(64), 10, 0.02, 0.03, 1e6, 1e5, ctypes.byref(med), P(64),
                                     None) == vp.VP_ERR_ARG
+
+
+def test_fno_descriptor_checks_on_the_host(vp):
+    from paper_2011_03009_gb300 import fno
+    P = ctypes.c_void_p
+    cfg = fno.FnoConfig(n=16, width=8, hidden=12, layers=2, modes=(4, 6, 3))
+    d = cfg.desc()
+    W, H, (mx, my, mz) = 8, 12, cfg.modes
+    per_layer = mx * my * mz * W * W * 2 + W * W + W
+    expect = 10 * W + W + 2 * per_layer + W * H + H + H * 8 + 8
+    assert fno.lib.vp_fno_param_count(ctypes.byref(d)) == expect
+    offs = (ctypes.c_longlong * (3 * 2 + 7))()
+    assert fno.lib.vp_fno_param_offsets(ctypes.byref(d), offs) == vp.VP_OK
+    o = list(offs)
+    assert o[0] == 0 and o[-1] == expect and all(b > a for a, b in zip(o, o[1:]))
+    assert o[3] - o[2] == mx * my * mz * W * W * 2          # R_0
+    assert fno.lib.vp_fno_workspace_bytes(ctypes.byref(d)) > 16 ** 3 * (2 + 8) * 4
+    for bad in (dict(n=2), dict(width=0), dict(layers=9), dict(modes=(5, 6, 3)), dict(modes=(4, 18, 3)),
+                dict(modes=(4, 6, 9)), dict(modes=(4, 6, 0))):
+        bd = fno.FnoConfig(**{**dict(n=16, width=8, hidden=12, layers=2, modes=(4, 6, 3)), **bad}).desc()
+        assert fno.lib.vp_fno_param_count(ctypes.byref(bd)) == -1, bad
+        assert fno.lib.vp_fno_workspace_bytes(ctypes.byref(bd)) == -1, bad
+        assert fno.lib.vp_fno_forward(ctypes.byref(bd), P(64), P(64), P(64), None, P(64), None) == vp.VP_ERR_ARG
+    assert fno.lib.vp_fno_forward(ctypes.byref(d), None, P(64), P(64), None, P(64), None) == vp.VP_ERR_ARG
+    assert fno.lib.vp_fno_adam(-1, P(64), P(64), P(64), P(64), P(64), 1e-3, 0.9, 0.999, 1e-8, 0.1, 0.001, 1.0,
+                               None) == vp.VP_ERR_ARG
+    assert fno.lib.vp_fno_to_bf16(4, None, P(64), None) == vp.VP_ERR_ARG

@@ -34,7 +34,7 @@ def test_forward_matches_fp64_reference(F):
     cfg = F.FnoConfig(n=16, width=8, hidden=16, layers=2, modes=(8, 8, 4))
     m, flat = make(F, cfg, 3)
     rng = np.random.default_rng(4)
-    x = rng.standard_normal((16, 16, 16, 2))
+    x = 0.5 * rng.standard_normal((16, 16, 16, 2))
     xt = torch.from_numpy(x.reshape(-1, 2).astype(np.float32)).cuda()
     y = torch.empty((16 ** 3, 8), dtype=torch.float32, device="cuda")
     m.forward(xt, y)
@@ -49,7 +49,7 @@ def test_gradients_match_finite_differences_of_the_reference(F):
     cfg = F.FnoConfig(n=8, width=4, hidden=8, layers=2, modes=(4, 4, 3))
     m, flat = make(F, cfg, 5)
     rng = np.random.default_rng(6)
-    x = bf16_round(rng.standard_normal((8, 8, 8, 2)))
+    x = bf16_round(0.5 * rng.standard_normal((8, 8, 8, 2)))
     t = rng.standard_normal((8, 8, 8, 8))
     xt = torch.from_numpy(x.reshape(-1, 2).astype(np.float32)).cuda()
     tt = torch.from_numpy(t.reshape(-1, 8).astype(np.float32)).cuda()
@@ -84,7 +84,7 @@ def test_training_steps_reduce_the_loss(F):
     rng = np.random.default_rng(8)
     xs, ts = [], []
     for _ in range(4):
-        x = rng.standard_normal((16 ** 3, 2)).astype(np.float32)
+        x = (0.5 * rng.standard_normal((16 ** 3, 2))).astype(np.float32)
         xs.append(torch.from_numpy(x).cuda())
         ts.append(torch.from_numpy(np.tile(x, (1, 4)) * 0.5).cuda())
     order = np.arange(4)
@@ -92,3 +92,25 @@ def test_training_steps_reduce_the_loss(F):
     for _ in range(30):
         last = m.train_epoch(xs, ts, lr=3e-3, batch=2, order=order)
     assert last < 0.5 * first, (first, last)
+
+
+def test_fused_tiles_and_inference_match_fp64_reference(F):
+    """N = 64: the spectral inverse rides inside the pointwise GEMM and vp_fno_infer fuses
+    the projection; both against the FP64 reference and against each other."""
+    cfg = F.FnoConfig(n=64, width=16, hidden=32, layers=2, modes=(8, 8, 4))
+    m, flat = make(F, cfg, 9)
+    rng = np.random.default_rng(10)
+    x = bf16_round(0.5 * rng.standard_normal((64, 64, 64, 2)))
+    xt = torch.from_numpy(x.reshape(-1, 2).astype(np.float32)).cuda()
+    y_fwd = torch.empty((64 ** 3, 8), dtype=torch.float32, device="cuda")
+    y_inf = torch.empty_like(y_fwd)
+    m.forward(xt, y_fwd)
+    m.infer(xt, y_inf)
+    torch.cuda.synchronize()
+    ref = ofno.forward(m.unpack(flat), x, cfg.modes).reshape(-1, 8)
+    for got in (y_fwd, y_inf):
+        g = got.cpu().numpy().astype(np.float64)
+        rel = np.linalg.norm(g - ref) / np.linalg.norm(ref)
+        assert rel <= 3e-2, rel
+    d = (y_fwd - y_inf).norm() / y_fwd.norm()
+    assert float(d) <= 1e-2, float(d)

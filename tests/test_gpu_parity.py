@@ -198,6 +198,19 @@ def test_incident_field_matches_oracle(vp):
     assert rel_l2(got, ref) <= 2e-6
 
 
+def test_incident_field_next_to_the_bowl(vp):
+    """A grid straddling the cap: points within a few voxels of the tile take the direct
+    FP64 distance, the others the tile-centred expansion; both against the oracle."""
+    bowl = synth.Bowl(l=0.02, R=0.01, f0=1.0e6, p0=0.5e6)
+    g = synth.Grid((12, 20, 20), (0.0005, -0.005, -0.005), 0.5e-3)
+    pts = synth.sample_bowl_points(bowl, 600, seed=5)
+    out = torch.empty(g.n, dtype=torch.complex64, device="cuda")
+    vp.vp_incident_field(g, torch.from_numpy(pts).cuda(), bowl, synth.WATER, out)
+    got = host(out)
+    ref = rayleigh.incident_field(g, pts, bowl, synth.WATER)
+    assert rel_l2(got, ref) <= 2e-6
+
+
 def test_small_workload_end_to_end(vp):
     """32^3 second harmonic of the 1 cm / 2 cm / 1 MHz bowl, against oracle and brute force."""
     w = synth.workload_small_p2()
@@ -282,3 +295,29 @@ def test_two_level_kernel_spectrum_octant(vp):
     plan.close()
     full = potential.kernel_spectrum(n, g.h, physics.wavenumber(3, 1.1e6, synth.WATER), m)
     assert rel_l2(got, full[: o[0], : o[1], : o[2]]) <= 1e-6
+
+
+def test_retargeted_plan_matches_a_fresh_plan_and_the_oracle(vp):
+    """vp_plan_retarget: same N, new spacing/origin/harmonic/f0; K^ rebuilt, result equal
+    to a plan created for the new problem, and to the oracle."""
+    n = (24, 20, 18)
+    g1, g2 = grid(n, h=1.25e-4), grid(n, h=0.9e-4, origin=(0.01, 0.0, 0.002))
+    f = synth.random_field(n, seed=11)
+    plan = vp.vp_plan(g1, 2, 1.0e6, synth.WATER)
+    plan.kernel_fft()
+    u = torch.empty(n, dtype=torch.complex64, device="cuda")
+    plan.apply(dev(f), u)
+    plan.retarget(g2, 3, 1.3e6, synth.WATER)
+    assert plan.info().khat_ready == 0
+    with pytest.raises(vp.VpError):
+        plan.apply(dev(f), u)          # stale spectrum
+    plan.kernel_fft()
+    plan.apply(dev(f), u)
+    got = host(u)
+    fresh = gpu_apply(vp, g2, f, 3, f0=1.3e6)
+    assert np.array_equal(got, fresh)
+    k = physics.wavenumber(3, 1.3e6, synth.WATER)
+    assert rel_l2(got, potential.apply_fft(f, g2.h, k)) <= REL_L2
+    with pytest.raises(vp.VpError):
+        plan.retarget(grid((24, 20, 17)), 3, 1.3e6, synth.WATER)
+    plan.close()

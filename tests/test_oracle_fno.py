@@ -50,3 +50,13 @@ def test_forward_shapes_and_loss_zero_at_its_own_output():
     y = fno.forward(p, x, (4, 4, 3))
     assert y.shape == (8, 8, 8, 8)
     assert fno.loss(p, x, y, (4, 4, 3)) == 0.0
+
+
+def test_features_follow_de_moivre():
+    # q = r e^{i theta}: q^k = r^k (cos k theta + i sin k theta)
+    r, th = 0.8, 0.37
+    x = np.array([r * math.cos(th), r * math.sin(th)])
+    f = fno.features(x)
+    for k in range(1, 6):
+        assert abs(f[2 * k - 2] - r ** k * math.cos(k * th)) < 1e-15
+        assert abs(f[2 * k - 1] - r ** k * math.sin(k * th)) < 1e-15
