@@ -187,10 +187,26 @@ VP_API int vp_apply(vp_plan_t p, const void* f, void* u, vp_stream_t stream);
  * Every target centre must lie within the box spanned by the source centres (a
  * relative slack of 1e-9 voxel is allowed); otherwise VP_ERR_NOT_NESTED unless
  * flags & VP_RESTRICT_ZERO_OUTSIDE, which writes zero there instead.
+ * flags & VP_RESTRICT_QUADRATIC selects quadratic interpolation instead (the higher-
+ * order inter-mesh interpolation Section 6 leaves as an option): per axis the Lagrange
+ * quadratic through the three nearest source centres, c = floor(t + 1/2) clamped to
+ * [1, N-2], u = t - c, weights (u(u-1)/2, 1-u^2, u(u+1)/2) on v[c-1], v[c], v[c+1];
+ * an axis of two voxels stays linear.  Exact for fields quadratic along each axis.
  * Errors: VP_ERR_ARG, VP_ERR_NOT_NESTED, VP_ERR_CUDA. */
 #define VP_RESTRICT_ZERO_OUTSIDE 1
+#define VP_RESTRICT_QUADRATIC 2
 VP_API int vp_restrict_to_nested_box(const vp_grid* src, const void* src_field, const vp_grid* dst,
                                      void* dst_field, int flags, vp_stream_t stream);
+
+/* ---- integration-domain selection (Section 5) -------------------------------------
+ * Smallest voxel box D of the N^3 field f (complex64, device) outside which
+ * Q(x) = log10(|f(x)| / max|f|) < q0 (Section 5's domain-convergence study; q0 <= 0):
+ * box[0..2] = first and box[3..5] = last index per axis, inclusive, written to host
+ * memory.  Squares |f|^2 are formed in FP64 from the FP32 parts and compared with
+ * 10^(2 q0) max|f|^2 (so a field that is zero everywhere gives the whole grid).  If
+ * max_abs is not NULL it receives max|f|.  Synchronises `stream`.
+ * Errors: VP_ERR_ARG (null pointers, n[i] < 1, q0 > 0 or not finite), VP_ERR_CUDA. */
+VP_API int vp_q0_box(const int n[3], const void* f, double q0, int box[6], double* max_abs, vp_stream_t stream);
 
 /* ---- incident field (input generator) -------------------------------------------
  * p1 on grid g from a bowl of focal length l and aperture radius R driven at f0 with

@@ -1,4 +1,5 @@
-"""Linear (trilinear) interpolation of a field from one voxel grid onto a nested one (Section 6).
+"""Linear (trilinear) and quadratic interpolation of a field from one voxel grid onto a
+nested one (Section 6; test infrastructure only).
 
 The paper interpolates each lower harmonic from the mesh it was computed on onto
 the voxel centres of the next mesh with linear interpolation on a regular grid.
@@ -8,6 +9,10 @@ spanned by the source centres (no extrapolation); the oracle raises otherwise.
 For a target coordinate x on one axis, t = (x - o_src) / h_src; i0 = floor(t),
 clamped to [0, N-2]; weight w = t - i0; the value is the tensor product of the
 1-D linear interpolants (1 - w) v[i0] + w v[i0 + 1] over the three axes.
+
+Quadratic (the higher-order option Section 6 mentions): per axis the Lagrange
+polynomial through the three nearest source centres c - 1, c, c + 1 with
+c = floor(t + 1/2) clamped to [1, N-2], evaluated at u = t - c.
 """
 from __future__ import annotations
 
@@ -58,4 +63,44 @@ def restrict_trilinear(src: np.ndarray, src_grid, dst_grid) -> np.ndarray:
                 iz = idx[2] + cz
                 w = wx[:, None, None] * wy[None, :, None] * wz[None, None, :]
                 out += w * src[np.ix_(ix, iy, iz)]
+    return out
+
+
+def _axis_quadratic(src_origin: float, src_h: float, src_n: int, dst_coords: np.ndarray):
+    """Indices (k, 3) and weights (k, 3) of the quadratic Lagrange interpolant through the
+    three source centres nearest to each target; a two-centre axis stays linear and a
+    one-centre axis takes its only value."""
+    t = (dst_coords - src_origin) / src_h
+    k = len(t)
+    if src_n < 3:
+        i0, w, single = _axis_weights(src_origin, src_h, src_n, dst_coords)
+        idx = np.stack([i0, i0 + (0 if single else 1), i0 + (0 if single else 1)], axis=1)
+        wts = np.stack([1.0 - w if not single else np.ones(k), w if not single else np.zeros(k), np.zeros(k)], axis=1)
+        return idx, wts
+    if np.any(t < -TOL) or np.any(t > (src_n - 1) + TOL):
+        raise ValueError("target outside the source grid")
+    c = np.clip(np.floor(t + 0.5).astype(np.int64), 1, src_n - 2)
+    u = t - c
+    # Lagrange basis on the nodes -1, 0, 1
+    l_m = u * (u - 1.0) / 2.0
+    l_0 = (1.0 - u) * (1.0 + u)
+    l_p = u * (u + 1.0) / 2.0
+    return np.stack([c - 1, c, c + 1], axis=1), np.stack([l_m, l_0, l_p], axis=1)
+
+
+def restrict_quadratic(src: np.ndarray, src_grid, dst_grid) -> np.ndarray:
+    """Values of the tensor-product quadratic interpolant of ``src`` at dst_grid's centres."""
+    src = np.asarray(src, dtype=np.complex128)
+    idx, wts = [], []
+    for a in range(3):
+        coords = dst_grid.origin[a] + dst_grid.h * np.arange(dst_grid.n[a], dtype=np.float64)
+        i, w = _axis_quadratic(src_grid.origin[a], src_grid.h, src_grid.n[a], coords)
+        idx.append(i)
+        wts.append(w)
+    out = np.zeros(tuple(dst_grid.n), dtype=np.complex128)
+    for p in range(3):
+        for q in range(3):
+            for r in range(3):
+                w = wts[0][:, p][:, None, None] * wts[1][:, q][None, :, None] * wts[2][:, r][None, None, :]
+                out += w * src[np.ix_(idx[0][:, p], idx[1][:, q], idx[2][:, r])]
     return out

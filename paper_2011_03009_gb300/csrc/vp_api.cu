@@ -835,7 +835,7 @@ VP_API int vp_apply(vp_plan_t p, const void* f, void* u, vp_stream_t stream) {
 VP_API int vp_restrict_to_nested_box(const vp_grid* src, const void* src_field, const vp_grid* dst,
                                      void* dst_field, int flags, vp_stream_t stream) {
   if (!grid_ok(src) || !grid_ok(dst) || !src_field || !dst_field) return VP_ERR_ARG;
-  if (flags & ~VP_RESTRICT_ZERO_OUTSIDE) return VP_ERR_ARG;
+  if (flags & ~(VP_RESTRICT_ZERO_OUTSIDE | VP_RESTRICT_QUADRATIC)) return VP_ERR_ARG;
   double a[3], b[3];
   const double tol = 1e-9;
   for (int ax = 0; ax < 3; ++ax) {
@@ -851,8 +851,44 @@ VP_API int vp_restrict_to_nested_box(const vp_grid* src, const void* src_field, 
       return VP_ERR_NOT_NESTED;
   }
   cudaError_t e = vp::launch_restrict((const float2*)src_field, src->n, (float2*)dst_field, dst->n, a, b,
-                                      flags & VP_RESTRICT_ZERO_OUTSIDE, (cudaStream_t)stream);
+                                      (flags & VP_RESTRICT_QUADRATIC) ? 2 : 1, flags & VP_RESTRICT_ZERO_OUTSIDE,
+                                      (cudaStream_t)stream);
   return cuda_status(e);
+}
+
+VP_API int vp_q0_box(const int n[3], const void* f, double q0, int box[6], double* max_abs, vp_stream_t stream) {
+  if (!n || !f || !box || !std::isfinite(q0) || q0 > 0.0) return VP_ERR_ARG;
+  for (int a = 0; a < 3; ++a)
+    if (n[a] < 1) return VP_ERR_ARG;
+  int dev = 0;
+  VP_TRY_CUDA(cudaGetDevice(&dev));
+  cudaStream_t s = (cudaStream_t)stream;
+  void* scratch = nullptr;
+  const size_t bytes = sizeof(unsigned long long) + 6 * sizeof(int);
+  cudaMemPool_t pool = scratch_pool(dev);
+  if (pool) {
+    VP_TRY_CUDA(cudaMallocFromPoolAsync(&scratch, bytes, pool, s));
+  } else {
+    VP_TRY_CUDA(cudaMallocAsync(&scratch, bytes, s));
+  }
+  // threshold on squares: |f|^2 >= 10^(2 Q0) max |f|^2
+  const double factor = std::pow(10.0, 2.0 * q0);
+  unsigned char host[sizeof(unsigned long long) + 6 * sizeof(int)];
+  cudaError_t e = vp::launch_q0_box((const float2*)f, n, factor, scratch, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host, scratch, bytes, cudaMemcpyDeviceToHost, s);
+  cudaError_t e2 = cudaFreeAsync(scratch, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = e2;
+  if (e != cudaSuccess) return cuda_status(e);
+  unsigned long long bits;
+  std::memcpy(&bits, host, sizeof(bits));
+  std::memcpy(box, host + sizeof(bits), 6 * sizeof(int));
+  if (max_abs) {
+    double m2;
+    std::memcpy(&m2, &bits, sizeof(m2));
+    *max_abs = std::sqrt(m2);
+  }
+  return VP_OK;
 }
 
 VP_API int vp_incident_field(const vp_grid* g, const double* points, int n_points, double l, double R,

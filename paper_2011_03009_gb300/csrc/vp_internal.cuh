@@ -123,8 +123,10 @@ cudaError_t launch_octant_extract(const float2* scr, float2* oct, const int m[3]
 cudaError_t launch_source_assemble(const float2* const* lower, int harmonic, float cn, float2* out,
                                    long long count, cudaStream_t s);
 cudaError_t launch_restrict(const float2* src, const int ns[3], float2* dst, const int nd[3],
-                            const double a[3], const double b[3], int zero_outside,
+                            const double a[3], const double b[3], int order, int zero_outside,
                             cudaStream_t s);
+// scratch: 8-byte max |f|^2 followed by int box[6]
+cudaError_t launch_q0_box(const float2* f, const int n[3], double factor, void* scratch, cudaStream_t s);
 cudaError_t launch_incident(const double* pts, int npts, const int n[3], const double origin[3],
                             double h, double kr, double ki, double scale_re, double scale_im,
                             float2* out, cudaStream_t s);

@@ -127,25 +127,53 @@ constexpr int kFixBits = 40;
 
 struct AxisFix { long long A, B; int n; };
 
-__device__ __forceinline__ bool axis_weights(const AxisFix& m, int i, int& i0, float& w) {
+// Interpolation stencil of one target along one axis: cnt source indices i0 .. i0+cnt-1
+// with weights w[0..cnt-1].
+//   ORD 1 (linear, Section 6): i0 = floor(t) clamped to [0, n-2], f = t - i0,
+//         w = (1 - f, f).
+//   ORD 2 (quadratic Lagrange through the three nearest centres): c = floor(t + 1/2)
+//         clamped to [1, n-2], u = t - c, i0 = c - 1,
+//         w = (u (u - 1) / 2, 1 - u^2, u (u + 1) / 2); a two-voxel axis falls back to
+//         ORD 1.
+// A one-voxel axis has cnt = 1, w = (1).  Returns whether t lies inside [0, n-1]
+// (with 1e-9 voxel of slack).
+template <int ORD>
+__device__ __forceinline__ bool stencil(const AxisFix& m, int i, int& i0, float (&w)[3], int& cnt) {
   const long long T = m.A + (long long)i * m.B;
   const long long tol = 1100;  // 1e-9 voxel in fixed point
   const bool inside = T >= -tol && T <= ((long long)(m.n - 1) << kFixBits) + tol;
+  w[0] = 1.f;
+  w[1] = w[2] = 0.f;
   if (m.n == 1) {
     i0 = 0;
-    w = 0.f;
+    cnt = 1;
+    return inside;
+  }
+  if (ORD == 2 && m.n >= 3) {
+    long long c = (T + (1LL << (kFixBits - 1))) >> kFixBits;  // floor(t + 1/2)
+    if (c < 1) c = 1;
+    if (c > m.n - 2) c = m.n - 2;
+    const float u = (float)(T - (c << kFixBits)) * (1.0f / (float)(1LL << kFixBits));
+    i0 = (int)c - 1;
+    cnt = 3;
+    w[0] = 0.5f * u * (u - 1.f);
+    w[1] = (1.f - u) * (1.f + u);
+    w[2] = 0.5f * u * (u + 1.f);
     return inside;
   }
   long long fl = T >> kFixBits;  // floor (arithmetic shift)
   if (fl < 0) fl = 0;
   if (fl > m.n - 2) fl = m.n - 2;
   i0 = (int)fl;
-  float wf = (float)(T - (fl << kFixBits)) * (1.0f / (float)(1LL << kFixBits));
-  w = fminf(fmaxf(wf, 0.f), 1.f);
+  cnt = 2;
+  const float f = fminf(fmaxf((float)(T - (fl << kFixBits)) * (1.0f / (float)(1LL << kFixBits)), 0.f), 1.f);
+  w[0] = 1.f - f;
+  w[1] = f;
   return inside;
 }
 
-// One CTA row of 128 targets along z at fixed (x, y) = (blockIdx.z, blockIdx.y).
+// Direct form: one thread per target, gathers from global memory (any spacing ratio).
+template <int ORD>
 __global__ void __launch_bounds__(128) restrict_kernel(const float2* __restrict__ src, int snx, int sny, int snz,
                                                        float2* __restrict__ dst, int dnx, int dny, int dnz,
                                                        AxisFix mx, AxisFix my, AxisFix mz, int zero_outside) {
@@ -154,35 +182,182 @@ __global__ void __launch_bounds__(128) restrict_kernel(const float2* __restrict_
   const int ix = blockIdx.z;
   if (iz >= dnz) return;
   const long long idx = ((long long)ix * dny + iy) * dnz + iz;
-  int x0, y0, z0;
-  float wx, wy, wz;
-  bool in = axis_weights(mx, ix, x0, wx);
-  in &= axis_weights(my, iy, y0, wy);
-  in &= axis_weights(mz, iz, z0, wz);
+  int x0, y0, z0, cx, cy, cz;
+  float wx[3], wy[3], wz[3];
+  bool in = stencil<ORD>(mx, ix, x0, wx, cx);
+  in &= stencil<ORD>(my, iy, y0, wy, cy);
+  in &= stencil<ORD>(mz, iz, z0, wz, cz);
   if (!in && zero_outside) {
     dst[idx] = make_float2(0.f, 0.f);
     return;
   }
-  const int x1 = snx > 1 ? x0 + 1 : x0;
-  const int y1 = sny > 1 ? y0 + 1 : y0;
-  const int z1 = snz > 1 ? z0 + 1 : z0;
   const long long sy = snz, sx = (long long)sny * snz;
-  const float2 c000 = __ldg(&src[x0 * sx + y0 * sy + z0]);
-  const float2 c001 = __ldg(&src[x0 * sx + y0 * sy + z1]);
-  const float2 c010 = __ldg(&src[x0 * sx + y1 * sy + z0]);
-  const float2 c011 = __ldg(&src[x0 * sx + y1 * sy + z1]);
-  const float2 c100 = __ldg(&src[x1 * sx + y0 * sy + z0]);
-  const float2 c101 = __ldg(&src[x1 * sx + y0 * sy + z1]);
-  const float2 c110 = __ldg(&src[x1 * sx + y1 * sy + z0]);
-  const float2 c111 = __ldg(&src[x1 * sx + y1 * sy + z1]);
-  const float uz = 1.f - wz, uy = 1.f - wy, ux = 1.f - wx;
-  const float2 c00 = make_float2(uz * c000.x + wz * c001.x, uz * c000.y + wz * c001.y);
-  const float2 c01 = make_float2(uz * c010.x + wz * c011.x, uz * c010.y + wz * c011.y);
-  const float2 c10 = make_float2(uz * c100.x + wz * c101.x, uz * c100.y + wz * c101.y);
-  const float2 c11 = make_float2(uz * c110.x + wz * c111.x, uz * c110.y + wz * c111.y);
-  const float2 c0 = make_float2(uy * c00.x + wy * c01.x, uy * c00.y + wy * c01.y);
-  const float2 c1 = make_float2(uy * c10.x + wy * c11.x, uy * c10.y + wy * c11.y);
-  dst[idx] = make_float2(ux * c0.x + wx * c1.x, ux * c0.y + wx * c1.y);
+  float2 acc = make_float2(0.f, 0.f);
+  for (int a = 0; a < cx; ++a) {
+    float2 py = make_float2(0.f, 0.f);
+    for (int b = 0; b < cy; ++b) {
+      const float2* row = src + (x0 + a) * sx + (y0 + b) * sy + z0;
+      float2 pz = make_float2(0.f, 0.f);
+      for (int c = 0; c < cz; ++c) {
+        const float2 v = __ldg(row + c);
+        pz.x = fmaf(wz[c], v.x, pz.x);
+        pz.y = fmaf(wz[c], v.y, pz.y);
+      }
+      py.x = fmaf(wy[b], pz.x, py.x);
+      py.y = fmaf(wy[b], pz.y, py.y);
+    }
+    acc.x = fmaf(wx[a], py.x, acc.x);
+    acc.y = fmaf(wx[a], py.y, acc.y);
+  }
+  dst[idx] = acc;
+}
+
+// Shared-memory tiled form: one CTA computes a 1 x 8 x 64 block of targets (two per
+// thread) from the source sub-block they touch (ORD + 1 x planes, at most kRsY x kRsZ
+// source voxels), staged once with coalesced loads.  Used when the target spacing is
+// at most about the source spacing on y and z (nested grids of higher harmonics are
+// finer), so the sub-block always fits.
+constexpr int kRtY = 8, kRtZ = 64, kRsY = 12, kRsZ = 80;
+
+template <int ORD>
+__global__ void __launch_bounds__(256) restrict_tiled_kernel(const float2* __restrict__ src, int snx, int sny,
+                                                             int snz, float2* __restrict__ dst, int dnx, int dny,
+                                                             int dnz, AxisFix mx, AxisFix my, AxisFix mz,
+                                                             int zero_outside) {
+  __shared__ float2 tile[ORD + 1][kRsY][kRsZ];
+  const int ix = blockIdx.z, iy0 = blockIdx.y * kRtY, iz0 = blockIdx.x * kRtZ;
+  int x0, cx, ys, ye, zs, ze, c_;
+  float wx[3], wt[3];
+  const bool inx = stencil<ORD>(mx, ix, x0, wx, cx);
+  stencil<ORD>(my, iy0, ys, wt, c_);
+  stencil<ORD>(my, min(iy0 + kRtY - 1, dny - 1), ye, wt, c_);
+  ye = min(ye + c_ - 1, sny - 1);
+  stencil<ORD>(mz, iz0, zs, wt, c_);
+  stencil<ORD>(mz, min(iz0 + kRtZ - 1, dnz - 1), ze, wt, c_);
+  ze = min(ze + c_ - 1, snz - 1);
+  const int ny_r = ye - ys + 1, nz_r = ze - zs + 1;  // <= kRsY, kRsZ by the host's spacing check
+  const long long sy = snz, sx = (long long)sny * snz;
+  for (int e = threadIdx.x; e < cx * ny_r * nz_r; e += blockDim.x) {
+    const int zz = e % nz_r;
+    const int r = e / nz_r;
+    const int yy = r % ny_r, xi = r / ny_r;
+    tile[xi][yy][zz] = __ldg(&src[(x0 + xi) * sx + (ys + yy) * sy + zs + zz]);
+  }
+  __syncthreads();
+  const int iz = iz0 + threadIdx.x % kRtZ;
+  if (iz >= dnz) return;
+  int z0, cz;
+  float wz[3];
+  const bool inz = stencil<ORD>(mz, iz, z0, wz, cz);
+  z0 -= zs;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int iy = iy0 + 2 * (threadIdx.x / kRtZ) + k;
+    if (iy >= dny) break;
+    int y0, cy;
+    float wy[3];
+    const bool iny = stencil<ORD>(my, iy, y0, wy, cy);
+    const long long idx = ((long long)ix * dny + iy) * dnz + iz;
+    if (!(inx && iny && inz) && zero_outside) {
+      dst[idx] = make_float2(0.f, 0.f);
+      continue;
+    }
+    y0 -= ys;
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int a = 0; a <= ORD; ++a) {
+      if (a >= cx) break;
+      float2 py = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int b = 0; b <= ORD; ++b) {
+        if (b >= cy) break;
+        float2 pz = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int c = 0; c <= ORD; ++c) {
+          if (c >= cz) break;
+          const float2 v = tile[a][y0 + b][z0 + c];
+          pz.x = fmaf(wz[c], v.x, pz.x);
+          pz.y = fmaf(wz[c], v.y, pz.y);
+        }
+        py.x = fmaf(wy[b], pz.x, py.x);
+        py.y = fmaf(wy[b], pz.y, py.y);
+      }
+      acc.x = fmaf(wx[a], py.x, acc.x);
+      acc.y = fmaf(wx[a], py.y, acc.y);
+    }
+    dst[idx] = acc;
+  }
+}
+
+// Localisation measure of Section 5: Q(x) = log10(|f(x)| / max |f|).  The smallest box
+// holding every voxel with Q >= Q0 is found in two passes: max |f|^2, then the index
+// bounds of the voxels with |f|^2 >= 10^(2 Q0) max |f|^2.  Squares are formed in FP64
+// from the FP32 parts (exact products, one rounding in the sum), so the decision is
+// reproducible on the host.  Non-negative doubles order like their bit patterns, which
+// lets atomicMax work on the 64-bit integer view.
+__device__ __forceinline__ double abs2_fp64(float2 v) {
+  const double re = v.x, im = v.y;
+  return re * re + im * im;
+}
+
+__global__ void __launch_bounds__(256) max_abs2_kernel(const float2* __restrict__ f, long long count,
+                                                       unsigned long long* __restrict__ out_bits) {
+  __shared__ double part[8];
+  double m = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x)
+    m = fmax(m, abs2_fp64(__ldg(&f[i])));
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, part[w]);
+    atomicMax(out_bits, (unsigned long long)__double_as_longlong(m));
+  }
+}
+
+// box[0..2] = min index per axis, box[3..5] = max index (initialised to n and -1)
+__global__ void __launch_bounds__(256) q0_box_kernel(const float2* __restrict__ f, int nx, int ny, int nz,
+                                                     const unsigned long long* __restrict__ max_bits,
+                                                     double factor, int* __restrict__ box) {
+  __shared__ int sb[6];
+  if (threadIdx.x < 6) sb[threadIdx.x] = threadIdx.x < 3 ? 0x7fffffff : -1;
+  __syncthreads();
+  const double thr = __longlong_as_double((long long)*max_bits) * factor;
+  const long long count = (long long)nx * ny * nz;
+  int lo[3] = {0x7fffffff, 0x7fffffff, 0x7fffffff}, hi[3] = {-1, -1, -1};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x) {
+    if (abs2_fp64(__ldg(&f[i])) >= thr) {
+      const int iz = (int)(i % nz);
+      const long long r = i / nz;
+      const int iy = (int)(r % ny), ix = (int)(r / ny);
+      lo[0] = min(lo[0], ix); hi[0] = max(hi[0], ix);
+      lo[1] = min(lo[1], iy); hi[1] = max(hi[1], iy);
+      lo[2] = min(lo[2], iz); hi[2] = max(hi[2], iz);
+    }
+  }
+  for (int a = 0; a < 3; ++a) {
+    for (int o = 16; o > 0; o >>= 1) {
+      lo[a] = min(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
+      hi[a] = max(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
+    }
+  }
+  if ((threadIdx.x & 31) == 0) {
+    for (int a = 0; a < 3; ++a) {
+      atomicMin(&sb[a], lo[a]);
+      atomicMax(&sb[3 + a], hi[a]);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) atomicMin(&box[threadIdx.x], sb[threadIdx.x]);
+  else if (threadIdx.x < 6) atomicMax(&box[threadIdx.x], sb[threadIdx.x]);
+}
+
+__global__ void q0_init_kernel(unsigned long long* max_bits, int* box) {
+  if (threadIdx.x == 0) *max_bits = 0ULL;
+  if (threadIdx.x < 3) box[threadIdx.x] = 0x7fffffff;
+  else if (threadIdx.x < 6) box[threadIdx.x] = -1;
 }
 
 constexpr int kIncBlock = 256;
@@ -326,7 +501,7 @@ cudaError_t launch_source_assemble(const float2* const* lower, int harmonic, flo
 }
 
 cudaError_t launch_restrict(const float2* src, const int ns[3], float2* dst, const int nd[3],
-                            const double a[3], const double b[3], int zero_outside, cudaStream_t s) {
+                            const double a[3], const double b[3], int order, int zero_outside, cudaStream_t s) {
   if (nd[1] > 65535 || nd[0] > 65535) return cudaErrorInvalidConfiguration;
   AxisFix m[3];
   for (int i = 0; i < 3; ++i) {
@@ -334,9 +509,27 @@ cudaError_t launch_restrict(const float2* src, const int ns[3], float2* dst, con
     m[i].B = llround(b[i] * (double)(1LL << kFixBits));
     m[i].n = ns[i];
   }
+  // tiled form when the source footprint of a 8 x 64 (y, z) target block fits the
+  // staging tile: (8 - 1) b_y + order + 2 <= kRsY and (64 - 1) b_z + order + 2 <= kRsZ
+  // source voxels (b = target spacing / source spacing), with a margin for rounding
+  const double extra = order + 2.0;
+  if (b[1] * (kRtY - 1) + extra <= kRsY && b[2] * (kRtZ - 1) + extra <= kRsZ) {
+    const dim3 grid((unsigned)((nd[2] + kRtZ - 1) / kRtZ), (unsigned)((nd[1] + kRtY - 1) / kRtY), (unsigned)nd[0]);
+    if (order == 2)
+      restrict_tiled_kernel<2><<<grid, 256, 0, s>>>(src, ns[0], ns[1], ns[2], dst, nd[0], nd[1], nd[2], m[0], m[1],
+                                                    m[2], zero_outside);
+    else
+      restrict_tiled_kernel<1><<<grid, 256, 0, s>>>(src, ns[0], ns[1], ns[2], dst, nd[0], nd[1], nd[2], m[0], m[1],
+                                                    m[2], zero_outside);
+    return cudaGetLastError();
+  }
   const dim3 grid((unsigned)((nd[2] + 127) / 128), (unsigned)nd[1], (unsigned)nd[0]);
-  restrict_kernel<<<grid, 128, 0, s>>>(src, ns[0], ns[1], ns[2], dst, nd[0], nd[1], nd[2], m[0], m[1], m[2],
-                                        zero_outside);
+  if (order == 2)
+    restrict_kernel<2><<<grid, 128, 0, s>>>(src, ns[0], ns[1], ns[2], dst, nd[0], nd[1], nd[2], m[0], m[1], m[2],
+                                             zero_outside);
+  else
+    restrict_kernel<1><<<grid, 128, 0, s>>>(src, ns[0], ns[1], ns[2], dst, nd[0], nd[1], nd[2], m[0], m[1], m[2],
+                                             zero_outside);
   return cudaGetLastError();
 }
 
@@ -348,6 +541,16 @@ cudaError_t launch_incident(const double* pts, int npts, const int n[3], const d
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
   incident_kernel<<<(unsigned)blocks, kIncBlock, 0, s>>>(pts, npts, n[0], n[1], n[2], origin[0], origin[1],
                                                          origin[2], h, kr, ki, scale_re, scale_im, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_q0_box(const float2* f, const int n[3], double factor, void* scratch, cudaStream_t s) {
+  unsigned long long* max_bits = static_cast<unsigned long long*>(scratch);
+  int* box = reinterpret_cast<int*>(max_bits + 1);
+  const long long count = (long long)n[0] * n[1] * n[2];
+  q0_init_kernel<<<1, 32, 0, s>>>(max_bits, box);
+  max_abs2_kernel<<<grid_for(count, 256), 256, 0, s>>>(f, count, max_bits);
+  q0_box_kernel<<<grid_for(count, 256), 256, 0, s>>>(f, n[0], n[1], n[2], max_bits, factor, box);
   return cudaGetLastError();
 }
 

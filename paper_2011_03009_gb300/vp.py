@@ -24,6 +24,7 @@ VP_ERR_STATE = -6
 VP_ERR_TIMEOUT = -7
 VP_ERR_UNSUPPORTED = -8
 VP_RESTRICT_ZERO_OUTSIDE = 1
+VP_RESTRICT_QUADRATIC = 2
 MAX_PASS = 8
 MAX_LOWER = 8
 
@@ -79,6 +80,7 @@ def _load():
         "vp_profile_read": (I, [P, ctypes.POINTER(D), ctypes.POINTER(I), I]),
         "vp_version": (ctypes.c_char_p, []),
         "vp_apply_static": (I, [ctypes.POINTER(vp_grid), I, D, ctypes.POINTER(vp_medium), P, P, P]),
+        "vp_q0_box": (I, [ctypes.POINTER(I), P, D, ctypes.POINTER(I), ctypes.POINTER(D), P]),
         "vp_batch_create": (I, [I, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P),
                                 ctypes.POINTER(P)]),
         "vp_batch_run": (I, [P, P]),
@@ -268,12 +270,23 @@ def vp_apply(plan: Plan, f, u, stream=None):
     plan.apply(f, u, stream)
 
 
-def vp_restrict_to_nested_box(src_grid, src, dst_grid, dst, zero_outside: bool = False, stream=None):
+def vp_restrict_to_nested_box(src_grid, src, dst_grid, dst, zero_outside: bool = False, quadratic: bool = False,
+                              stream=None):
     gs = src_grid if isinstance(src_grid, vp_grid) else grid_of(src_grid)
     gd = dst_grid if isinstance(dst_grid, vp_grid) else grid_of(dst_grid)
-    flags = VP_RESTRICT_ZERO_OUTSIDE if zero_outside else 0
+    flags = (VP_RESTRICT_ZERO_OUTSIDE if zero_outside else 0) | (VP_RESTRICT_QUADRATIC if quadratic else 0)
     _check(lib.vp_restrict_to_nested_box(ctypes.byref(gs), _ptr(src), ctypes.byref(gd), _ptr(dst), flags,
                                          _stream(stream)), "vp_restrict_to_nested_box")
+
+
+def vp_q0_box(field, q0: float, stream=None):
+    """Smallest index box holding every voxel with log10(|f| / max|f|) >= q0 (Section 5).
+    Returns (lo, hi, max_abs) with inclusive bounds per axis."""
+    n = (ctypes.c_int * 3)(*field.shape)
+    box = (ctypes.c_int * 6)()
+    m = ctypes.c_double(0.0)
+    _check(lib.vp_q0_box(n, _ptr(field), float(q0), box, ctypes.byref(m), _stream(stream)), "vp_q0_box")
+    return tuple(box[0:3]), tuple(box[3:6]), m.value
 
 
 def vp_incident_field(grid, points, bowl, medium, out, stream=None):

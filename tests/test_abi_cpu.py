@@ -101,6 +101,14 @@ def test_other_calls_reject_bad_arguments_on_the_host(vp):
     assert vp.lib.vp_apply(None, None, P(16), None) == vp.VP_ERR_ARG
     assert vp.lib.vp_source_assemble(None, None, 1, 0, None, None) == vp.VP_ERR_ARG
     assert vp.lib.vp_destroy(None) == vp.VP_OK
+    n3 = (ctypes.c_int * 3)(4, 4, 4)
+    box = (ctypes.c_int * 6)()
+    assert vp.lib.vp_q0_box(n3, None, -1.0, box, None, None) == vp.VP_ERR_ARG
+    assert vp.lib.vp_q0_box(n3, P(64), 0.5, box, None, None) == vp.VP_ERR_ARG
+    assert vp.lib.vp_q0_box(n3, P(64), float("nan"), box, None, None) == vp.VP_ERR_ARG
+    src2 = vp.make_grid((5, 5, 5), (0.0, 0.0, 0.0), 1e-3)
+    assert vp.lib.vp_restrict_to_nested_box(ctypes.byref(src2), P(64), ctypes.byref(src2), P(64), 4,
+                                            None) == vp.VP_ERR_ARG
     g8 = vp.make_grid((8, 8, 8), (0, 0, 0), 1e-4)
     assert vp.lib.vp_plan_retarget(None, ctypes.byref(g8), 2, 1e6, ctypes.byref(_medium(vp))) == vp.VP_ERR_ARG
     assert vp.lib.vp_profile_enable(None, 1) == vp.VP_ERR_ARG

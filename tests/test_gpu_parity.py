@@ -175,6 +175,41 @@ def test_restriction_matches_oracle(vp):
     assert rel_l2(host(same), f.astype(np.complex64).astype(np.complex128)) <= 1e-7
 
 
+@pytest.mark.parametrize("quadratic", [False, True])
+@pytest.mark.parametrize("case", ["several_tiles", "coarser_target", "flat_axis", "two_point_axis"])
+def test_restriction_tiles_and_direct_form(vp, case, quadratic):
+    """Shared-memory tiles (target spacing <= ~source spacing) over several ragged
+    8 x 64 blocks, the direct form for a coarser target, and a one-voxel source axis."""
+    if case == "several_tiles":
+        src = synth.Grid((12, 40, 90), (0.0, 0.0, 0.0), 2.0e-4)
+        dst = synth.Grid((9, 53, 130), (1.0e-4, 3.0e-4, 1.1e-4), 1.3e-4)
+    elif case == "coarser_target":
+        src = synth.Grid((30, 31, 32), (0.0, 0.0, 0.0), 1.0e-4)
+        dst = synth.Grid((10, 11, 12), (2.0e-4, 1.0e-4, 3.0e-4), 2.5e-4)
+    elif case == "flat_axis":
+        src = synth.Grid((1, 20, 70), (0.001, 0.0, 0.0), 2.0e-4)
+        dst = synth.Grid((1, 25, 90), (0.001, 1.0e-4, 2.0e-4), 1.4e-4)
+    else:
+        src = synth.Grid((2, 20, 70), (0.001, 0.0, 0.0), 2.0e-4)
+        dst = synth.Grid((2, 25, 90), (0.00105, 1.0e-4, 2.0e-4), 1.4e-4)
+    f = synth.random_field(src.n, seed=7)
+    out = torch.empty(dst.n, dtype=torch.complex64, device="cuda")
+    vp.vp_restrict_to_nested_box(src, dev(f), dst, out, quadratic=quadratic)
+    ref = (interp.restrict_quadratic if quadratic else interp.restrict_trilinear)(f, src, dst)
+    assert rel_l2(host(out), ref) <= 1e-6
+
+
+def test_quadratic_restriction_exact_on_triquadratic_field(vp):
+    src = synth.Grid((21, 19, 23), (0.01, -0.003, -0.0032), 3.1e-4)
+    dst = synth.centred_grid((30, 27, 33), 1.7e-4, (0.0131, -0.0001, 0.0002))
+    X, Y, Z = np.meshgrid(src.axis(0), src.axis(1), src.axis(2), indexing="ij")
+    Xd, Yd, Zd = np.meshgrid(dst.axis(0), dst.axis(1), dst.axis(2), indexing="ij")
+    q = lambda x, y, z: (1 + 30 * (x - 0.013) + 900 * (x - 0.013) ** 2) * (2 - 40 * y + 1e3 * y * y) * (1j + 50 * z)
+    out = torch.empty(dst.n, dtype=torch.complex64, device="cuda")
+    vp.vp_restrict_to_nested_box(src, dev(q(X, Y, Z)), dst, out, quadratic=True)
+    assert rel_l2(host(out), q(Xd, Yd, Zd)) <= 1e-6
+
+
 def test_restriction_not_nested(vp):
     src = synth.Grid((5, 5, 5), (0.0, 0.0, 0.0), 1e-3)
     dst = synth.Grid((3, 3, 3), (0.0, 0.0, 0.0031), 1e-3)

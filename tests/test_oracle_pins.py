@@ -302,3 +302,46 @@ def test_trilinear_restriction_rejects_targets_outside():
     dst = synth.Grid((3, 3, 3), (0.0, 0.0, 0.0031), 1e-3)
     with pytest.raises(ValueError):
         interp.restrict_trilinear(np.zeros((5, 5, 5), complex), src, dst)
+
+
+def test_quadratic_restriction_is_exact_on_triquadratic_fields():
+    src = synth.Grid((9, 7, 11), (0.01, -0.002, 0.003), 3e-4)
+    dst = synth.centred_grid((13, 10, 12), 1.6e-4, (0.0112, -0.0011, 0.0045))
+    rng = np.random.default_rng(1)
+    c = rng.standard_normal((3, 3, 3)) + 1j * rng.standard_normal((3, 3, 3))
+
+    def quad(g, deg=2):
+        X, Y, Z = np.meshgrid(g.axis(0), g.axis(1), g.axis(2), indexing="ij")
+        out = np.zeros(X.shape, dtype=np.complex128)
+        for p in range(deg + 1):
+            for q in range(deg + 1):
+                for r in range(deg + 1):
+                    out += c[p % 3, q % 3, r % 3] * (X * 100) ** p * (Y * 100) ** q * (Z * 100) ** r
+        return out
+
+    got = interp.restrict_quadratic(quad(src), src, dst)
+    want = quad(dst)
+    assert np.max(np.abs(got - want)) <= 1e-11 * np.max(np.abs(want))
+    # a cubic term is not reproduced: the stencil really is three points wide
+    cub = quad(src, 3)
+    err = np.max(np.abs(interp.restrict_quadratic(cub, src, dst) - quad(dst, 3)))
+    assert err > 1e-6 * np.max(np.abs(quad(dst, 3)))
+    # coincident grids: identity
+    f = synth.random_field(src.n, 5)
+    assert np.max(np.abs(interp.restrict_quadratic(f, src, src) - f)) <= 1e-13 * np.max(np.abs(f))
+
+
+def test_quadratic_restriction_single_and_two_point_axes():
+    # one-voxel axis takes its value; two-voxel axis is linear
+    src = synth.Grid((1, 2, 6), (0.0, 0.0, 0.0), 1e-3)
+    dst = synth.Grid((1, 3, 4), (0.0, 0.0, 1.5e-3), 5e-4)
+    f = synth.random_field(src.n, 6)
+    got = interp.restrict_quadratic(f, src, dst)
+    # along y (2 points) linear in y; along z quadratic through 3 nearest
+    for iy, y in enumerate([0.0, 0.5, 1.0]):
+        for iz, t in enumerate([1.5, 2.0, 2.5, 3.0]):
+            c = min(max(int(np.floor(t + 0.5)), 1), 4)
+            u = t - c
+            wz = {c - 1: u * (u - 1) / 2, c: 1 - u * u, c + 1: u * (u + 1) / 2}
+            want = sum(w * ((1 - y) * f[0, 0, k] + y * f[0, 1, k]) for k, w in wz.items())
+            assert abs(got[0, iy, iz] - want) <= 1e-13
