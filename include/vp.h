@@ -160,13 +160,20 @@ VP_API int vp_kernel_spectrum_set(vp_plan_t p, const void* src_device, vp_stream
 /* ---- source assembly -----------------------------------------------------------
  * f_n = C_n * sum_{m=1}^{n-1} p_m p_{n-m} (Eq. 2.6; Eqs. 3.5-3.8 for n = 2..5).
  * lower[m-1] is p_m on the plan's grid (device pointer, N voxels), n_lower must be
- * n - 1 (>= 1).  flags must be 0 (conjugate terms of Eq. 2.5 are not implemented).
+ * n - 1 (>= 1).
+ * flags & VP_SRC_CONJ: the full cascade of Eq. 2.5 instead, which keeps the products
+ *   with harmonics above n:  f_n = C_n [ sum_{m=1}^{n-1} p_m p_{n-m}
+ *   + 2 sum_{m=n+1}^{N_h} p_m conj(p_{m-n}) ];  lower[m-1] = p_m for m = 1..N_h with
+ *   n_lower = N_h (n <= N_h <= 8, N_h >= 2), every entry non-NULL (p_n itself enters
+ *   through p_{2n} conj(p_n) when 2n <= N_h); any harmonic n >= 1.  The source is
+ *   formed in its own pass (not fused into the first sweep).
  * f_out != NULL: write f_n (N voxels, complex64) there.
  * f_out == NULL: fuse the assembly with the zero padding and the first FFT sweep of
  *   vp_apply, leaving the transformed source in the plan's workspace; the next
  *   vp_apply(p, NULL, u, ...) on the same stream consumes it.
- * Errors: VP_ERR_ARG (null plan or field pointer, n_lower != n - 1, flags != 0),
+ * Errors: VP_ERR_ARG (null plan or field pointer, n_lower out of range, unknown flags),
  * VP_ERR_CUDA. */
+#define VP_SRC_CONJ 1
 VP_API int vp_source_assemble(vp_plan_t p, const void* const* lower, int n_lower, int flags,
                               void* f_out, vp_stream_t stream);
 
@@ -183,7 +190,9 @@ VP_API int vp_apply(vp_plan_t p, const void* f, void* u, vp_stream_t stream);
  * the voxel centres of grid dst (Section 6, step 2a).  For a target coordinate on
  * one axis, t = (x - o_src)/h_src, i0 = floor(t) clamped to [0, N-2], w = t - i0;
  * the result is the tensor product of (1-w) v[i0] + w v[i0+1].  Axis positions are
- * computed in FP64, weights applied in FP32.
+ * held as exact 40-bit fixed-point numbers, T_i = round(a 2^40) + i round(b 2^40) with
+ * a = (o_dst - o_src)/h_src and b = h_dst/h_src formed in FP64 (round half away from
+ * zero), and every index decision is taken on T_i; weights are applied in FP32.
  * Every target centre must lie within the box spanned by the source centres (a
  * relative slack of 1e-9 voxel is allowed); otherwise VP_ERR_NOT_NESTED unless
  * flags & VP_RESTRICT_ZERO_OUTSIDE, which writes zero there instead.
@@ -197,6 +206,35 @@ VP_API int vp_apply(vp_plan_t p, const void* f, void* u, vp_stream_t stream);
 #define VP_RESTRICT_QUADRATIC 2
 VP_API int vp_restrict_to_nested_box(const vp_grid* src, const void* src_field, const vp_grid* dst,
                                      void* dst_field, int flags, vp_stream_t stream);
+
+/* ---- field vector operations ----------------------------------------------------------
+ * Complex64 device arrays of n elements; FP32 arithmetic, FP64 accumulation for dot.
+ * Used by the fixed-point iteration of the full cascade and the VIE solver.
+ * vp_vec_axpby: out = a x + b y (y may be NULL: out = a x); out may alias x or y.
+ * vp_vec_mul:   out = x * y elementwise; out may alias x or y.
+ * vp_vec_dot:   out[0] + i out[1] = sum_i (conj_x ? conj(x_i) : x_i) y_i, to host
+ *               memory (synchronises the stream).
+ * Errors: VP_ERR_ARG (n < 1, null pointers), VP_ERR_CUDA. */
+VP_API int vp_vec_axpby(long long n, double a_re, double a_im, const void* x, double b_re, double b_im,
+                        const void* y, void* out, vp_stream_t stream);
+VP_API int vp_vec_mul(long long n, const void* x, const void* y, void* out, vp_stream_t stream);
+VP_API int vp_vec_dot(long long n, const void* x, const void* y, int conj_x, double out[2], vp_stream_t stream);
+
+/* ---- inhomogeneous medium: volume integral equation (Section 7) -----------------------
+ * Solves  p(x) - int G_{k_n}(x - y) q(y) p(y) dy = b(x)  (Eqs. 7.1-7.5 with the contrast
+ * q(y) = k_n(y)^2 - kbar_n^2, zero where the medium is the background of the plan), in
+ * the quadrature of vp_apply: (I - V_{k_n} Q) p = b on the plan's grid.  For n = 1, b is
+ * the incident field; for n >= 2 it is the potential of the harmonic's source.
+ * BiCGStab, two operator applications per iteration (each: q x, vp_apply, x - V[q x]),
+ * inner products in FP64.  q, b: device complex64 (N voxels); x: in the initial guess,
+ * out the solution.  Stops when ||b - A x|| <= tol ||b|| (*relres, host) or after
+ * max_iter iterations (*iters, host; either may be NULL); a breakdown of the recurrence
+ * returns the current iterate with its residual.  Allocates 8 N-voxel fields from the
+ * stream-ordered pool and synchronises the stream once per inner product.
+ * Errors: VP_ERR_ARG (null pointers, tol <= 0, max_iter < 1), VP_ERR_STATE (spectrum not
+ * built), VP_ERR_NOMEM, VP_ERR_CUDA. */
+VP_API int vp_vie_solve(vp_plan_t plan, const void* q, const void* b, void* x, double tol, int max_iter,
+                        int* iters, double* relres, vp_stream_t stream);
 
 /* ---- integration-domain selection (Section 5) -------------------------------------
  * Smallest voxel box D of the N^3 field f (complex64, device) outside which

@@ -59,3 +59,47 @@ def nested_run(p1_on_first: np.ndarray, grids: Dict[int, object], f0: float, med
         fields[n] = harmonic(n, lower, g.h, f0, medium)
         home[n] = g
     return {n: v for n, v in fields.items() if n >= 2}
+
+
+# ---- the full cascade with conjugate terms (Eq. 2.5) ---------------------------------
+# Matching the e^{-i n omega t} coefficients of the Westervelt equation with the field
+# written as (1/2) sum_n (p_n e^{-i n omega t} + conj(p_n) e^{i n omega t}) gives, for
+# every n >= 1, a source that also draws on the harmonics above n:
+#   f_n = C_n sum_{m >= 1} p_m (p_{n-m} + 2 conj(p_{m-n})),  p_j = 0 for j <= 0,
+# truncated at the highest harmonic kept, N_h.  The weakly nonlinear cascade (Eq. 2.6)
+# is the same sum without the conjugate products.
+
+def source_term_full(n: int, fields: Sequence[np.ndarray], f0: float, medium) -> np.ndarray:
+    """Eq. 2.5 source of harmonic n from ``fields[m-1]`` = p_m, m = 1..N_h (same grid)."""
+    nh = len(fields)
+    if not 1 <= n <= nh:
+        raise ValueError("harmonic outside 1..N_h")
+    p = [None] + [np.asarray(v, dtype=np.complex128) for v in fields]
+    acc = np.zeros_like(p[1])
+    for m in range(1, nh + 1):
+        if 1 <= n - m:
+            acc = acc + p[m] * p[n - m]
+        if 1 <= m - n:
+            acc = acc + 2.0 * p[m] * np.conj(p[m - n])
+    return physics.source_coefficient(n, f0, medium) * acc
+
+
+def full_cascade(p_inc: np.ndarray, nh: int, h: float, f0: float, medium, iters: int,
+                 start=None):
+    """Jacobi fixed-point iteration of Eq. 2.5 on one grid:
+    p_1 <- p_inc + V_{k_1}[f_1(p)],  p_n <- V_{k_n}[f_n(p)] for n = 2..N_h,
+    starting from ``start`` (default: the weakly nonlinear cascade of Eq. 2.6).
+    Returns the list of iterates' fields after ``iters`` sweeps."""
+    if start is None:
+        p = [np.asarray(p_inc, dtype=np.complex128)]
+        for n in range(2, nh + 1):
+            p.append(harmonic(n, p[:n - 1], h, f0, medium))
+    else:
+        p = [np.asarray(v, dtype=np.complex128) for v in start]
+    for _ in range(iters):
+        new = []
+        for n in range(1, nh + 1):
+            u = potential.apply_fft(source_term_full(n, p, f0, medium), h, physics.wavenumber(n, f0, medium))
+            new.append(p_inc + u if n == 1 else u)
+        p = new
+    return p

@@ -12,9 +12,14 @@ clamped to [0, N-2]; weight w = t - i0; the value is the tensor product of the
 
 Quadratic (the higher-order option Section 6 mentions): per axis the Lagrange
 polynomial through the three nearest source centres c - 1, c, c + 1 with
-c = floor(t + 1/2) clamped to [1, N-2], evaluated at u = t - c.
+c = floor(t + 1/2) clamped to [1, N-2], evaluated at u = t - c.  At a half-integer t
+two stencils are equally near; which one is used is decided on t held as an exact
+40-bit fixed-point number (the positions the C interface defines), so that both
+implementations take the same decision.
 """
 from __future__ import annotations
+
+import math
 
 import numpy as np
 
@@ -66,10 +71,29 @@ def restrict_trilinear(src: np.ndarray, src_grid, dst_grid) -> np.ndarray:
     return out
 
 
-def _axis_quadratic(src_origin: float, src_h: float, src_n: int, dst_coords: np.ndarray):
+FIX_BITS = 40
+
+
+def _round_half_away(x: float) -> int:
+    return int(math.floor(x + 0.5)) if x >= 0 else -int(math.floor(-x + 0.5))
+
+
+def _fixed_positions(src_origin: float, src_h: float, dst_origin: float, dst_h: float, count: int) -> np.ndarray:
+    """Target positions in source-voxel units as exact integers with FIX_BITS fractional
+    bits: T_i = round(a 2^F) + i round(b 2^F), a = (o_dst - o_src) / h_src, b = h_dst / h_src.
+    The quadratic stencil's centre is a discontinuous function of t (at half-integers),
+    so it is decided on these exact positions, as the header of the C interface defines."""
+    a = (dst_origin - src_origin) / src_h
+    b = dst_h / src_h
+    A = _round_half_away(a * 2.0 ** FIX_BITS)
+    B = _round_half_away(b * 2.0 ** FIX_BITS)
+    return np.array([A + i * B for i in range(count)], dtype=object)
+
+
+def _axis_quadratic(src_origin: float, src_h: float, src_n: int, dst_coords: np.ndarray, T=None):
     """Indices (k, 3) and weights (k, 3) of the quadratic Lagrange interpolant through the
     three source centres nearest to each target; a two-centre axis stays linear and a
-    one-centre axis takes its only value."""
+    one-centre axis takes its only value.  T: exact fixed-point positions (optional)."""
     t = (dst_coords - src_origin) / src_h
     k = len(t)
     if src_n < 3:
@@ -79,8 +103,13 @@ def _axis_quadratic(src_origin: float, src_h: float, src_n: int, dst_coords: np.
         return idx, wts
     if np.any(t < -TOL) or np.any(t > (src_n - 1) + TOL):
         raise ValueError("target outside the source grid")
-    c = np.clip(np.floor(t + 0.5).astype(np.int64), 1, src_n - 2)
-    u = t - c
+    if T is None:
+        c = np.clip(np.floor(t + 0.5).astype(np.int64), 1, src_n - 2)
+        u = t - c
+    else:
+        half = 1 << (FIX_BITS - 1)
+        c = np.array([min(max((int(v) + half) >> FIX_BITS, 1), src_n - 2) for v in T], dtype=np.int64)
+        u = np.array([(int(v) - (int(ci) << FIX_BITS)) / 2.0 ** FIX_BITS for v, ci in zip(T, c)])
     # Lagrange basis on the nodes -1, 0, 1
     l_m = u * (u - 1.0) / 2.0
     l_0 = (1.0 - u) * (1.0 + u)
@@ -94,7 +123,8 @@ def restrict_quadratic(src: np.ndarray, src_grid, dst_grid) -> np.ndarray:
     idx, wts = [], []
     for a in range(3):
         coords = dst_grid.origin[a] + dst_grid.h * np.arange(dst_grid.n[a], dtype=np.float64)
-        i, w = _axis_quadratic(src_grid.origin[a], src_grid.h, src_grid.n[a], coords)
+        T = _fixed_positions(src_grid.origin[a], src_grid.h, dst_grid.origin[a], dst_grid.h, dst_grid.n[a])
+        i, w = _axis_quadratic(src_grid.origin[a], src_grid.h, src_grid.n[a], coords, T)
         idx.append(i)
         wts.append(w)
     out = np.zeros(tuple(dst_grid.n), dtype=np.complex128)

@@ -15,7 +15,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libvp.so")
 
 SOURCES = ["vp_api.cu", "vp_sweeps.cu", "vp_kernels.cu", "vp_static.cu", "vp_sweeps2_part0.cu",
-           "vp_sweeps2_part1.cu", "vp_sweeps2_part2.cu", "fno.cu"]
+           "vp_sweeps2_part1.cu", "vp_sweeps2_part2.cu", "fno.cu", "vp_vec.cu", "vp_vie.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -799,7 +799,29 @@ VP_API int vp_kernel_spectrum_set(vp_plan_t p, const void* src, vp_stream_t stre
 
 VP_API int vp_source_assemble(vp_plan_t p, const void* const* lower, int n_lower, int flags, void* f_out,
                               vp_stream_t stream) {
-  if (!p || !lower || flags != 0) return VP_ERR_ARG;
+  if (!p || !lower || (flags & ~VP_SRC_CONJ)) return VP_ERR_ARG;
+  if (flags & VP_SRC_CONJ) {
+    // Eq. 2.5: lower[m-1] = p_m for m = 1..n_lower (= N_h); every entry may be read
+    // (p_n itself enters through p_{2n} conj(p_n) when 2n <= N_h)
+    const int n = p->harmonic;
+    if (n_lower < n || n_lower < 2 || n_lower > vp::kMaxLower) return VP_ERR_ARG;
+    for (int i = 0; i < n_lower; ++i)
+      if (!lower[i]) return VP_ERR_ARG;
+    const float2* fields[vp::kMaxLower] = {};
+    for (int i = 0; i < n_lower; ++i) fields[i] = (const float2*)lower[i];
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long count = (long long)p->n[0] * p->n[1] * p->n[2];
+    // without f_out the source goes to the plan's second workspace buffer, which the
+    // first sweep reads before the second sweep writes it
+    float2* dst = f_out ? (float2*)f_out : p->wsB;
+    cudaError_t e = vp::launch_source_full(fields, n, n_lower, (float)p->cn, dst, count, s);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (f_out) return VP_OK;
+    const int st = run_sweep(p, 0, p->wsB, nullptr, nullptr, s);
+    if (st != VP_OK) return st;
+    p->staged = true;
+    return VP_OK;
+  }
   if (p->harmonic < 2 || n_lower != p->harmonic - 1) return VP_ERR_ARG;
   for (int i = 0; i < n_lower; ++i)
     if (!lower[i]) return VP_ERR_ARG;
@@ -853,6 +875,39 @@ VP_API int vp_restrict_to_nested_box(const vp_grid* src, const void* src_field, 
   cudaError_t e = vp::launch_restrict((const float2*)src_field, src->n, (float2*)dst_field, dst->n, a, b,
                                       (flags & VP_RESTRICT_QUADRATIC) ? 2 : 1, flags & VP_RESTRICT_ZERO_OUTSIDE,
                                       (cudaStream_t)stream);
+  return cuda_status(e);
+}
+
+VP_API int vp_vec_axpby(long long n, double a_re, double a_im, const void* x, double b_re, double b_im,
+                        const void* y, void* out, vp_stream_t stream) {
+  if (n < 1 || !x || !out) return VP_ERR_ARG;
+  return cuda_status(vp::launch_axpby(n, make_float2((float)a_re, (float)a_im), (const float2*)x,
+                                      make_float2((float)b_re, (float)b_im), (const float2*)y, (float2*)out,
+                                      (cudaStream_t)stream));
+}
+
+VP_API int vp_vec_mul(long long n, const void* x, const void* y, void* out, vp_stream_t stream) {
+  if (n < 1 || !x || !y || !out) return VP_ERR_ARG;
+  return cuda_status(vp::launch_mul(n, (const float2*)x, (const float2*)y, (float2*)out, (cudaStream_t)stream));
+}
+
+VP_API int vp_vec_dot(long long n, const void* x, const void* y, int conj_x, double out[2], vp_stream_t stream) {
+  if (n < 1 || !x || !y || !out) return VP_ERR_ARG;
+  int dev = 0;
+  VP_TRY_CUDA(cudaGetDevice(&dev));
+  cudaStream_t s = (cudaStream_t)stream;
+  double* acc = nullptr;
+  cudaMemPool_t pool = scratch_pool(dev);
+  if (pool) {
+    VP_TRY_CUDA(cudaMallocFromPoolAsync((void**)&acc, 2 * sizeof(double), pool, s));
+  } else {
+    VP_TRY_CUDA(cudaMallocAsync((void**)&acc, 2 * sizeof(double), s));
+  }
+  cudaError_t e = vp::launch_dot(n, (const float2*)x, (const float2*)y, conj_x ? 1 : 0, acc, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, acc, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+  cudaError_t e2 = cudaFreeAsync(acc, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = e2;
   return cuda_status(e);
 }
 

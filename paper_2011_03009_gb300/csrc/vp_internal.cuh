@@ -125,6 +125,13 @@ cudaError_t launch_source_assemble(const float2* const* lower, int harmonic, flo
 cudaError_t launch_restrict(const float2* src, const int ns[3], float2* dst, const int nd[3],
                             const double a[3], const double b[3], int order, int zero_outside,
                             cudaStream_t s);
+// field vector operations and the Eq. 2.5 source (vp_vec.cu)
+cudaError_t launch_axpby(long long n, float2 a, const float2* x, float2 b, const float2* y, float2* out,
+                         cudaStream_t s);
+cudaError_t launch_mul(long long n, const float2* x, const float2* y, float2* out, cudaStream_t s);
+cudaError_t launch_dot(long long n, const float2* x, const float2* y, int conj_x, double* acc, cudaStream_t s);
+cudaError_t launch_source_full(const float2* const* fields, int n, int nh, float cn, float2* out, long long count,
+                               cudaStream_t s);
 // scratch: 8-byte max |f|^2 followed by int box[6]
 cudaError_t launch_q0_box(const float2* f, const int n[3], double factor, void* scratch, cudaStream_t s);
 cudaError_t launch_incident(const double* pts, int npts, const int n[3], const double origin[3],

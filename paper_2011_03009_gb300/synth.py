@@ -36,6 +36,8 @@ class Medium:
 
 
 WATER = Medium()
+# soft-tissue-like inclusion for the inhomogeneous-medium equations (Section 7)
+TISSUE = Medium(c0=1540.0, rho0=1000.0, beta=4.5, alpha0=5.0, eta=1.1)
 
 
 @dataclasses.dataclass(frozen=True)

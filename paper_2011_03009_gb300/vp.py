@@ -25,6 +25,7 @@ VP_ERR_TIMEOUT = -7
 VP_ERR_UNSUPPORTED = -8
 VP_RESTRICT_ZERO_OUTSIDE = 1
 VP_RESTRICT_QUADRATIC = 2
+VP_SRC_CONJ = 1
 MAX_PASS = 8
 MAX_LOWER = 8
 
@@ -80,6 +81,10 @@ def _load():
         "vp_profile_read": (I, [P, ctypes.POINTER(D), ctypes.POINTER(I), I]),
         "vp_version": (ctypes.c_char_p, []),
         "vp_apply_static": (I, [ctypes.POINTER(vp_grid), I, D, ctypes.POINTER(vp_medium), P, P, P]),
+        "vp_vie_solve": (I, [P, P, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D), P]),
+        "vp_vec_axpby": (I, [ctypes.c_longlong, D, D, P, D, D, P, P, P]),
+        "vp_vec_mul": (I, [ctypes.c_longlong, P, P, P, P]),
+        "vp_vec_dot": (I, [ctypes.c_longlong, P, P, I, ctypes.POINTER(D), P]),
         "vp_q0_box": (I, [ctypes.POINTER(I), P, D, ctypes.POINTER(I), ctypes.POINTER(D), P]),
         "vp_batch_create": (I, [I, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P),
                                 ctypes.POINTER(P)]),
@@ -186,13 +191,24 @@ class Plan:
     def kernel_spectrum_set(self, src, stream=None):
         _check(lib.vp_kernel_spectrum_set(self._h, _ptr(src), _stream(stream)), "vp_kernel_spectrum_set")
 
-    def source_assemble(self, lower, f_out=None, stream=None):
+    def source_assemble(self, lower, f_out=None, stream=None, conj: bool = False):
+        """Eq. 2.6 from lower = [p_1 .. p_{n-1}], or with conj=True the full source of
+        Eq. 2.5 from lower = [p_1 .. p_{N_h}] (all entries are read)."""
         arr = (ctypes.c_void_p * max(1, len(lower)))(*[_ptr(t).value for t in lower])
-        _check(lib.vp_source_assemble(self._h, arr, len(lower), 0, _ptr(f_out), _stream(stream)),
-               "vp_source_assemble")
+        _check(lib.vp_source_assemble(self._h, arr, len(lower), VP_SRC_CONJ if conj else 0, _ptr(f_out),
+                                      _stream(stream)), "vp_source_assemble")
 
     def apply(self, f, u, stream=None):
         _check(lib.vp_apply(self._h, _ptr(f), _ptr(u), _stream(stream)), "vp_apply")
+
+    def vie_solve(self, q, b, x, tol: float = 1e-6, max_iter: int = 200, stream=None):
+        """Solve x - V[q x] = b (Section 7) by BiCGStab in the library; x holds the initial
+        guess and receives the solution.  Returns (iterations, relative residual)."""
+        it = ctypes.c_int(0)
+        res = ctypes.c_double(0.0)
+        _check(lib.vp_vie_solve(self._h, _ptr(q), _ptr(b), _ptr(x), float(tol), int(max_iter), ctypes.byref(it),
+                                ctypes.byref(res), _stream(stream)), "vp_vie_solve")
+        return it.value, res.value
 
     def profile_enable(self, on: bool = True):
         _check(lib.vp_profile_enable(self._h, 1 if on else 0), "vp_profile_enable")
@@ -277,6 +293,24 @@ def vp_restrict_to_nested_box(src_grid, src, dst_grid, dst, zero_outside: bool =
     flags = (VP_RESTRICT_ZERO_OUTSIDE if zero_outside else 0) | (VP_RESTRICT_QUADRATIC if quadratic else 0)
     _check(lib.vp_restrict_to_nested_box(ctypes.byref(gs), _ptr(src), ctypes.byref(gd), _ptr(dst), flags,
                                          _stream(stream)), "vp_restrict_to_nested_box")
+
+
+def vp_vec_axpby(a, x, b, y, out, stream=None):
+    """out = a x + b y (complex scalars; y may be None)."""
+    a, b = complex(a), complex(b)
+    _check(lib.vp_vec_axpby(x.numel(), a.real, a.imag, _ptr(x), b.real, b.imag, _ptr(y), _ptr(out), _stream(stream)),
+           "vp_vec_axpby")
+
+
+def vp_vec_mul(x, y, out, stream=None):
+    _check(lib.vp_vec_mul(x.numel(), _ptr(x), _ptr(y), _ptr(out), _stream(stream)), "vp_vec_mul")
+
+
+def vp_vec_dot(x, y, conj_x: bool = True, stream=None) -> complex:
+    """sum conj(x) y (or sum x y), accumulated in FP64."""
+    out = (ctypes.c_double * 2)()
+    _check(lib.vp_vec_dot(x.numel(), _ptr(x), _ptr(y), 1 if conj_x else 0, out, _stream(stream)), "vp_vec_dot")
+    return complex(out[0], out[1])
 
 
 def vp_q0_box(field, q0: float, stream=None):

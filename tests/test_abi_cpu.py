@@ -101,6 +101,13 @@ def test_other_calls_reject_bad_arguments_on_the_host(vp):
     assert vp.lib.vp_apply(None, None, P(16), None) == vp.VP_ERR_ARG
     assert vp.lib.vp_source_assemble(None, None, 1, 0, None, None) == vp.VP_ERR_ARG
     assert vp.lib.vp_destroy(None) == vp.VP_OK
+    assert vp.lib.vp_vie_solve(None, P(64), P(64), P(64), 1e-6, 10, None, None, None) == vp.VP_ERR_ARG
+    assert vp.lib.vp_vec_axpby(0, 1.0, 0.0, P(64), 0.0, 0.0, None, P(64), None) == vp.VP_ERR_ARG
+    assert vp.lib.vp_vec_mul(4, None, P(64), P(64), None) == vp.VP_ERR_ARG
+    d2 = (ctypes.c_double * 2)()
+    assert vp.lib.vp_vec_dot(4, P(64), None, 1, d2, None) == vp.VP_ERR_ARG
+    assert vp.lib.vp_source_assemble(None, None, 1, 1, None, None) == vp.VP_ERR_ARG
+    assert vp.lib.vp_source_assemble(None, None, 1, 4, None, None) == vp.VP_ERR_ARG  # unknown flag
     n3 = (ctypes.c_int * 3)(4, 4, 4)
     box = (ctypes.c_int * 6)()
     assert vp.lib.vp_q0_box(n3, None, -1.0, box, None, None) == vp.VP_ERR_ARG

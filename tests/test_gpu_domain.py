@@ -44,3 +44,33 @@ def test_q0_box_zero_field_and_errors(vp):
     assert vp.vp_q0_box(z, -1.0)[:2] == ((0, 0, 0), (3, 4, 5))
     with pytest.raises(vp.VpError):
         vp.vp_q0_box(z, 0.5)
+
+
+def test_q0_study_error_shrinks_with_the_box(vp):
+    """Harmonic 3's source on its grid: a lower Q0 keeps a larger box and gives a smaller
+    axis error; a box covering the whole grid reproduces the reference exactly."""
+    from paper_2011_03009_gb300 import domain
+    bowl = synth.Bowl(l=0.02, R=0.01, f0=1.0e6, p0=1.0e6)
+    g2 = synth.focus_grid(bowl, (48, 40, 40), 2)
+    g3 = synth.focus_grid(bowl, (48, 40, 40), 3)
+    pts = torch.from_numpy(synth.sample_bowl_points(bowl, 1024, 3)).cuda()
+    p1 = torch.empty(g2.n, dtype=torch.complex64, device="cuda")
+    vp.vp_incident_field(g2, pts, bowl, synth.WATER, p1)
+    plan2 = vp.vp_plan(g2, 2, bowl.f0, synth.WATER)
+    plan2.kernel_fft()
+    p2 = torch.empty_like(p1)
+    plan2.source_assemble([p1])
+    plan2.apply(None, p2)
+    r1 = torch.empty(g3.n, dtype=torch.complex64, device="cuda")
+    r2 = torch.empty_like(r1)
+    vp.vp_restrict_to_nested_box(g2, p1, g3, r1)
+    vp.vp_restrict_to_nested_box(g2, p2, g3, r2)
+    plan3 = vp.vp_plan(g3, 3, bowl.f0, synth.WATER)
+    f3 = torch.empty_like(r1)
+    plan3.source_assemble([r1, r2], f_out=f3)
+    rows = domain.q0_study(g3, 3, bowl.f0, f3, r1, [-0.5, -1.0, -2.0, -12.0])
+    errs = [r["axis_error_pct"] for r in rows]
+    fr = [r["volume_fraction"] for r in rows]
+    assert all(e is not None for e in errs)
+    assert fr == sorted(fr) and fr[-1] == 1.0
+    assert errs[2] <= errs[0] and errs[-1] == 0.0

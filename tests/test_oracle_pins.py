@@ -345,3 +345,42 @@ def test_quadratic_restriction_single_and_two_point_axes():
             wz = {c - 1: u * (u - 1) / 2, c: 1 - u * u, c + 1: u * (u + 1) / 2}
             want = sum(w * ((1 - y) * f[0, 0, k] + y * f[0, 1, k]) for k, w in wz.items())
             assert abs(got[0, iy, iz] - want) <= 1e-13
+
+
+# ----------------------------------------------------------------------------- Eq. 2.5
+
+def test_full_source_terms_written_out():
+    """Eq. 2.5 with N_h = 3 expanded by hand on constant fields:
+    f1 = C1 * 2 (p2 p1* + p3 p2*),  f2 = C2 (p1^2 + 2 p3 p1*),  f3 = C3 (2 p1 p2)."""
+    a, b, c = 0.3 + 0.4j, -0.7 + 0.2j, 0.1 - 0.9j
+    f = [np.full((2, 2, 2), v) for v in (a, b, c)]
+    med = synth.WATER
+    C = {n: physics.source_coefficient(n, 1.0e6, med) for n in (1, 2, 3)}
+    got = {n: cascade.source_term_full(n, f, 1.0e6, med)[0, 0, 0] for n in (1, 2, 3)}
+    want = {1: C[1] * 2 * (b * np.conj(a) + c * np.conj(b)),
+            2: C[2] * (a * a + 2 * c * np.conj(a)),
+            3: C[3] * (2 * a * b)}
+    for n in (1, 2, 3):
+        assert abs(got[n] - want[n]) <= 1e-15 * abs(want[n])
+    # without harmonics above n the full source is the weakly nonlinear one (Eq. 2.6)
+    for n in (2, 3):
+        assert np.allclose(cascade.source_term_full(n, f[:n], 1.0e6, med),
+                           cascade.source_term(n, f[:n - 1], 1.0e6, med), rtol=1e-15, atol=0)
+
+
+def test_full_cascade_fixed_point_converges_and_is_a_fixed_point():
+    """The Jacobi iteration contracts (the nonlinear coupling is weak) and its limit
+    satisfies every equation of Eq. 2.5 to round-off."""
+    n = (12, 10, 8)
+    h = 2.0e-4
+    p_inc = synth.random_field(n, 3, scale=4.0e5)
+    it = cascade.full_cascade(p_inc, 3, h, 1.0e6, synth.WATER, iters=12)
+    nxt = cascade.full_cascade(p_inc, 3, h, 1.0e6, synth.WATER, iters=1, start=it)
+    for a, b in zip(it, nxt):
+        assert np.linalg.norm(a - b) <= 1e-9 * np.linalg.norm(b)
+    # residual of each equation
+    for k in range(1, 4):
+        u = potential.apply_fft(cascade.source_term_full(k, it, 1.0e6, synth.WATER), h,
+                                physics.wavenumber(k, 1.0e6, synth.WATER))
+        want = p_inc + u if k == 1 else u
+        assert np.linalg.norm(it[k - 1] - want) <= 1e-9 * np.linalg.norm(want)
