@@ -38,10 +38,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="nested3", choices=["small", "nested3", "nested5", "batch64"])
+    ap.add_argument("--workload", default="nested3",
+                    choices=["small", "nested3", "nested5", "batch64", "vie", "fullcascade", "q0"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--check", action="store_true", help="per-harmonic rel-L2 vs the FP64 oracle (slow)")
     return ap.parse_args()
 
 
@@ -366,9 +366,6 @@ def run_ours(args, world, rank, local):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w)
 
-    check = None
-    if args.check and rank == 0:
-        check = rel_l2_check(gw)
 
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
@@ -384,8 +381,6 @@ def run_ours(args, world, rank, local):
         "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
         "gpu_launches": gw.launches_per_step() * args.steps, "wall_s_timed": round(t_wall, 4),
     }
-    if check is not None:
-        line["rel_l2_vs_oracle"] = check
     if rank == 0:
         print(json.dumps(line))
 
@@ -458,30 +453,6 @@ def cpu_baseline(w):
     return {"value": vox * reps / t_total, "unit": METRIC, "cores": os.cpu_count(), "kind": "oracle",
             "sample": f"FP64 oracle apply_fft (zero-padded FFT convolution, spectrum precomputed) on the "
                       f"{'x'.join(map(str, g.n))} grid, {reps} repetitions"}
-
-
-def rel_l2_check(gw):
-    import numpy as np
-    from oracle import cascade, interp, physics, potential
-    w = gw.w
-    res = {}
-    if w.v1_grid is not None:
-        p1 = gw.p1_v1.cpu().numpy().astype(np.complex128)
-        ref = potential.apply_fft(p1, w.v1_grid.h, physics.wavenumber(1, w.bowl.f0, w.medium))
-        got = gw.outs[1].cpu().numpy().astype(np.complex128)
-        res["1"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
-    fields = {1: (gw.p1.cpu().numpy().astype(np.complex128), w.p1_grid)}
-    for st in w.steps:
-        n = st.harmonic
-        lower = []
-        for m in range(1, n):
-            f, g = fields[m]
-            lower.append(f if g is st.grid else interp.restrict_trilinear(f, g, st.grid))
-        ref = cascade.harmonic(n, lower, st.grid.h, w.bowl.f0, w.medium)
-        got = gw.outs[n].cpu().numpy().astype(np.complex128)
-        res[str(n)] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
-        fields[n] = (got, st.grid)
-    return res
 
 
 def run_reference(args, world, rank):
@@ -624,6 +595,129 @@ def run_batch(args, world, rank, local):
     print(json.dumps(line))
 
 
+def _dev_timeit(fn, reps, warmup):
+    import torch
+    for _ in range(max(1, warmup)):
+        fn()
+    torch.cuda.synchronize()
+    a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        fn()
+    z.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(z) / reps
+
+
+def _line(metric, value, unit, ms, steps, warmup, higher, config, **extra):
+    d = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": steps, "warmup": warmup,
+         "ms_per_step": ms, "higher_is_better": higher, "scaling": "weak", "vs_baseline": None, "dtype": "c64",
+         "data": "synthetic", "config": config}
+    d.update(extra)
+    print(json.dumps(d))
+
+
+def _focal_setup(n, harmonic_spacing, n_points=4096, seed=2):
+    """128^3-class focal grid of the 3 cm / 6 cm / 1.1 MHz bowl and p1 on it."""
+    import torch
+    from paper_2011_03009_gb300 import synth, vp
+    bowl = synth.Bowl(l=0.06, R=0.03, f0=1.1e6, p0=1.0e6)
+    g = synth.focus_grid(bowl, (n, n, n), harmonic_spacing)
+    pts = torch.from_numpy(synth.sample_bowl_points(bowl, n_points, seed)).cuda()
+    p1 = torch.empty(g.n, dtype=torch.complex64, device="cuda")
+    vp.vp_incident_field(g, pts, bowl, synth.WATER, p1)
+    return bowl, g, p1
+
+
+def run_vie(args):
+    """Inhomogeneous medium (Section 7): tissue sphere (r = 4 mm) at the focus of the
+    nested3 bowl, harmonic 1 on a 128^3 grid at lambda_1/6; b = p_inc; BiCGStab to 1e-6."""
+    import numpy as np
+    import torch
+    from paper_2011_03009_gb300 import synth, vp
+    bowl, g, p_inc = _focal_setup(128, 1)
+    X, Y, Z = np.meshgrid(g.axis(0), g.axis(1), g.axis(2), indexing="ij")
+    inside = (X - bowl.l - 1e-3) ** 2 + (Y - 5e-4) ** 2 + Z ** 2 <= 4e-3 ** 2
+    # wavenumbers (with attenuation) from the library's own plan constants
+    plan = vp.vp_plan(g, 1, bowl.f0, synth.WATER)
+    inf = plan.info()
+    kbg = complex(inf.k_re, inf.k_im)
+    tplan = vp.vp_plan(synth.Grid((1, 1, 1), (0, 0, 0), g.h), 1, bowl.f0, synth.TISSUE)
+    kin = complex(tplan.info().k_re, tplan.info().k_im)
+    tplan.close()
+    q = torch.from_numpy(np.where(inside, kin * kin - kbg * kbg, 0.0).astype(np.complex64)).cuda()
+    plan.kernel_fft()
+    x = torch.zeros_like(p_inc)
+    stats = {}
+
+    def solve():
+        x.zero_()
+        stats["it"], stats["res"] = plan.vie_solve(q, p_inc, x, tol=1e-6, max_iter=200)
+
+    reps = max(1, min(args.steps, 5))
+    ms = _dev_timeit(solve, reps, min(args.warmup, 2))
+    applies = 2 * stats["it"] + 1
+    _line("VIE solves/s", 1e3 / ms, "solves/s", ms, reps, min(args.warmup, 2), True,
+          {"workload": "vie_tissue_sphere_r4mm_128cube_h1_R3cm_l6cm_1.1MHz", "grid": list(g.n),
+           "solver": "BiCGStab", "tol": 1e-6, "inclusion_voxels": int(inside.sum())},
+          iterations=stats["it"], relres=stats["res"], ms_per_iteration=ms / max(1, stats["it"]),
+          operator_applies=applies, voxel_potentials_per_s=applies * g.voxels / (ms / 1e3))
+
+
+def run_fullcascade(args):
+    """Eq. 2.5 with N_h = 5 on one 128^3 focal grid at lambda_5/6 (Jacobi from Eq. 2.6)."""
+    import torch
+    from paper_2011_03009_gb300 import cascade, synth
+    bowl, g, p_inc = _focal_setup(128, 5)
+    fc = cascade.FullCascade(g, 5, bowl.f0, synth.WATER)
+    stats = {}
+
+    def solve():
+        _, hist = fc.run(p_inc, max_iter=30, tol=1e-6)
+        stats["hist"] = hist
+
+    reps = max(1, min(args.steps, 3))
+    ms = _dev_timeit(solve, reps, min(args.warmup, 1))
+    sweeps = len(stats["hist"])
+    _line("full-cascade solves/s", 1e3 / ms, "solves/s", ms, reps, min(args.warmup, 1), True,
+          {"workload": "fullcascade_Nh5_128cube_h5spacing_R3cm_l6cm_1.1MHz", "grid": list(g.n), "harmonics": 5,
+           "tol": 1e-6},
+          sweeps=sweeps, change_history=stats["hist"], ms_per_sweep=ms / max(1, sweeps),
+          voxel_potentials_per_s=(5 * (sweeps + 1)) * g.voxels / (ms / 1e3))
+    fc.close()
+
+
+def run_q0(args):
+    """Section 5 domain study on the nested3 harmonic-3 source (256^3 at lambda_3/6)."""
+    import torch
+    from paper_2011_03009_gb300 import domain, synth, vp
+    wl = synth.WORKLOADS["nested3"]()
+    g2, g3 = wl.steps[0].grid, wl.steps[1].grid
+    pts = torch.from_numpy(synth.sample_bowl_points(wl.bowl, wl.n_points, wl.seed)).cuda()
+    p1 = torch.empty(g2.n, dtype=torch.complex64, device="cuda")
+    vp.vp_incident_field(g2, pts, wl.bowl, wl.medium, p1)
+    plan2 = vp.vp_plan(g2, 2, wl.bowl.f0, wl.medium)
+    plan2.kernel_fft()
+    p2 = torch.empty_like(p1)
+    plan2.source_assemble([p1])
+    plan2.apply(None, p2)
+    r1 = torch.empty(g3.n, dtype=torch.complex64, device="cuda")
+    r2 = torch.empty_like(r1)
+    vp.vp_restrict_to_nested_box(g2, p1, g3, r1)
+    vp.vp_restrict_to_nested_box(g2, p2, g3, r2)
+    plan3 = vp.vp_plan(g3, 3, wl.bowl.f0, wl.medium)
+    f3 = torch.empty_like(r1)
+    plan3.source_assemble([r1, r2], f_out=f3)
+    q0s = [-0.5, -1.0, -1.5, -2.0, -3.0, -4.0]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rows = domain.q0_study(g3, 3, wl.bowl.f0, f3, r1, q0s, wl.medium)
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    _line("Q0 study time", sec, "s", sec * 1e3, 1, 0, False,
+          {"workload": "q0_study_h3_256cube_nested3", "q0": q0s, "grid": list(g3.n)}, rows=rows)
+
+
 def main():
     args = parse()
     world, rank, local = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), \
@@ -634,6 +728,11 @@ def main():
     world, rank, local = dist_init(args)
     if args.workload == "batch64":
         run_batch(args, world, rank, local)
+    elif args.workload in ("vie", "fullcascade", "q0"):
+        import torch
+        torch.cuda.set_device(local)
+        if rank == 0:
+            {"vie": run_vie, "fullcascade": run_fullcascade, "q0": run_q0}[args.workload](args)
     else:
         run_ours(args, world, rank, local)
     if world > 1:
