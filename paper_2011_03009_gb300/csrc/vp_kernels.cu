@@ -137,6 +137,15 @@ struct AxisFix { long long A, B; int n; };
 //         ORD 1.
 // A one-voxel axis has cnt = 1, w = (1).  Returns whether t lies inside [0, n-1]
 // (with 1e-9 voxel of slack).
+// A fixed-point offset (kFixBits fractional bits) as a float: clamped to +-4 voxels
+// (offsets of in-range targets are within [-1.5, 1.5]), dropped to 24 fractional bits and
+// converted from 32 bits (a 64-bit integer conversion is a slow multi-cycle operation).
+__device__ __forceinline__ float frac_to_float(long long d) {
+  const long long lim = 4LL << kFixBits;
+  d = d < -lim ? -lim : (d > lim ? lim : d);
+  return (float)(int)(d >> (kFixBits - 24)) * (1.0f / 16777216.0f);
+}
+
 template <int ORD>
 __device__ __forceinline__ bool stencil(const AxisFix& m, int i, int& i0, float (&w)[3], int& cnt) {
   const long long T = m.A + (long long)i * m.B;
@@ -153,7 +162,7 @@ __device__ __forceinline__ bool stencil(const AxisFix& m, int i, int& i0, float 
     long long c = (T + (1LL << (kFixBits - 1))) >> kFixBits;  // floor(t + 1/2)
     if (c < 1) c = 1;
     if (c > m.n - 2) c = m.n - 2;
-    const float u = (float)(T - (c << kFixBits)) * (1.0f / (float)(1LL << kFixBits));
+    const float u = frac_to_float(T - (c << kFixBits));
     i0 = (int)c - 1;
     cnt = 3;
     w[0] = 0.5f * u * (u - 1.f);
@@ -166,7 +175,7 @@ __device__ __forceinline__ bool stencil(const AxisFix& m, int i, int& i0, float 
   if (fl > m.n - 2) fl = m.n - 2;
   i0 = (int)fl;
   cnt = 2;
-  const float f = fminf(fmaxf((float)(T - (fl << kFixBits)) * (1.0f / (float)(1LL << kFixBits)), 0.f), 1.f);
+  const float f = fminf(fmaxf(frac_to_float(T - (fl << kFixBits)), 0.f), 1.f);
   w[0] = 1.f - f;
   w[1] = f;
   return inside;
@@ -237,11 +246,13 @@ __global__ void __launch_bounds__(256) restrict_tiled_kernel(const float2* __res
   ze = min(ze + c_ - 1, snz - 1);
   const int ny_r = ye - ys + 1, nz_r = ze - zs + 1;  // <= kRsY, kRsZ by the host's spacing check
   const long long sy = snz, sx = (long long)sny * snz;
-  for (int e = threadIdx.x; e < cx * ny_r * nz_r; e += blockDim.x) {
-    const int zz = e % nz_r;
-    const int r = e / nz_r;
-    const int yy = r % ny_r, xi = r / ny_r;
-    tile[xi][yy][zz] = __ldg(&src[(x0 + xi) * sx + (ys + yy) * sy + zs + zz]);
+  // one warp per source row, lanes along z (coalesced, no index division)
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int r = warp; r < cx * ny_r; r += (int)(blockDim.x >> 5)) {
+    const int xi = r >= 2 * ny_r ? 2 : (r >= ny_r ? 1 : 0);
+    const int yy = r - xi * ny_r;
+    const float2* row = src + (x0 + xi) * sx + (ys + yy) * sy + zs;
+    for (int zz = lane; zz < nz_r; zz += 32) tile[xi][yy][zz] = __ldg(&row[zz]);
   }
   __syncthreads();
   const int iz = iz0 + threadIdx.x % kRtZ;
