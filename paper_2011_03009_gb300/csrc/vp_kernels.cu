@@ -56,41 +56,56 @@ __device__ cd self_cell_fp64(double kr, double ki, double a) {
   return cd_div(num, cd_mul(k, k));
 }
 
-__device__ __forceinline__ int lattice_offset(int m, int n, int M) {
-  if (m < n) return m;
-  if (m > M - n) return m - M;
-  return INT_MIN;
+// Distance in FP64 without a full-precision square root: one Newton step on the
+// single-precision reciprocal square root brings it to about 1e-14 relative.
+__device__ __forceinline__ double fp64_norm(double r2) {
+  double y = (double)rsqrtf((float)r2);
+  y = y * fma(-0.5 * r2, y * y, 1.5);
+  return r2 * y;
 }
 
+// Kernel lattice of Eq. 3.9 for the circulant embedding (Section 3.1): for every offset
+// d in (-N, N)^3, h^3 e^{i k |d| h} / (4 pi |d| h) at index d mod M, the self-cell integral
+// at d = 0.  The lattice is even in every axis, so one thread evaluates |d| for
+// non-negative offsets and writes the value to each of its (up to 8) mirror positions;
+// indices no offset maps to are zeroed beforehand.  |d| in FP64 (one Newton step on the
+// FP32 reciprocal square root), phase reduced modulo 2 pi in FP64, amplitude in FP32.
 __global__ void lattice_kernel(float2* out, int nx, int ny, int nz, int mx, int my, int mz, double h,
                                double kr, double ki) {
-  const long long total = (long long)mx * my * mz;
+  const long long total = (long long)nx * ny * nz;
   const double h3_4pi = h * h * h / (4.0 * kPi);
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
-    const int iz = (int)(idx % mz);
-    const long long r1 = idx / mz;
-    const int iy = (int)(r1 % my);
-    const int ix = (int)(r1 / my);
-    const int dx = lattice_offset(ix, nx, mx);
-    const int dy = lattice_offset(iy, ny, my);
-    const int dz = lattice_offset(iz, nz, mz);
-    float2 v = make_float2(0.f, 0.f);
-    if (dx != INT_MIN && dy != INT_MIN && dz != INT_MIN) {
-      if (dx == 0 && dy == 0 && dz == 0) {
-        const double a = 0.62035049089940001666800681204778 * h;  // (3 / (4 pi))^(1/3) h
-        const cd s = self_cell_fp64(kr, ki, a);
-        v = make_float2((float)s.re, (float)s.im);
-      } else {
-        const double d2 = (double)((long long)dx * dx + (long long)dy * dy + (long long)dz * dz);
-        const double d = sqrt(d2);
-        const double r = d * h;
-        const double amp = h3_4pi * exp(-ki * r) / r;
-        const float2 ph = unit_phasor(kr * r);
-        v = make_float2((float)amp * ph.x, (float)amp * ph.y);
+    const int dz = (int)(idx % nz);
+    const long long r1 = idx / nz;
+    const int dy = (int)(r1 % ny);
+    const int dx = (int)(r1 / ny);
+    float2 v;
+    if (dx == 0 && dy == 0 && dz == 0) {
+      const double a = 0.62035049089940001666800681204778 * h;  // (3 / (4 pi))^(1/3) h
+      const cd s = self_cell_fp64(kr, ki, a);
+      v = make_float2((float)s.re, (float)s.im);
+    } else {
+      const double d2 = (double)((long long)dx * dx + (long long)dy * dy + (long long)dz * dz);
+      const double r = fp64_norm(d2) * h;
+      const float amp = (float)(h3_4pi / r) * expf(-(float)(ki * r));
+      const float2 ph = unit_phasor(kr * r);
+      v = make_float2(amp * ph.x, amp * ph.y);
+    }
+    const int xs[2] = {dx, dx > 0 ? mx - dx : -1};
+    const int ys[2] = {dy, dy > 0 ? my - dy : -1};
+    const int zs[2] = {dz, dz > 0 ? mz - dz : -1};
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+      if (xs[a] < 0) continue;
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        if (ys[b] < 0) continue;
+        float2* row = out + ((long long)xs[a] * my + ys[b]) * mz;
+        row[zs[0]] = v;
+        if (zs[1] >= 0) row[zs[1]] = v;
       }
     }
-    out[idx] = v;
   }
 }
 
@@ -221,12 +236,14 @@ __global__ void __launch_bounds__(128) restrict_kernel(const float2* __restrict_
   dst[idx] = acc;
 }
 
-// Shared-memory tiled form: one CTA computes a 1 x 8 x 64 block of targets (two per
-// thread) from the source sub-block they touch (ORD + 1 x planes, at most kRsY x kRsZ
-// source voxels), staged once with coalesced loads.  Used when the target spacing is
-// at most about the source spacing on y and z (nested grids of higher harmonics are
-// finer), so the sub-block always fits.
-constexpr int kRtY = 8, kRtZ = 64, kRsY = 12, kRsZ = 80;
+// Shared-memory tiled form: one CTA computes a 1 x 16 x 64 block of targets (four rows
+// per thread) from the source sub-block they touch (ORD + 1 x planes, at most kRsY x kRsZ
+// source voxels), staged once with coalesced loads.  The block's x stencil and the
+// source ranges are computed once per CTA.  Used when the target spacing is at most
+// about the source spacing on y and z (nested grids of higher harmonics are finer), so
+// the sub-block always fits.  (A persistent variant that prefetched the next tile with
+// cp.async measured slower: fewer resident warps and more barriers per tile.)
+constexpr int kRtY = 16, kRtZ = 64, kRsY = 20, kRsZ = 80, kRowsPerThread = kRtY / 4;
 
 template <int ORD>
 __global__ void __launch_bounds__(256) restrict_tiled_kernel(const float2* __restrict__ src, int snx, int sny,
@@ -234,17 +251,39 @@ __global__ void __launch_bounds__(256) restrict_tiled_kernel(const float2* __res
                                                              int dnz, AxisFix mx, AxisFix my, AxisFix mz,
                                                              int zero_outside) {
   __shared__ float2 tile[ORD + 1][kRsY][kRsZ];
+  __shared__ int sh_i[6];     // x0, cx, ys, ye, zs, ze
+  __shared__ float sh_wx[3];
+  __shared__ int sh_inx;
   const int ix = blockIdx.z, iy0 = blockIdx.y * kRtY, iz0 = blockIdx.x * kRtZ;
-  int x0, cx, ys, ye, zs, ze, c_;
-  float wx[3], wt[3];
-  const bool inx = stencil<ORD>(mx, ix, x0, wx, cx);
-  stencil<ORD>(my, iy0, ys, wt, c_);
-  stencil<ORD>(my, min(iy0 + kRtY - 1, dny - 1), ye, wt, c_);
-  ye = min(ye + c_ - 1, sny - 1);
-  stencil<ORD>(mz, iz0, zs, wt, c_);
-  stencil<ORD>(mz, min(iz0 + kRtZ - 1, dnz - 1), ze, wt, c_);
-  ze = min(ze + c_ - 1, snz - 1);
-  const int ny_r = ye - ys + 1, nz_r = ze - zs + 1;  // <= kRsY, kRsZ by the host's spacing check
+  (void)snx;
+  (void)dnx;
+  if (threadIdx.x < 5) {
+    int i0, c;
+    float w[3];
+    if (threadIdx.x == 0) {
+      sh_inx = stencil<ORD>(mx, ix, i0, w, c) ? 1 : 0;
+      sh_i[0] = i0;
+      sh_i[1] = c;
+      sh_wx[0] = w[0];
+      sh_wx[1] = w[1];
+      sh_wx[2] = w[2];
+    } else if (threadIdx.x == 1) {
+      stencil<ORD>(my, iy0, i0, w, c);
+      sh_i[2] = i0;
+    } else if (threadIdx.x == 2) {
+      stencil<ORD>(my, min(iy0 + kRtY - 1, dny - 1), i0, w, c);
+      sh_i[3] = min(i0 + c - 1, sny - 1);
+    } else if (threadIdx.x == 3) {
+      stencil<ORD>(mz, iz0, i0, w, c);
+      sh_i[4] = i0;
+    } else {
+      stencil<ORD>(mz, min(iz0 + kRtZ - 1, dnz - 1), i0, w, c);
+      sh_i[5] = min(i0 + c - 1, snz - 1);
+    }
+  }
+  __syncthreads();
+  const int x0 = sh_i[0], cx = sh_i[1], ys = sh_i[2], zs = sh_i[4];
+  const int ny_r = sh_i[3] - ys + 1, nz_r = sh_i[5] - zs + 1;  // <= kRsY, kRsZ by the host's spacing check
   const long long sy = snz, sx = (long long)sny * snz;
   // one warp per source row, lanes along z (coalesced, no index division)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -255,21 +294,23 @@ __global__ void __launch_bounds__(256) restrict_tiled_kernel(const float2* __res
     for (int zz = lane; zz < nz_r; zz += 32) tile[xi][yy][zz] = __ldg(&row[zz]);
   }
   __syncthreads();
-  const int iz = iz0 + threadIdx.x % kRtZ;
+  const int iz = iz0 + (threadIdx.x & (kRtZ - 1));
   if (iz >= dnz) return;
   int z0, cz;
   float wz[3];
   const bool inz = stencil<ORD>(mz, iz, z0, wz, cz);
   z0 -= zs;
+  const float wx[3] = {sh_wx[0], sh_wx[1], sh_wx[2]};
+  const bool inxz = sh_inx && inz;
 #pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    const int iy = iy0 + 2 * (threadIdx.x / kRtZ) + k;
+  for (int k = 0; k < kRowsPerThread; ++k) {
+    const int iy = iy0 + (threadIdx.x / kRtZ) * kRowsPerThread + k;
     if (iy >= dny) break;
     int y0, cy;
     float wy[3];
     const bool iny = stencil<ORD>(my, iy, y0, wy, cy);
     const long long idx = ((long long)ix * dny + iy) * dnz + iz;
-    if (!(inx && iny && inz) && zero_outside) {
+    if (!(inxz && iny) && zero_outside) {
       dst[idx] = make_float2(0.f, 0.f);
       continue;
     }
@@ -374,13 +415,6 @@ __global__ void q0_init_kernel(unsigned long long* max_bits, int* box) {
 constexpr int kIncBlock = 256;
 constexpr int kIncTx = 4, kIncTy = 8, kIncTz = 8;  // voxel tile of one CTA (kIncBlock voxels)
 
-// Distance in FP64 without a full-precision square root: one Newton step on the
-// single-precision reciprocal square root brings it to about 1e-14 relative.
-__device__ __forceinline__ double fp64_norm(double r2) {
-  double y = (double)rsqrtf((float)r2);
-  y = y * fma(-0.5 * r2, y * y, 1.5);
-  return r2 * y;
-}
 
 // Incident field of Eq. 3.10 on a voxel grid, one CTA per 4 x 8 x 8 voxel tile.
 // For each bowl point p and the tile centre c, the FP64 work is done once per CTA:
@@ -490,7 +524,10 @@ int grid_for(long long total, int threads) {
 
 cudaError_t launch_kernel_lattice(float2* out, const int n[3], const int m[3], double h, double kr,
                                   double ki, cudaStream_t s) {
-  const long long total = (long long)m[0] * m[1] * m[2];
+  const long long cube = (long long)m[0] * m[1] * m[2];
+  cudaError_t e = cudaMemsetAsync(out, 0, (size_t)cube * sizeof(float2), s);
+  if (e != cudaSuccess) return e;
+  const long long total = (long long)n[0] * n[1] * n[2];
   lattice_kernel<<<grid_for(total, 256), 256, 0, s>>>(out, n[0], n[1], n[2], m[0], m[1], m[2], h, kr, ki);
   return cudaGetLastError();
 }
@@ -520,8 +557,8 @@ cudaError_t launch_restrict(const float2* src, const int ns[3], float2* dst, con
     m[i].B = llround(b[i] * (double)(1LL << kFixBits));
     m[i].n = ns[i];
   }
-  // tiled form when the source footprint of a 8 x 64 (y, z) target block fits the
-  // staging tile: (8 - 1) b_y + order + 2 <= kRsY and (64 - 1) b_z + order + 2 <= kRsZ
+  // tiled form when the source footprint of a 16 x 64 (y, z) target block fits the
+  // staging tile: (16 - 1) b_y + order + 2 <= kRsY and (64 - 1) b_z + order + 2 <= kRsZ
   // source voxels (b = target spacing / source spacing), with a margin for rounding
   const double extra = order + 2.0;
   if (b[1] * (kRtY - 1) + extra <= kRsY && b[2] * (kRtZ - 1) + extra <= kRsZ) {
