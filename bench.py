@@ -42,6 +42,7 @@ def parse():
                     choices=["small", "nested3", "nested5", "batch64", "vie", "fullcascade", "q0"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT comparison timing")
     return ap.parse_args()
 
 
@@ -366,6 +367,10 @@ def run_ours(args, world, rank, local):
     if not args.no_e2e:
         e2e = measure_e2e(gw, args, world, voxels, flush)
 
+    cufft = None
+    if rank == 0 and world == 1 and not args.no_cufft:
+        cufft = cufft_comparison(gw, flush)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w)
@@ -382,11 +387,53 @@ def run_ours(args, world, rank, local):
                    "l2": "flushed between steps (256 MiB write outside the timed events)",
                    "khat_build_ms": round(gw.khat_build_ms, 2)},
         "roofline": roofline, "per_harmonic": per_h, "sweeps": sweeps,
-        "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
+        "e2e": e2e, "cpu_baseline": cpu, "cufft_comparison": cufft, "clocks": clk,
         "gpu_launches": gw.launches_per_step() * args.steps, "wall_s_timed": round(t_wall, 4),
     }
     if rank == 0:
         print(json.dumps(line))
+
+
+def cufft_comparison(gw, flush):
+    """cuFFT (through torch.fft), timed as a comparison only: the same zero-padded
+    circulant convolution per harmonic (pad f into an M^3 cube, 3-D FFT, multiply by a
+    full M^3 spectrum, inverse 3-D FFT, crop), unpruned, outside the metric.  The
+    spectrum's values do not change the work; a random cube stands in for it."""
+    import torch
+    out = {}
+    for n, p in gw.plans.items():
+        inf = p.info()
+        N, M = tuple(inf.n), tuple(inf.m)
+        f = torch.randn(N, dtype=torch.complex64, device=gw.dev)
+        K = torch.randn(M, dtype=torch.complex64, device=gw.dev)
+        cube = torch.zeros(M, dtype=torch.complex64, device=gw.dev)
+        u = torch.empty(N, dtype=torch.complex64, device=gw.dev)
+
+        def conv():
+            cube.zero_()
+            cube[:N[0], :N[1], :N[2]] = f
+            F = torch.fft.fftn(cube)
+            F *= K
+            u.copy_(torch.fft.ifftn(F)[:N[0], :N[1], :N[2]])
+
+        for _ in range(3):
+            conv()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(5):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            conv()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        ms = sorted(ts)[len(ts) // 2]
+        vox = N[0] * N[1] * N[2]
+        out[str(n)] = {"n": list(N), "m": list(M), "ms": round(ms, 4), "voxels_per_s": vox / (ms * 1e-3)}
+        del f, K, cube, u
+    torch.cuda.empty_cache()
+    return out
 
 
 def measure_e2e(gw, args, world, voxels, flush):

@@ -25,7 +25,11 @@ constexpr int kThreads2 = 256;
 __host__ __device__ constexpr int col2_pitch(int L) { return L + 1; }
 // Resident CTAs per SM the column kernels are compiled for: three while three tiles fit
 // in shared memory (the register cap then is 85 per thread), else one.
-__host__ __device__ constexpr int col2_min_blocks(int L) { return L <= 512 ? 3 : 1; }
+__host__ __device__ constexpr int col2_min_blocks(int L, int dir) {
+  // forward sweeps up to L = 384 fit four CTAs (64 registers) without spilling much and
+  // are latency-bound, so the fourth CTA pays; their inverse variants spill there
+  return (L <= 384 && dir == kForward) ? 4 : (L <= 512 ? 3 : 1);
+}
 __host__ __device__ constexpr int line2_bpitch(int B) { return B + 1; }
 __host__ __device__ constexpr int line2_pitch(int A, int B) { return A * (B + 1) + 1; }
 
@@ -141,7 +145,7 @@ __device__ __forceinline__ void col2_tile(const ColSweep& p, int tile, float2* S
 }
 
 template <int A, int B, int DIR, bool SRC>
-__global__ void __launch_bounds__(kThreads2, col2_min_blocks(A * B)) col2_kernel(const ColSweep p) {
+__global__ void __launch_bounds__(kThreads2, col2_min_blocks(A * B, DIR)) col2_kernel(const ColSweep p) {
   extern __shared__ float2 S[];
   col2_tile<A, B, DIR, SRC>(p, blockIdx.x, S);
 }
@@ -169,7 +173,7 @@ __device__ __forceinline__ void copy_params(T* dst, const T* src) {
 }
 
 template <int A, int B, int DIR, bool SRC>
-__global__ void __launch_bounds__(kThreads2, col2_min_blocks(A * B))
+__global__ void __launch_bounds__(kThreads2, col2_min_blocks(A * B, DIR))
     col2_batch_kernel(const __grid_constant__ BatchParams<ColSweep> bp) {
   extern __shared__ float2 S[];
   const int owner = batch_owner(bp, blockIdx.x);

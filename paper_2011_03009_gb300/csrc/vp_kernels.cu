@@ -238,12 +238,19 @@ __global__ void __launch_bounds__(128) restrict_kernel(const float2* __restrict_
 
 // Shared-memory tiled form: one CTA computes a 1 x 16 x 64 block of targets (four rows
 // per thread) from the source sub-block they touch (ORD + 1 x planes, at most kRsY x kRsZ
-// source voxels), staged once with coalesced loads.  The block's x stencil and the
-// source ranges are computed once per CTA.  Used when the target spacing is at most
-// about the source spacing on y and z (nested grids of higher harmonics are finer), so
-// the sub-block always fits.  (A persistent variant that prefetched the next tile with
-// cp.async measured slower: fewer resident warps and more barriers per tile.)
+// source voxels), staged once with coalesced loads.  Every stencil of the block (its x
+// stencil, the 16 y and the 64 z stencils) is computed once, in parallel, into shared
+// memory, so a target costs only its tile reads and multiply-adds.  Used when the target
+// spacing is at most about the source spacing on y and z (nested grids of higher
+// harmonics are finer), so the sub-block always fits.  (A persistent variant that
+// prefetched the next tile with cp.async measured slower: fewer resident warps and more
+// barriers per tile.)
 constexpr int kRtY = 16, kRtZ = 64, kRsY = 20, kRsZ = 80, kRowsPerThread = kRtY / 4;
+
+struct RStencil {
+  int i0, cnt, in;
+  float w[3];
+};
 
 template <int ORD>
 __global__ void __launch_bounds__(256) restrict_tiled_kernel(const float2* __restrict__ src, int snx, int sny,
@@ -251,70 +258,60 @@ __global__ void __launch_bounds__(256) restrict_tiled_kernel(const float2* __res
                                                              int dnz, AxisFix mx, AxisFix my, AxisFix mz,
                                                              int zero_outside) {
   __shared__ float2 tile[ORD + 1][kRsY][kRsZ];
-  __shared__ int sh_i[6];     // x0, cx, ys, ye, zs, ze
-  __shared__ float sh_wx[3];
-  __shared__ int sh_inx;
+  __shared__ RStencil sx_[1], sy_[kRtY], sz_[kRtZ];
   const int ix = blockIdx.z, iy0 = blockIdx.y * kRtY, iz0 = blockIdx.x * kRtZ;
   (void)snx;
   (void)dnx;
-  if (threadIdx.x < 5) {
-    int i0, c;
-    float w[3];
-    if (threadIdx.x == 0) {
-      sh_inx = stencil<ORD>(mx, ix, i0, w, c) ? 1 : 0;
-      sh_i[0] = i0;
-      sh_i[1] = c;
-      sh_wx[0] = w[0];
-      sh_wx[1] = w[1];
-      sh_wx[2] = w[2];
-    } else if (threadIdx.x == 1) {
-      stencil<ORD>(my, iy0, i0, w, c);
-      sh_i[2] = i0;
-    } else if (threadIdx.x == 2) {
-      stencil<ORD>(my, min(iy0 + kRtY - 1, dny - 1), i0, w, c);
-      sh_i[3] = min(i0 + c - 1, sny - 1);
-    } else if (threadIdx.x == 3) {
-      stencil<ORD>(mz, iz0, i0, w, c);
-      sh_i[4] = i0;
-    } else {
-      stencil<ORD>(mz, min(iz0 + kRtZ - 1, dnz - 1), i0, w, c);
-      sh_i[5] = min(i0 + c - 1, snz - 1);
+  {
+    // threads 0..63: z stencils; 64..79: y stencils; 80: x stencil (targets past the
+    // grid's end reuse the last target's stencil so that the source ranges stay valid)
+    const int t = threadIdx.x;
+    RStencil r;
+    if (t < kRtZ) {
+      r.in = stencil<ORD>(mz, min(iz0 + t, dnz - 1), r.i0, r.w, r.cnt);
+      sz_[t] = r;
+    } else if (t < kRtZ + kRtY) {
+      r.in = stencil<ORD>(my, min(iy0 + t - kRtZ, dny - 1), r.i0, r.w, r.cnt);
+      sy_[t - kRtZ] = r;
+    } else if (t == kRtZ + kRtY) {
+      r.in = stencil<ORD>(mx, ix, r.i0, r.w, r.cnt);
+      sx_[0] = r;
     }
   }
   __syncthreads();
-  const int x0 = sh_i[0], cx = sh_i[1], ys = sh_i[2], zs = sh_i[4];
-  const int ny_r = sh_i[3] - ys + 1, nz_r = sh_i[5] - zs + 1;  // <= kRsY, kRsZ by the host's spacing check
-  const long long sy = snz, sx = (long long)sny * snz;
+  const int x0 = sx_[0].i0, cx = sx_[0].cnt;
+  const int ys = sy_[0].i0, zs = sz_[0].i0;
+  const int ny_r = min(sy_[kRtY - 1].i0 + sy_[kRtY - 1].cnt - 1, sny - 1) - ys + 1;
+  const int nz_r = min(sz_[kRtZ - 1].i0 + sz_[kRtZ - 1].cnt - 1, snz - 1) - zs + 1;  // <= kRsY, kRsZ (host check)
+  const long long sy = snz, sxs = (long long)sny * snz;
   // one warp per source row, lanes along z (coalesced, no index division)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int r = warp; r < cx * ny_r; r += (int)(blockDim.x >> 5)) {
     const int xi = r >= 2 * ny_r ? 2 : (r >= ny_r ? 1 : 0);
     const int yy = r - xi * ny_r;
-    const float2* row = src + (x0 + xi) * sx + (ys + yy) * sy + zs;
+    const float2* row = src + (x0 + xi) * sxs + (ys + yy) * sy + zs;
     for (int zz = lane; zz < nz_r; zz += 32) tile[xi][yy][zz] = __ldg(&row[zz]);
   }
   __syncthreads();
-  const int iz = iz0 + (threadIdx.x & (kRtZ - 1));
+  const int lz = threadIdx.x & (kRtZ - 1);
+  const int iz = iz0 + lz;
   if (iz >= dnz) return;
-  int z0, cz;
-  float wz[3];
-  const bool inz = stencil<ORD>(mz, iz, z0, wz, cz);
-  z0 -= zs;
-  const float wx[3] = {sh_wx[0], sh_wx[1], sh_wx[2]};
-  const bool inxz = sh_inx && inz;
+  const RStencil zst = sz_[lz];
+  const int z0 = zst.i0 - zs;
+  const float wx0 = sx_[0].w[0], wx1 = sx_[0].w[1], wx2 = sx_[0].w[2];
+  const bool inxz = sx_[0].in && zst.in;
 #pragma unroll
   for (int k = 0; k < kRowsPerThread; ++k) {
-    const int iy = iy0 + (threadIdx.x / kRtZ) * kRowsPerThread + k;
+    const int ly = (threadIdx.x / kRtZ) * kRowsPerThread + k;
+    const int iy = iy0 + ly;
     if (iy >= dny) break;
-    int y0, cy;
-    float wy[3];
-    const bool iny = stencil<ORD>(my, iy, y0, wy, cy);
+    const RStencil yst = sy_[ly];
     const long long idx = ((long long)ix * dny + iy) * dnz + iz;
-    if (!(inxz && iny) && zero_outside) {
+    if (!(inxz && yst.in) && zero_outside) {
       dst[idx] = make_float2(0.f, 0.f);
       continue;
     }
-    y0 -= ys;
+    const int y0 = yst.i0 - ys;
     float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
     for (int a = 0; a <= ORD; ++a) {
@@ -322,20 +319,21 @@ __global__ void __launch_bounds__(256) restrict_tiled_kernel(const float2* __res
       float2 py = make_float2(0.f, 0.f);
 #pragma unroll
       for (int b = 0; b <= ORD; ++b) {
-        if (b >= cy) break;
+        if (b >= yst.cnt) break;
         float2 pz = make_float2(0.f, 0.f);
 #pragma unroll
         for (int c = 0; c <= ORD; ++c) {
-          if (c >= cz) break;
+          if (c >= zst.cnt) break;
           const float2 v = tile[a][y0 + b][z0 + c];
-          pz.x = fmaf(wz[c], v.x, pz.x);
-          pz.y = fmaf(wz[c], v.y, pz.y);
+          pz.x = fmaf(zst.w[c], v.x, pz.x);
+          pz.y = fmaf(zst.w[c], v.y, pz.y);
         }
-        py.x = fmaf(wy[b], pz.x, py.x);
-        py.y = fmaf(wy[b], pz.y, py.y);
+        py.x = fmaf(yst.w[b], pz.x, py.x);
+        py.y = fmaf(yst.w[b], pz.y, py.y);
       }
-      acc.x = fmaf(wx[a], py.x, acc.x);
-      acc.y = fmaf(wx[a], py.y, acc.y);
+      const float wxa = a == 0 ? wx0 : (a == 1 ? wx1 : wx2);
+      acc.x = fmaf(wxa, py.x, acc.x);
+      acc.y = fmaf(wxa, py.y, acc.y);
     }
     dst[idx] = acc;
   }
