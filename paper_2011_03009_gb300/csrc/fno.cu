@@ -53,7 +53,11 @@ struct Gemm {
   int K2, rows_per_line;
 };
 
+// The K slices of the main product and of the optional second contraction form one
+// pipeline of stages: the next stage's tiles are loaded while the current one computes.
+// (BK = 64, one stage for K <= 64, measured slower: more registers, fewer resident CTAs.)
 constexpr int BM = 64, BN = 64, BK = 32, KP = BK + 8;  // padded rows: conflict-free fragments
+constexpr int kChunks = BM * BK / 8 / 128;             // 16-byte chunks per thread per tile
 
 __device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_grad(float x) {
@@ -67,7 +71,7 @@ __device__ __forceinline__ float gelu_grad(float x) {
 // and 16-byte aligned:  A: 1 = k contiguous, 2 = m contiguous;  B: 1 = n contiguous,
 // 2 = k contiguous;  0 = element by element.  Each thread moves two chunks per tile.
 struct TileRegs {
-  uint4 a[2], b[2];
+  uint4 a[kChunks], b[kChunks];
 };
 
 __device__ __forceinline__ long long a_row(const Gemm& g, int m) {
@@ -79,11 +83,12 @@ __device__ __forceinline__ long long a_row(const Gemm& g, int m) {
 __device__ __forceinline__ void load_tiles(const Gemm& g, const bf16* A, const bf16* B, int m0, int n0, int k0,
                                            int k_end, int tid, TileRegs& r) {
   const uint4 z4 = make_uint4(0u, 0u, 0u, 0u);
+  constexpr int KC = BK / 8;  // chunks along k in a row of the tile
 #pragma unroll
-  for (int c = 0; c < 2; ++c) {
+  for (int c = 0; c < kChunks; ++c) {
     const int e = tid + c * 128;
     if (g.a_mode == 1) {
-      const int m = e >> 2, kc = (e & 3) * 8;
+      const int m = e / KC, kc = (e % KC) * 8;
       const int gm = m0 + m, gk = k0 + kc;
       r.a[c] = (gm < g.M && gk < k_end) ? *reinterpret_cast<const uint4*>(A + a_row(g, gm) + gk) : z4;
     } else if (g.a_mode == 2) {
@@ -96,7 +101,7 @@ __device__ __forceinline__ void load_tiles(const Gemm& g, const bf16* A, const b
       const int gn = n0 + nc, gk = k0 + k;
       r.b[c] = (gn < g.N && gk < k_end) ? *reinterpret_cast<const uint4*>(B + (long long)gk * g.b_rs + gn) : z4;
     } else if (g.b_mode == 2) {
-      const int n = e >> 2, kc = (e & 3) * 8;
+      const int n = e / KC, kc = (e % KC) * 8;
       const int gn = n0 + n, gk = k0 + kc;
       r.b[c] = (gn < g.N && gk < k_end) ? *reinterpret_cast<const uint4*>(B + gk + (long long)gn * g.b_cs) : z4;
     }
@@ -107,11 +112,12 @@ __device__ __forceinline__ void store_tiles(const Gemm& g, const bf16* A, const 
                                             int k_end, int tid, const TileRegs& r, bf16 (*As)[KP],
                                             bf16 (*Bs)[KP]) {
   const bf16 zero = __float2bfloat16(0.f);
+  constexpr int KC = BK / 8;
 #pragma unroll
-  for (int c = 0; c < 2; ++c) {
+  for (int c = 0; c < kChunks; ++c) {
     const int e = tid + c * 128;
     if (g.a_mode == 1) {
-      *reinterpret_cast<uint4*>(&As[e >> 2][(e & 3) * 8]) = r.a[c];
+      *reinterpret_cast<uint4*>(&As[e / KC][(e % KC) * 8]) = r.a[c];
     } else if (g.a_mode == 2) {
       const bf16* v = reinterpret_cast<const bf16*>(&r.a[c]);
       const int mc = (e & 7) * 8, k = e >> 3;
@@ -124,7 +130,7 @@ __device__ __forceinline__ void store_tiles(const Gemm& g, const bf16* A, const 
 #pragma unroll
       for (int i = 0; i < 8; ++i) Bs[nc + i][k] = v[i];
     } else if (g.b_mode == 2) {
-      *reinterpret_cast<uint4*>(&Bs[e >> 2][(e & 3) * 8]) = r.b[c];
+      *reinterpret_cast<uint4*>(&Bs[e / KC][(e % KC) * 8]) = r.b[c];
     }
   }
   if (g.a_mode == 0) {
@@ -200,32 +206,38 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(const Gemm g) {
     for (int j = 0; j < 4; ++j)
 #pragma unroll
       for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
-  TileRegs regs;
-  if (k_begin < k_end) load_tiles(g, A, B, m0, n0, k_begin, k_end, tid, regs);
-  for (int k0 = k_begin; k0 < k_end; k0 += BK) {
-    store_tiles(g, A, B, m0, n0, k0, k_end, tid, regs, As, Bs);
-    __syncthreads();
-    if (k0 + BK < k_end) load_tiles(g, A, B, m0, n0, k0 + BK, k_end, tid, regs);
-    mma_slice(As, Bs, wm, wn, gq, tq, acc);
-    __syncthreads();
-  }
+  // stages: the K slices of the main product, then those of the second contraction
+  Gemm g2 = g;
+  const bf16* A2 = nullptr;
+  const bf16* B2 = nullptr;
+  int n1 = k_begin < k_end ? (k_end - k_begin + BK - 1) / BK : 0, n2 = 0;
   if (g.A2 && ks == 0) {
-    Gemm g2 = g;
     g2.M = min(BM, g.M - m0);
     g2.K = g.K2;
-    g2.a_rs = g.a2_rs; g2.a_cs = 1; g2.a_mode = 1;
+    g2.a_rs = g.a2_rs; g2.a_cs = 1; g2.a_mode = 1; g2.a_group = 0;
     g2.b_rs = g.b2_rs; g2.b_cs = 1; g2.b_mode = 1;
     const int line = m0 / g.rows_per_line, z0 = m0 - line * g.rows_per_line;
-    const bf16* A2 = g.A2 + (long long)z0 * g.a2_rs;
-    const bf16* B2 = g.B2 + (long long)line * g.b2_line;
-    load_tiles(g2, A2, B2, 0, n0, 0, g2.K, tid, regs);
-    for (int k0 = 0; k0 < g2.K; k0 += BK) {
-      store_tiles(g2, A2, B2, 0, n0, k0, g2.K, tid, regs, As, Bs);
-      __syncthreads();
-      if (k0 + BK < g2.K) load_tiles(g2, A2, B2, 0, n0, k0 + BK, g2.K, tid, regs);
-      mma_slice(As, Bs, wm, wn, gq, tq, acc);
-      __syncthreads();
-    }
+    A2 = g.A2 + (long long)z0 * g.a2_rs;
+    B2 = g.B2 + (long long)line * g.b2_line;
+    n2 = (g2.K + BK - 1) / BK;
+  }
+  auto load_stage = [&](int st, TileRegs& r) {
+    if (st < n1) load_tiles(g, A, B, m0, n0, k_begin + st * BK, k_end, tid, r);
+    else load_tiles(g2, A2, B2, 0, n0, (st - n1) * BK, g2.K, tid, r);
+  };
+  auto store_stage = [&](int st, const TileRegs& r) {
+    if (st < n1) store_tiles(g, A, B, m0, n0, k_begin + st * BK, k_end, tid, r, As, Bs);
+    else store_tiles(g2, A2, B2, 0, n0, (st - n1) * BK, g2.K, tid, r, As, Bs);
+  };
+  TileRegs regs;
+  const int nst = n1 + n2;
+  if (nst > 0) load_stage(0, regs);
+  for (int st = 0; st < nst; ++st) {
+    store_stage(st, regs);
+    __syncthreads();
+    if (st + 1 < nst) load_stage(st + 1, regs);
+    mma_slice(As, Bs, wm, wn, gq, tq, acc);
+    __syncthreads();
   }
   // epilogue: column pairs (n, n + 1) go out as one 8-byte / 4-byte store when the
   // output rows are contiguous and even-aligned
@@ -333,9 +345,30 @@ __device__ __forceinline__ void features(const float* __restrict__ x, long long 
   }
 }
 
-// h0[v][c] = sum_f feat[v][f] P[f][c] + bP[c]
+// h0[v][c] = sum_f feat[v][f] P[f][c] + bP[c]: one thread per (voxel, 8 channels), the
+// features once per thread, one 16-byte store (W % 8 == 0; else one channel per thread)
 __global__ void lift_kernel(const float* __restrict__ x, const float* __restrict__ P, const float* __restrict__ bP,
                             bf16* __restrict__ h, long long V, int W) {
+  if (W % 8 == 0) {
+    const int groups = W / 8;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < V * groups;
+         i += (long long)gridDim.x * blockDim.x) {
+      const long long v = i / groups;
+      const int c0 = (int)(i - v * groups) * 8;
+      float f[VP_FNO_IN];
+      features(x, v, f);
+      __align__(16) bf16 out[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        float acc = bP[c0 + j];
+#pragma unroll
+        for (int k = 0; k < VP_FNO_IN; ++k) acc = fmaf(f[k], P[k * W + c0 + j], acc);
+        out[j] = __float2bfloat16(acc);
+      }
+      *reinterpret_cast<uint4*>(h + v * W + c0) = *reinterpret_cast<const uint4*>(out);
+    }
+    return;
+  }
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < V * W; i += (long long)gridDim.x * blockDim.x) {
     const long long v = i / W;
     const int c = (int)(i - v * W);

@@ -306,9 +306,11 @@ __global__ void __launch_bounds__(kThreads2) line2_batch_kernel(const __grid_con
 // shared memory.
 // Shared memory: transpose buffer (16 x line2_pitch), staging buffer (16 x ni),
 // spectrum lines (4 x Oz), twiddles (L).
+// NL = 8 (long lines): a CTA takes half a tile of the host's list (2 mirror groups of
+// 4 lines and their 2 octant lines), so the buffers fit in shared memory at L >= 1024.
 __host__ __device__ constexpr int conv_stage_pitch(int n_in) { return n_in | 1; }  // odd: lanes = lines
-__host__ __device__ constexpr size_t conv_pipe_smem(int A, int B, int n_in, int Oz) {
-  return ((size_t)kLines2 * line2_pitch(A, B) + (size_t)kLines2 * conv_stage_pitch(n_in) + (size_t)4 * Oz +
+__host__ __device__ constexpr size_t conv_pipe_smem(int A, int B, int n_in, int Oz, int NL = kLines2) {
+  return ((size_t)NL * line2_pitch(A, B) + (size_t)NL * conv_stage_pitch(n_in) + (size_t)(NL / 4) * Oz +
           (size_t)A * B) *
          sizeof(float2);
 }
@@ -318,7 +320,7 @@ __host__ __device__ constexpr size_t conv_pipe_smem(int A, int B, int n_in, int 
 // numbered consecutively (plan i owns [offsets[i], offsets[i + 1])), all with the same
 // line length L and spectrum octant length; ni is the staging pitch for the longest
 // input line.
-template <int A, int B, bool BATCH>
+template <int A, int B, bool BATCH, int NL = kLines2>
 __global__ void __launch_bounds__(kThreads2)
     line2_conv_pipe_kernel(const __grid_constant__ LineSweep p, const __grid_constant__ BatchParams<LineSweep> bp,
                            long long ntiles, int NI) {
@@ -327,11 +329,13 @@ __global__ void __launch_bounds__(kThreads2)
   constexpr int LP = line2_pitch(A, B);
   extern __shared__ float2 S[];
   const int Oz = p.Oz;  // shared by every plan of a batch group
-  float2* I = S + kLines2 * LP;
-  float2* K = I + kLines2 * NI;  // [4][Oz]
-  float2* T = K + 4 * Oz;        // twiddles
-  __shared__ long long line_of[2][kLines2];
-  __shared__ int oct_of[2][4];
+  constexpr int NG = NL / 4;       // mirror groups per CTA tile
+  constexpr int LSH = NL == 16 ? 4 : 3;
+  float2* I = S + NL * LP;
+  float2* K = I + NL * NI;  // [NG][Oz]
+  float2* T = K + NG * Oz;  // twiddles
+  __shared__ long long line_of[2][NL];
+  __shared__ int oct_of[2][NG];
   __shared__ const LineSweep* plan_of[2];
   const float2 zero = make_float2(0.f, 0.f);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -347,6 +351,13 @@ __global__ void __launch_bounds__(kThreads2)
       return &p;
     }
   };
+  // line slots and octant ids of local tile lt in the host's 20-int tile records
+  auto line_base = [&](long long lt) -> long long {
+    return NL == 16 ? 20LL * lt : 20LL * (lt >> 1) + 8 * (lt & 1);
+  };
+  auto oct_base = [&](long long lt) -> long long {
+    return NL == 16 ? 20LL * lt + 16 : 20LL * (lt >> 1) + 16 + 2 * (lt & 1);
+  };
   auto fetch_lines = [&](long long t, int slot) {
     long long lt = 0;
     const LineSweep* q = resolve(t, lt);
@@ -354,22 +365,23 @@ __global__ void __launch_bounds__(kThreads2)
     const float2* data = q->data;
     const long long ld = q->ld;
     const int n_in = q->n_in;
-    for (int b = warp; b < kLines2; b += kThreads2 / 32) {
-      const long long l = tiles[20LL * lt + b];
+    const long long lb = line_base(lt), ob = oct_base(lt);
+    for (int b = warp; b < NL; b += kThreads2 / 32) {
+      const long long l = tiles[lb + b];
       const float2* src = data + (l < 0 ? 0 : l * ld);
       for (int n = lane; n < NI; n += 32) cp_async8(&I[b * NI + n], &src[n < n_in ? n : 0], l >= 0 && n < n_in);
     }
-    if (threadIdx.x < kLines2) line_of[slot][threadIdx.x] = tiles[20LL * lt + threadIdx.x];
-    if (threadIdx.x < 4) oct_of[slot][threadIdx.x] = tiles[20LL * lt + 16 + threadIdx.x];
+    if (threadIdx.x < NL) line_of[slot][threadIdx.x] = tiles[lb + threadIdx.x];
+    if (threadIdx.x < NG) oct_of[slot][threadIdx.x] = tiles[ob + threadIdx.x];
     if (threadIdx.x == 0) plan_of[slot] = q;
   };
   auto fetch_spectrum = [&](long long t) {
     long long lt = 0;
     const LineSweep* q = resolve(t, lt);
-    const int g = warp & 3;
-    const int oc = q->tiles[20LL * lt + 16 + g];
+    const int g = warp % NG;
+    const int oc = q->tiles[oct_base(lt) + g];
     const float2* kl = q->khat + (oc < 0 ? 0 : (long long)oc * Oz);
-    for (int i = (warp >> 2) * 32 + lane; i < Oz; i += (kThreads2 / 128) * 32)
+    for (int i = (warp / NG) * 32 + lane; i < Oz; i += (kThreads2 / 32 / NG) * 32)
       cp_async8(&K[g * Oz + i], &kl[i], oc >= 0);
   };
 
@@ -390,9 +402,9 @@ __global__ void __launch_bounds__(kThreads2)
     const long long ld = q->ld;
     // forward step 1 from the staging buffer; the 16 lanes of a half-warp hold the 16
     // lines (odd staging pitch), so every twiddle read is a broadcast
-    for (int tau = threadIdx.x; tau < kLines2 * B; tau += blockDim.x) {
-      const int line = tau & (kLines2 - 1);
-      const int b = tau >> 4;
+    for (int tau = threadIdx.x; tau < NL * B; tau += blockDim.x) {
+      const int line = tau & (NL - 1);
+      const int b = tau >> LSH;
       const float2* src = I + line * NI;
       float2 v[A];
 #pragma unroll
@@ -411,9 +423,9 @@ __global__ void __launch_bounds__(kThreads2)
     if (tn < ntiles) fetch_lines(tn, cur ^ 1);
     asm volatile("cp.async.commit_group;\n" ::: "memory");
     // forward step 2, spectrum multiply, inverse step 2 (lanes = lines again)
-    for (int tau = threadIdx.x; tau < kLines2 * A; tau += blockDim.x) {
-      const int line = tau & (kLines2 - 1);
-      const int k1 = tau >> 4;
+    for (int tau = threadIdx.x; tau < NL * A; tau += blockDim.x) {
+      const int line = tau & (NL - 1);
+      const int k1 = tau >> LSH;
       float2 z[B];
       float2* s = S + line * LP + k1 * BP;
 #pragma unroll
@@ -436,7 +448,7 @@ __global__ void __launch_bounds__(kThreads2)
     if (tn < ntiles) fetch_spectrum(tn);
     asm volatile("cp.async.commit_group;\n" ::: "memory");
     // inverse step 1 and store
-    for (int tau = threadIdx.x; tau < kLines2 * B; tau += blockDim.x) {
+    for (int tau = threadIdx.x; tau < NL * B; tau += blockDim.x) {
       const int line = tau / B;
       const int b = tau - line * B;
       float2 v[A];

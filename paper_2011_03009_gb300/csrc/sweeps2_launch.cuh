@@ -86,24 +86,46 @@ cudaError_t resident_slots(K kernel, size_t smem, volatile int* granted, int* gr
 template <int A, int B>
 cudaError_t line2_conv_pipe_launch(const LineSweep& p, cudaStream_t s, bool* used) {
   static volatile int granted[64] = {0};
+  static volatile int granted8[64] = {0};
   *used = false;
   const int ni = conv_stage_pitch(p.n_in);
-  const size_t smem = conv_pipe_smem(A, B, p.n_in, p.Oz);
-  if (smem > 200 * 1024) return cudaSuccess;  // too large to pipeline: caller falls back
-  if (p.nlines <= 0) {
-    *used = true;
-    return cudaSuccess;
-  }
-  auto k = line2_conv_pipe_kernel<A, B, false>;
-  int grid = 0;
-  cudaError_t e = resident_slots(k, smem, granted, &grid);
-  if (e != cudaSuccess) return e;
-  if (grid < 1) return cudaSuccess;
-  if (grid > p.nlines) grid = (int)p.nlines;
   static BatchParams<LineSweep> none{};  // unused by the single-plan form
-  k<<<(unsigned)grid, kThreads2, smem, s>>>(p, none, p.nlines, ni);
-  *used = true;
-  return cudaGetLastError();
+  const size_t smem = conv_pipe_smem(A, B, p.n_in, p.Oz);
+  if (smem <= 200 * 1024) {
+    if (p.nlines <= 0) {
+      *used = true;
+      return cudaSuccess;
+    }
+    auto k = line2_conv_pipe_kernel<A, B, false>;
+    int grid = 0;
+    cudaError_t e = resident_slots(k, smem, granted, &grid);
+    if (e != cudaSuccess) return e;
+    if (grid < 1) return cudaSuccess;
+    if (grid > p.nlines) grid = (int)p.nlines;
+    k<<<(unsigned)grid, kThreads2, smem, s>>>(p, none, p.nlines, ni);
+    *used = true;
+    return cudaGetLastError();
+  }
+  if constexpr (A * B >= 1024) {
+    // long lines: half tiles of 8 lines keep the pipeline within one CTA's shared memory
+    const size_t smem8 = conv_pipe_smem(A, B, p.n_in, p.Oz, 8);
+    if (smem8 > 200 * 1024) return cudaSuccess;  // too large to pipeline: caller falls back
+    if (p.nlines <= 0) {
+      *used = true;
+      return cudaSuccess;
+    }
+    auto k = line2_conv_pipe_kernel<A, B, false, 8>;
+    int grid = 0;
+    cudaError_t e = resident_slots(k, smem8, granted8, &grid);
+    if (e != cudaSuccess) return e;
+    if (grid < 1) return cudaSuccess;
+    const long long halves = 2LL * p.nlines;
+    if (grid > halves) grid = (int)halves;
+    k<<<(unsigned)grid, kThreads2, smem8, s>>>(p, none, halves, ni);
+    *used = true;
+    return cudaGetLastError();
+  }
+  return cudaSuccess;  // too large to pipeline: caller falls back
 }
 
 template <int A, int B>
