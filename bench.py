@@ -153,13 +153,13 @@ def sweep_bytes(n, m, harmonic, fused_source: bool):
 SWEEP_NAMES = ["x_forward_source", "y_forward", "z_conv", "y_inverse", "x_inverse"]
 
 
-SWEEP_SOURCES = ("fft_engine.cuh", "regfft.cuh", "sweeps2.cuh", "sweeps2_launch.cuh", "vp_internal.cuh",
-                 "vp_sweeps2_part0.cu", "vp_sweeps2_part1.cu", "vp_sweeps2_part2.cu")
+# the device code of the FFT sweep kernels (launch logic lives elsewhere)
+SWEEP_SOURCES = ("fft_engine.cuh", "regfft.cuh", "sweeps2.cuh", "vp_internal.cuh")
 
 
 def csrc_digest() -> str:
-    """Short digest of the sources the FFT sweep kernels are compiled from; a stored ncu
-    traffic figure is used only while it matches (a change there invalidates it)."""
+    """Short digest of the device code of the FFT sweep kernels; a stored ncu traffic
+    figure is used only while it matches (a change of the kernels invalidates it)."""
     import hashlib
     d = os.path.join(ROOT, "paper_2011_03009_gb300", "csrc")
     h = hashlib.sha256()

@@ -90,42 +90,42 @@ cudaError_t line2_conv_pipe_launch(const LineSweep& p, cudaStream_t s, bool* use
   *used = false;
   const int ni = conv_stage_pitch(p.n_in);
   static BatchParams<LineSweep> none{};  // unused by the single-plan form
-  const size_t smem = conv_pipe_smem(A, B, p.n_in, p.Oz);
-  if (smem <= 200 * 1024) {
-    if (p.nlines <= 0) {
-      *used = true;
-      return cudaSuccess;
-    }
-    auto k = line2_conv_pipe_kernel<A, B, false>;
-    int grid = 0;
-    cudaError_t e = resident_slots(k, smem, granted, &grid);
+  // tiles of 16 lines, or (long lines) half tiles of 8 lines when those fit more CTAs per
+  // SM: at L = 640-864 one 16-line CTA fills an SM's shared memory, two 8-line CTAs fit;
+  // from L = 1024 only the 8-line form fits at all
+  const size_t smem16 = conv_pipe_smem(A, B, p.n_in, p.Oz);
+  int grid16 = 0, grid8 = 0;
+  cudaError_t e;
+  if (smem16 <= 200 * 1024) {
+    e = resident_slots(line2_conv_pipe_kernel<A, B, false>, smem16, granted, &grid16);
     if (e != cudaSuccess) return e;
-    if (grid < 1) return cudaSuccess;
-    if (grid > p.nlines) grid = (int)p.nlines;
-    k<<<(unsigned)grid, kThreads2, smem, s>>>(p, none, p.nlines, ni);
-    *used = true;
-    return cudaGetLastError();
   }
-  if constexpr (A * B >= 1024) {
-    // long lines: half tiles of 8 lines keep the pipeline within one CTA's shared memory
-    const size_t smem8 = conv_pipe_smem(A, B, p.n_in, p.Oz, 8);
-    if (smem8 > 200 * 1024) return cudaSuccess;  // too large to pipeline: caller falls back
-    if (p.nlines <= 0) {
-      *used = true;
-      return cudaSuccess;
+  size_t smem8 = 0;
+  if constexpr (A * B >= 640) {
+    smem8 = conv_pipe_smem(A, B, p.n_in, p.Oz, 8);
+    if (smem8 <= 200 * 1024) {
+      e = resident_slots(line2_conv_pipe_kernel<A, B, false, 8>, smem8, granted8, &grid8);
+      if (e != cudaSuccess) return e;
     }
-    auto k = line2_conv_pipe_kernel<A, B, false, 8>;
-    int grid = 0;
-    cudaError_t e = resident_slots(k, smem8, granted8, &grid);
-    if (e != cudaSuccess) return e;
-    if (grid < 1) return cudaSuccess;
-    const long long halves = 2LL * p.nlines;
-    if (grid > halves) grid = (int)halves;
-    k<<<(unsigned)grid, kThreads2, smem8, s>>>(p, none, halves, ni);
-    *used = true;
-    return cudaGetLastError();
   }
-  return cudaSuccess;  // too large to pipeline: caller falls back
+  if (grid16 < 1 && grid8 < 1) return cudaSuccess;  // too large to pipeline: caller falls back
+  if (p.nlines <= 0) {
+    *used = true;
+    return cudaSuccess;
+  }
+  if constexpr (A * B >= 640) {
+    if (grid8 > grid16) {
+      const long long halves = 2LL * p.nlines;
+      const int grid = (int)(grid8 > halves ? halves : grid8);
+      line2_conv_pipe_kernel<A, B, false, 8><<<(unsigned)grid, kThreads2, smem8, s>>>(p, none, halves, ni);
+      *used = true;
+      return cudaGetLastError();
+    }
+  }
+  const int grid = (int)(grid16 > p.nlines ? p.nlines : grid16);
+  line2_conv_pipe_kernel<A, B, false><<<(unsigned)grid, kThreads2, smem16, s>>>(p, none, p.nlines, ni);
+  *used = true;
+  return cudaGetLastError();
 }
 
 template <int A, int B>
