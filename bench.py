@@ -373,7 +373,7 @@ def run_ours(args, world, rank, local):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(w)
+        cpu = cpu_baseline(w, gw)
 
 
     line = {
@@ -521,18 +521,32 @@ def oracle_sample(w):
     return g, f, k, khat, np.prod(g.n)
 
 
-def cpu_baseline(w):
+def cpu_baseline(w, gw=None):
+    """The FP64 oracle timed on the host cores; with the GPU workload given, the same
+    apply on the same synthetic input through the C ABI is compared with it (rel-L2)."""
+    import numpy as np
     from oracle import potential
     g, f, k, khat, vox = oracle_sample(w)
     reps, t_total = 0, 0.0
+    u_ref = None
     while t_total < 10.0 and reps < 20:
         t0 = time.perf_counter()
-        potential.apply_fft(f, g.h, k, khat=khat)
+        u_ref = potential.apply_fft(f, g.h, k, khat=khat)
         t_total += time.perf_counter() - t0
         reps += 1
-    return {"value": vox * reps / t_total, "unit": METRIC, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"FP64 oracle apply_fft (zero-padded FFT convolution, spectrum precomputed) on the "
-                      f"{'x'.join(map(str, g.n))} grid, {reps} repetitions"}
+    out = {"value": vox * reps / t_total, "unit": METRIC, "cores": os.cpu_count(), "kind": "oracle",
+           "sample": f"FP64 oracle apply_fft (zero-padded FFT convolution, spectrum precomputed) on the "
+                     f"{'x'.join(map(str, g.n))} grid, {reps} repetitions"}
+    if gw is not None:
+        import torch
+        n_h = 1 if w.v1_grid is not None else w.steps[0].harmonic
+        fd = torch.from_numpy(np.ascontiguousarray(f).astype(np.complex64)).to(gw.dev)
+        ud = torch.empty_like(fd)
+        gw.plans[n_h].apply(fd, ud)
+        got = ud.cpu().numpy().astype(np.complex128)
+        out["rel_l2_vs_oracle"] = {"harmonic": n_h, "grid": list(g.n),
+                                   "value": float(np.linalg.norm(got - u_ref) / np.linalg.norm(u_ref))}
+    return out
 
 
 def run_reference(args, world, rank):

@@ -34,20 +34,21 @@ __host__ __device__ constexpr int line2_bpitch(int B) { return B + 1; }
 __host__ __device__ constexpr int line2_pitch(int A, int B) { return A * (B + 1) + 1; }
 
 // One 16-column tile (tile index `tile` of p's n_outer x ceil(C/16) tiles).
-template <int A, int B, int DIR, bool SRC>
+template <int A, int B, int DIR, bool SRC, int NL = kLines2>
 __device__ __forceinline__ void col2_tile(const ColSweep& p, int tile, float2* S) {
   constexpr int L = A * B;
   constexpr int LP = col2_pitch(L);
-  const int ncb = (p.C + kLines2 - 1) / kLines2;
+  constexpr int LSH = NL == 16 ? 4 : 3;
+  const int ncb = (p.C + NL - 1) / NL;
   const int o = tile / ncb;
-  const int c0 = (tile - o * ncb) * kLines2;
+  const int c0 = (tile - o * ncb) * NL;
   const float2* __restrict__ tw = p.ax.tw;
   const float2 zero = make_float2(0.f, 0.f);
 
   if constexpr (DIR == kForward) {
-    for (int tau = threadIdx.x; tau < kLines2 * B; tau += blockDim.x) {
-      const int line = tau & (kLines2 - 1);
-      const int b = tau >> 4;
+    for (int tau = threadIdx.x; tau < NL * B; tau += blockDim.x) {
+      const int line = tau & (NL - 1);
+      const int b = tau >> LSH;
       const int c = c0 + line;
       const bool colok = c < p.C;
       const long long base = (long long)o * p.in_os + c;
@@ -87,9 +88,9 @@ __device__ __forceinline__ void col2_tile(const ColSweep& p, int tile, float2* S
       for (int k1 = 1; k1 < A; ++k1) s[k1 * B] = cmul(v[k1], __ldg(&tw[b * k1]));
     }
     __syncthreads();
-    for (int tau = threadIdx.x; tau < kLines2 * A; tau += blockDim.x) {
-      const int line = tau & (kLines2 - 1);
-      const int k1 = tau >> 4;
+    for (int tau = threadIdx.x; tau < NL * A; tau += blockDim.x) {
+      const int line = tau & (NL - 1);
+      const int k1 = tau >> LSH;
       float2 z[B];
       const float2* s = S + line * LP + k1 * B;
 #pragma unroll
@@ -106,9 +107,9 @@ __device__ __forceinline__ void col2_tile(const ColSweep& p, int tile, float2* S
       }
     }
   } else {
-    for (int tau = threadIdx.x; tau < kLines2 * A; tau += blockDim.x) {
-      const int line = tau & (kLines2 - 1);
-      const int k1 = tau >> 4;
+    for (int tau = threadIdx.x; tau < NL * A; tau += blockDim.x) {
+      const int line = tau & (NL - 1);
+      const int k1 = tau >> LSH;
       const int c = c0 + line;
       const bool colok = c < p.C;
       const long long base = (long long)o * p.in_os + c;
@@ -123,9 +124,9 @@ __device__ __forceinline__ void col2_tile(const ColSweep& p, int tile, float2* S
       for (int b = 1; b < B; ++b) s[b] = cmulc(z[b], __ldg(&tw[b * k1]));
     }
     __syncthreads();
-    for (int tau = threadIdx.x; tau < kLines2 * B; tau += blockDim.x) {
-      const int line = tau & (kLines2 - 1);
-      const int b = tau >> 4;
+    for (int tau = threadIdx.x; tau < NL * B; tau += blockDim.x) {
+      const int line = tau & (NL - 1);
+      const int b = tau >> LSH;
       float2 v[A];
       const float2* s = S + line * LP + b;
 #pragma unroll
@@ -148,6 +149,14 @@ template <int A, int B, int DIR, bool SRC>
 __global__ void __launch_bounds__(kThreads2, col2_min_blocks(A * B, DIR)) col2_kernel(const ColSweep p) {
   extern __shared__ float2 S[];
   col2_tile<A, B, DIR, SRC>(p, blockIdx.x, S);
+}
+
+// Long columns (L > 512): 8 columns per CTA, so that two CTAs share an SM; a quarter warp
+// covers one 64-byte row segment.
+template <int A, int B, int DIR, bool SRC>
+__global__ void __launch_bounds__(kThreads2, 2) col2_kernel8(const ColSweep p) {
+  extern __shared__ float2 S[];
+  col2_tile<A, B, DIR, SRC, 8>(p, blockIdx.x, S);
 }
 
 // Batched form: the parameters of up to kMaxBatch plans travel in the kernel's own

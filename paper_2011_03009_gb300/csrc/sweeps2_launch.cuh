@@ -22,6 +22,19 @@ cudaError_t grant_smem(K kernel, size_t bytes, volatile int* granted) {
 template <int A, int B, int DIR, bool SRC>
 cudaError_t col2_launch(const ColSweep& p, cudaStream_t s) {
   static volatile int granted[64] = {0};
+  if constexpr (A * B > 512) {
+    // one 16-column CTA per SM at these lengths: 8-column CTAs, two per SM, instead
+    static volatile int granted8[64] = {0};
+    const size_t smem = (size_t)8 * col2_pitch(A * B) * sizeof(float2);
+    const long long blocks = (long long)((p.C + 7) / 8) * p.n_outer;
+    if (blocks <= 0) return cudaSuccess;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    auto k = col2_kernel8<A, B, DIR, SRC>;
+    cudaError_t e = grant_smem(k, smem, granted8);
+    if (e != cudaSuccess) return e;
+    k<<<(unsigned)blocks, kThreads2, smem, s>>>(p);
+    return cudaGetLastError();
+  }
   const size_t smem = (size_t)kLines2 * col2_pitch(A * B) * sizeof(float2);
   const long long ncb = (p.C + kLines2 - 1) / kLines2;
   const long long blocks = ncb * p.n_outer;
