@@ -104,6 +104,8 @@ def dist_init(args):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch.distributed as dist
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)  # one GPU per rank before any collective
         backend = "nccl" if torch.cuda.is_available() else "gloo"
         dist.init_process_group(backend)
     return world, rank, local
@@ -686,7 +688,8 @@ def run_batch(args, world, rank, local):
             "batched": {"fields_per_s": fields / (ms_batched / 1e3), "ms_per_step": ms_batched},
             "batched_graph": {"fields_per_s": fields / (ms_graph / 1e3), "ms_per_step": ms_graph},
             "voxel_potentials_per_s": voxels / (ms_graph / 1e3)}
-    print(json.dumps(line))
+    if rank == 0:
+        print(json.dumps(line))
 
 
 def _dev_timeit(fn, reps, warmup):
