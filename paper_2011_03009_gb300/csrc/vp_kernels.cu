@@ -300,6 +300,7 @@ __global__ void __launch_bounds__(256) restrict_tiled_kernel(const float2* __res
   const int z0 = zst.i0 - zs;
   const float wx0 = sx_[0].w[0], wx1 = sx_[0].w[1], wx2 = sx_[0].w[2];
   const bool inxz = sx_[0].in && zst.in;
+  const bool full2 = cx == 2 && zst.cnt == 2;  // the y count is checked per row
 #pragma unroll
   for (int k = 0; k < kRowsPerThread; ++k) {
     const int ly = (threadIdx.x / kRtZ) * kRowsPerThread + k;
@@ -312,6 +313,21 @@ __global__ void __launch_bounds__(256) restrict_tiled_kernel(const float2* __res
       continue;
     }
     const int y0 = yst.i0 - ys;
+    if (ORD == 1 && full2 && yst.cnt == 2) {
+      // interior of a linear restriction: the 2 x 2 x 2 stencil, straight-line
+      const float2* t0 = &tile[0][y0][z0];
+      const float2* t1 = &tile[1][y0][z0];
+      const float wz0 = zst.w[0], wz1 = zst.w[1], wy0 = yst.w[0], wy1 = yst.w[1];
+      const float2 a00 = t0[0], a01 = t0[1], a10 = t0[kRsZ], a11 = t0[kRsZ + 1];
+      const float2 b00 = t1[0], b01 = t1[1], b10 = t1[kRsZ], b11 = t1[kRsZ + 1];
+      float2 p0, p1;
+      p0.x = wy0 * fmaf(wz1, a01.x, wz0 * a00.x) + wy1 * fmaf(wz1, a11.x, wz0 * a10.x);
+      p0.y = wy0 * fmaf(wz1, a01.y, wz0 * a00.y) + wy1 * fmaf(wz1, a11.y, wz0 * a10.y);
+      p1.x = wy0 * fmaf(wz1, b01.x, wz0 * b00.x) + wy1 * fmaf(wz1, b11.x, wz0 * b10.x);
+      p1.y = wy0 * fmaf(wz1, b01.y, wz0 * b00.y) + wy1 * fmaf(wz1, b11.y, wz0 * b10.y);
+      dst[idx] = make_float2(fmaf(wx1, p1.x, wx0 * p0.x), fmaf(wx1, p1.y, wx0 * p0.y));
+      continue;
+    }
     float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
     for (int a = 0; a <= ORD; ++a) {

@@ -54,7 +54,7 @@ def test_vector_operations(mods):
     assert rel(host(xt), 2 * x32) <= 1e-7
 
 
-@pytest.mark.parametrize("nh", [2, 4])
+@pytest.mark.parametrize("nh", [2, 4, 8])
 def test_full_source_matches_oracle(mods, nh):
     vp, _ = mods
     g = synth.Grid((20, 18, 22), (0.0, 0.0, 0.0), 1.25e-4)

@@ -54,3 +54,20 @@ def test_vie_matches_oracle(vp, n, harmonic):
     it0, res0 = plan.vie_solve(dev(np.zeros(n)), dev(b), x, tol=1e-7)
     assert np.linalg.norm(host(x) - b32) / np.linalg.norm(b32) <= 1e-6
     plan.close()
+
+
+def test_vie_zero_right_hand_side_and_bad_arguments(vp):
+    g = synth.centred_grid((12, 10, 8), 2e-4, (0.0, 0.0, 0.0))
+    plan = vp.vp_plan(g, 1, 1.0e6, synth.WATER)
+    q = torch.ones(g.n, dtype=torch.complex64, device="cuda") * 1e4
+    b = torch.zeros(g.n, dtype=torch.complex64, device="cuda")
+    x = torch.ones_like(b)
+    with pytest.raises(vp.VpError):       # spectrum not built
+        plan.vie_solve(q, b, x)
+    plan.kernel_fft()
+    it, res = plan.vie_solve(q, b, x)
+    torch.cuda.synchronize()
+    assert it == 0 and res == 0.0 and float(x.abs().max()) == 0.0
+    with pytest.raises(vp.VpError):
+        plan.vie_solve(q, b, x, tol=0.0)
+    plan.close()
