@@ -217,13 +217,23 @@ class GpuWorkload:
         pts = synth.sample_bowl_points(w.bowl, w.n_points, w.seed)
         self.pts = torch.from_numpy(pts).to(device)
         c64 = torch.complex64
-        # inputs: p1 on the grid of harmonic 2 (and on the fundamental grid for V_{k1})
+        # inputs: p1 on the grid of harmonic 2 (and on the fundamental grid for V_{k1}),
+        # from the Rayleigh sum (input generator, timed separately with CUDA events)
         self.p1 = torch.empty(w.p1_grid.n, dtype=c64, device=device)
-        vp.vp_incident_field(w.p1_grid, self.pts, w.bowl, w.medium, self.p1)
         self.p1_v1 = None
         if w.v1_grid is not None:
             self.p1_v1 = torch.empty(w.v1_grid.n, dtype=c64, device=device)
+        vp.vp_incident_field(w.p1_grid, self.pts, w.bowl, w.medium, self.p1)  # warm-up
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        vp.vp_incident_field(w.p1_grid, self.pts, w.bowl, w.medium, self.p1)
+        if w.v1_grid is not None:
             vp.vp_incident_field(w.v1_grid, self.pts, w.bowl, w.medium, self.p1_v1)
+        ev1.record()
+        torch.cuda.synchronize()
+        pairs = (w.p1_grid.voxels + (w.v1_grid.voxels if w.v1_grid is not None else 0)) * w.n_points
+        self.incident = {"ms": round(ev0.elapsed_time(ev1), 3), "voxel_point_pairs": pairs,
+                         "pairs_per_s": pairs / (ev0.elapsed_time(ev1) * 1e-3)}
         self.plans, self.outs = {}, {}
         if w.v1_grid is not None:
             self.plans[1] = vp.vp_plan(w.v1_grid, 1, w.bowl.f0, w.medium)
@@ -393,7 +403,7 @@ def run_ours(args, world, rank, local):
                    "engine": {str(n): list(geo[n][2]) for n in geo},
                    "voxels_per_step": voxels, "bowl_points": w.n_points, "parallelism": f"replicas x{world}",
                    "l2": "flushed between steps (256 MiB write outside the timed events)",
-                   "khat_build_ms": round(gw.khat_build_ms, 2)},
+                   "khat_build_ms": round(gw.khat_build_ms, 2), "incident_field": gw.incident},
         "roofline": roofline, "per_harmonic": per_h, "sweeps": sweeps,
         "e2e": e2e, "cpu_baseline": cpu, "cufft_comparison": cufft, "clocks": clk,
         "gpu_launches": gw.launches_per_step() * args.steps, "wall_s_timed": round(t_wall, 4),
@@ -760,11 +770,41 @@ def run_vie(args):
     reps = max(1, min(args.steps, 5))
     ms = _dev_timeit(solve, reps, min(args.warmup, 2))
     applies = 2 * stats["it"] + 1
+    cpu = None if args.no_cpu_baseline else _vie_cpu_baseline(bowl)
     _line("VIE solves/s", 1e3 / ms, "solves/s", ms, reps, min(args.warmup, 2), True,
           {"workload": "vie_tissue_sphere_r4mm_128cube_h1_R3cm_l6cm_1.1MHz", "grid": list(g.n),
            "solver": "BiCGStab", "tol": 1e-6, "inclusion_voxels": int(inside.sum())},
           iterations=stats["it"], relres=stats["res"], ms_per_iteration=ms / max(1, stats["it"]),
-          operator_applies=applies, voxel_potentials_per_s=applies * g.voxels / (ms / 1e3))
+          operator_applies=applies, voxel_potentials_per_s=applies * g.voxels / (ms / 1e3), cpu_baseline=cpu)
+
+
+def _vie_cpu_baseline(bowl):
+    """FP64 oracle (GMRES on the same discrete operator) on a 32^3 grid of the same
+    recipe: voxel-potentials/s of its operator applications."""
+    import numpy as np
+    from oracle import physics, potential, vie
+    from paper_2011_03009_gb300 import synth
+    g = synth.focus_grid(bowl, (32, 32, 32), 1)
+    kk = vie.sphere_wavenumber(g, (bowl.l + 1e-3, 5e-4, 0.0), 4e-3, 1, bowl.f0, synth.WATER, synth.TISSUE)
+    kb = physics.wavenumber(1, bowl.f0, synth.WATER)
+    q = vie.contrast(kk, kb)
+    b = synth.random_field(g.n, 1)
+    count = {"n": 0}
+    op = vie.operator(q, g.h, kb)
+
+    def counted(x):
+        count["n"] += 1
+        return op(x)
+    import scipy.sparse.linalg as sla
+    import inspect
+    A = sla.LinearOperator((q.size, q.size), matvec=counted, dtype=np.complex128)
+    kw = {"rtol": 1e-6} if "rtol" in inspect.signature(sla.gmres).parameters else {"tol": 1e-6}
+    t0 = time.perf_counter()
+    sla.gmres(A, b.reshape(-1), atol=0.0, restart=60, maxiter=50, **kw)
+    dt = time.perf_counter() - t0
+    return {"value": count["n"] * g.voxels / dt, "unit": "voxel-potentials/s", "cores": os.cpu_count(),
+            "kind": "oracle", "sample": f"FP64 oracle GMRES to 1e-6 on a 32^3 grid of the same recipe "
+                                        f"({count['n']} operator applications, {dt:.2f} s)"}
 
 
 def run_fullcascade(args):
@@ -782,11 +822,24 @@ def run_fullcascade(args):
     reps = max(1, min(args.steps, 3))
     ms = _dev_timeit(solve, reps, min(args.warmup, 1))
     sweeps = len(stats["hist"])
+    cpu = None
+    if not args.no_cpu_baseline:
+        import numpy as np
+        from oracle import cascade as ocascade
+        gs = synth.focus_grid(bowl, (32, 32, 32), 5)
+        p_inc_s = synth.random_field(gs.n, 3, scale=4.0e5)  # synthetic input of the oracle's own
+        t0 = time.perf_counter()
+        ocascade.full_cascade(p_inc_s, 5, gs.h, bowl.f0, synth.WATER, iters=3)
+        dt = time.perf_counter() - t0
+        applies = 4 + 3 * 5  # weakly nonlinear start + 3 sweeps of 5 harmonics
+        cpu = {"value": applies * gs.voxels / dt, "unit": "voxel-potentials/s", "cores": os.cpu_count(),
+               "kind": "oracle", "sample": f"FP64 oracle full cascade, 3 Jacobi sweeps of N_h = 5 on a 32^3 grid "
+                                           f"({dt:.2f} s)"}
     _line("full-cascade solves/s", 1e3 / ms, "solves/s", ms, reps, min(args.warmup, 1), True,
           {"workload": "fullcascade_Nh5_128cube_h5spacing_R3cm_l6cm_1.1MHz", "grid": list(g.n), "harmonics": 5,
            "tol": 1e-6},
           sweeps=sweeps, change_history=stats["hist"], ms_per_sweep=ms / max(1, sweeps),
-          voxel_potentials_per_s=(5 * (sweeps + 1)) * g.voxels / (ms / 1e3))
+          voxel_potentials_per_s=(5 * (sweeps + 1)) * g.voxels / (ms / 1e3), cpu_baseline=cpu)
     fc.close()
 
 
@@ -817,8 +870,24 @@ def run_q0(args):
     rows = domain.q0_study(g3, 3, wl.bowl.f0, f3, r1, q0s, wl.medium)
     torch.cuda.synchronize()
     sec = time.perf_counter() - t0
+    cpu = None
+    if not args.no_cpu_baseline:
+        from oracle import domain as odomain
+        # the oracle times its own synthetic field of the same size (no input from the GPU path)
+        f_host = synth.smooth_blob_field(g3, (wl.bowl.l, 0.0, 0.0), 20 * g3.h, 1.0).astype("complex64")
+        t0 = time.perf_counter()
+        for q0 in q0s:
+            odomain.q0_box(f_host, q0)
+        dt = time.perf_counter() - t0
+        t1 = time.perf_counter()
+        for q0 in q0s:
+            vp.vp_q0_box(f3, q0)
+        dt_gpu = time.perf_counter() - t1
+        cpu = {"value": dt, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"FP64 oracle Q0 boxes of the same 256^3 source for the {len(q0s)} thresholds "
+                         f"(the GPU's vp_q0_box for the same: {dt_gpu:.4f} s including host sync)"}
     _line("Q0 study time", sec, "s", sec * 1e3, 1, 0, False,
-          {"workload": "q0_study_h3_256cube_nested3", "q0": q0s, "grid": list(g3.n)}, rows=rows)
+          {"workload": "q0_study_h3_256cube_nested3", "q0": q0s, "grid": list(g3.n)}, rows=rows, cpu_baseline=cpu)
 
 
 def main():

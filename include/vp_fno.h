@@ -3,7 +3,7 @@
  *
  * The paper has no learned component; this surrogate maps the normalised fundamental
  * on an N^3 focal box to the normalised harmonics 2..5 on the same box, and the plain
- * volume potential (vp.h) stays the judge of its error and the fallback.  The cascade
+ * volume potential (vp.h) stays the reference for its error and the fallback.  The cascade
  * of Eq. 2.6 makes p_n homogeneous of degree n in p1, so with s = max |p1| the network
  * maps q1 = p1 / s (2 channels: Re, Im) to q_n = p_n / s^n (8 channels: Re, Im of
  * n = 2..5), and p_n = s^n q_n exactly undoes the scaling.

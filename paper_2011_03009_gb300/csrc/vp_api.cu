@@ -536,7 +536,7 @@ static void set_physics(vp_plan_s* p, const vp_grid* g, int harmonic_n, double f
 // Stream-ordered pool of this library for the kernel-spectrum scratch cube (8 M^3
 // bytes per vp_kernel_fft).  Freed blocks up to kScratchKeep bytes stay reserved across
 // synchronisations, so a sequence of vp_kernel_fft calls of one size maps device memory
-// once; larger cubes go back to the driver at the next synchronisation.  Null if the
+// once; larger cubes are released at the next synchronisation.  Null if the
 // device has no memory-pool support (the default pool is used then).
 constexpr unsigned long long kScratchKeep = 2ULL << 30;
 

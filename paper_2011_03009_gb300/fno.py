@@ -3,7 +3,7 @@
 Every step runs in libvp.so's kernels (include/vp_fno.h): the forward and backward
 passes on BF16 tensor cores, the loss and Adam.  This module only allocates device
 buffers (torch), orders the calls and generates training data with the plain
-volume-potential path (include/vp.h), which also judges the surrogate's error.
+volume-potential path (include/vp.h), which is also the reference for the surrogate's error.
 
 Data: each sample is one seeded bowl configuration.  Harmonic n lives on an N^3 grid
 at lambda_n / 6 centred on the focus (equal voxel counts, domains shrinking with the
@@ -230,7 +230,8 @@ def harmonic_grids(bowl: synth.Bowl, n: int, medium=synth.WATER):
 
 
 class PlainCascade:
-    """Harmonics 2..5 of one bowl on the focal box by the plain GPU path (the judge)."""
+    """Harmonics 2..5 of one bowl on the focal box by the plain GPU path (the reference the
+    surrogate is measured against)."""
 
     def __init__(self, n: int, n_points: int = 512, medium=synth.WATER, device="cuda"):
         self.n, self.n_points, self.medium, self.device = n, n_points, medium, torch.device(device)

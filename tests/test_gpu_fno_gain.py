@@ -1,14 +1,14 @@
 """What the trained surrogate gains over the method without it, on the GPU.
 
 - Training gains accuracy: a small surrogate trained briefly on fields from the plain
-  path (the judge) has a held-out relative L2 error, per harmonic, well below that of the
+  path (the reference) has a held-out relative L2 error, per harmonic, well below that of the
   same network before training.
 - Inference cost: at the 128^3 focal box, one evaluation of the surrogate in the
   workload's architecture (4 layers, width 48, 32 x 32 x 16 modes) is timed against the
   plain cascade it would replace (kernel spectra, restrictions, sources and potentials
   of harmonics 2..5), both from p1 on the device; timing does not depend on the weights'
   values.  Both are reported; which one is faster is a measured outcome, not assumed.
-- Every held-out sample is judged by the plain path; those above the 1e-2 threshold are
+- Every held-out sample is checked against the plain path; those above the 1e-2 threshold are
   the ones that fall back (counted, not hidden).
 """
 import numpy as np
