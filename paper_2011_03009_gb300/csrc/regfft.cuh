@@ -9,6 +9,8 @@
 // evaluated at compile time in double precision by constexpr series below.
 #pragma once
 
+#include <type_traits>
+
 #include "fft_engine.cuh"
 
 namespace vp {
@@ -143,6 +145,71 @@ __device__ __forceinline__ void dft_reg(float2* v) {
 #pragma unroll
       for (int b = 0; b < Q; ++b) z[b] = y[b * P + k1];
       dft_reg<Q, INV>(z);
+#pragma unroll
+      for (int k2 = 0; k2 < Q; ++k2) v[k1 + P * k2] = z[k2];
+    }
+  }
+}
+
+// f(std::integral_constant<int, i>) for i = I .. E-1, each i a compile-time constant.
+template <int I, int E, typename F>
+__device__ __forceinline__ void static_for(F& f) {
+  if constexpr (I < E) {
+    f(std::integral_constant<int, I>{});
+    static_for<I + 1, E>(f);
+  }
+}
+
+// dft_reg<N, INV> for an input whose entries v[n], n >= NZ, are zero: those entries are
+// neither read nor added.  A zero-padded line (NZ = N / 2) saves the first butterfly
+// layer and half the loads.  Outputs that the caller never reads are removed by the
+// compiler as dead code, so a cropped output needs no variant of its own.
+template <int N, bool INV, int NZ>
+__device__ __forceinline__ void dft_reg_nz(float2* v) {
+  if constexpr (NZ >= N) {
+    dft_reg<N, INV>(v);
+  } else if constexpr (NZ <= 0) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) v[k] = make_float2(0.f, 0.f);
+  } else if constexpr (NZ == 1) {
+#pragma unroll
+    for (int k = 1; k < N; ++k) v[k] = v[0];
+  } else if constexpr (N <= 5) {
+    // X[k] = sum_{n < NZ} v[n] w_N^(n k), written out
+    float2 x[NZ];
+#pragma unroll
+    for (int n = 0; n < NZ; ++n) x[n] = v[n];
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      float2 acc = x[0];
+#pragma unroll
+      for (int n = 1; n < NZ; ++n) acc = cadd(acc, twiddle_const<N, INV>(x[n], n * k));
+      v[k] = acc;
+    }
+  } else {
+    // the split of dft_reg; row b of the first level holds v[Q a + b], nonzero for
+    // Q a + b < NZ, and rows b >= NZ are zero altogether
+    constexpr int P = ct::first_factor(N);
+    constexpr int Q = N / P;
+    constexpr int NZ2 = NZ < Q ? NZ : Q;
+    float2 y[NZ2 * P];
+    auto row = [&](auto bc) {
+      constexpr int b = decltype(bc)::value;
+      constexpr int na = (NZ - b + Q - 1) / Q < P ? (NZ - b + Q - 1) / Q : P;
+      float2 u[P];
+#pragma unroll
+      for (int a = 0; a < na; ++a) u[a] = v[Q * a + b];
+      dft_reg_nz<P, INV, na>(u);
+#pragma unroll
+      for (int k1 = 0; k1 < P; ++k1) y[b * P + k1] = twiddle_const<N, INV>(u[k1], b * k1);
+    };
+    static_for<0, NZ2>(row);
+#pragma unroll
+    for (int k1 = 0; k1 < P; ++k1) {
+      float2 z[Q];
+#pragma unroll
+      for (int b = 0; b < NZ2; ++b) z[b] = y[b * P + k1];
+      dft_reg_nz<Q, INV, NZ2>(z);
 #pragma unroll
       for (int k2 = 0; k2 < Q; ++k2) v[k1 + P * k2] = z[k2];
     }

@@ -30,13 +30,18 @@ __host__ __device__ constexpr int col2_min_blocks(int L, int dir) {
   // are latency-bound, so the fourth CTA pays; their inverse variants spill there
   return (L <= 384 && dir == kForward) ? 4 : (L <= 512 ? 3 : 1);
 }
+// Rows a of x[B a + b] that can be nonzero on a zero-padded line (n <= L / 2).
+__host__ __device__ constexpr int conv_rows_in(int A) { return (A + 1) / 2; }
 __host__ __device__ constexpr int line2_bpitch(int B) { return B + 1; }
 __host__ __device__ constexpr int line2_pitch(int A, int B) { return A * (B + 1) + 1; }
 
 // One 16-column tile (tile index `tile` of p's n_outer x ceil(C/16) tiles).
-template <int A, int B, int DIR, bool SRC, int NL = kLines2>
+// HALF: the forward input has rows_in <= L / 2 (zero-padded), or the inverse output has
+// rows_out <= L / 2 (cropped), so only rows a < AH of x[B a + b] are read or written.
+template <int A, int B, int DIR, bool SRC, bool HALF, int NL = kLines2>
 __device__ __forceinline__ void col2_tile(const ColSweep& p, int tile, float2* S) {
   constexpr int L = A * B;
+  constexpr int AH = HALF ? conv_rows_in(A) : A;
   constexpr int LP = col2_pitch(L);
   constexpr int LSH = NL == 16 ? 4 : 3;
   const int ncb = (p.C + NL - 1) / NL;
@@ -63,7 +68,7 @@ __device__ __forceinline__ void col2_tile(const ColSweep& p, int tile, float2* S
           const float2* __restrict__ pb = p.lower[n - m - 1];
           const float w = ((2 * m == n) ? 1.f : 2.f) * p.cn;
 #pragma unroll
-          for (int a = 0; a < A; ++a) {
+          for (int a = 0; a < AH; ++a) {
             const int row = B * a + b;
             if (colok && row < p.rows_in) {
               const long long off = base + (long long)row * p.in_rs;
@@ -76,12 +81,12 @@ __device__ __forceinline__ void col2_tile(const ColSweep& p, int tile, float2* S
         }
       } else {
 #pragma unroll
-        for (int a = 0; a < A; ++a) {
+        for (int a = 0; a < AH; ++a) {
           const int row = B * a + b;
           v[a] = (colok && row < p.rows_in) ? __ldg(&p.in[base + (long long)row * p.in_rs]) : zero;
         }
       }
-      dft_reg<A, false>(v);
+      dft_reg_nz<A, false, AH>(v);
       float2* s = S + line * LP + b;
       s[0] = v[0];
 #pragma unroll
@@ -136,7 +141,7 @@ __device__ __forceinline__ void col2_tile(const ColSweep& p, int tile, float2* S
       if (c < p.C) {
         const long long base = (long long)o * p.out_os + c;
 #pragma unroll
-        for (int a = 0; a < A; ++a) {
+        for (int a = 0; a < AH; ++a) {
           const int row = B * a + b;
           if (row < p.rows_out) p.out[base + (long long)row * p.out_rs] = cscale(v[a], p.scale);
         }
@@ -145,18 +150,18 @@ __device__ __forceinline__ void col2_tile(const ColSweep& p, int tile, float2* S
   }
 }
 
-template <int A, int B, int DIR, bool SRC>
+template <int A, int B, int DIR, bool SRC, bool HALF>
 __global__ void __launch_bounds__(kThreads2, col2_min_blocks(A * B, DIR)) col2_kernel(const ColSweep p) {
   extern __shared__ float2 S[];
-  col2_tile<A, B, DIR, SRC>(p, blockIdx.x, S);
+  col2_tile<A, B, DIR, SRC, HALF>(p, blockIdx.x, S);
 }
 
 // Long columns (L > 512): 8 columns per CTA, so that two CTAs share an SM; a quarter warp
 // covers one 64-byte row segment.
-template <int A, int B, int DIR, bool SRC>
+template <int A, int B, int DIR, bool SRC, bool HALF>
 __global__ void __launch_bounds__(kThreads2, 2) col2_kernel8(const ColSweep p) {
   extern __shared__ float2 S[];
-  col2_tile<A, B, DIR, SRC, 8>(p, blockIdx.x, S);
+  col2_tile<A, B, DIR, SRC, HALF, 8>(p, blockIdx.x, S);
 }
 
 // Batched form: the parameters of up to kMaxBatch plans travel in the kernel's own
@@ -181,12 +186,12 @@ __device__ __forceinline__ void copy_params(T* dst, const T* src) {
   for (int i = threadIdx.x; i < (int)(sizeof(T) / 4); i += blockDim.x) d[i] = __ldg(&s[i]);
 }
 
-template <int A, int B, int DIR, bool SRC>
+template <int A, int B, int DIR, bool SRC, bool HALF>
 __global__ void __launch_bounds__(kThreads2, col2_min_blocks(A * B, DIR))
     col2_batch_kernel(const __grid_constant__ BatchParams<ColSweep> bp) {
   extern __shared__ float2 S[];
   const int owner = batch_owner(bp, blockIdx.x);
-  col2_tile<A, B, DIR, SRC>(bp.item[owner], blockIdx.x - bp.offsets[owner], S);
+  col2_tile<A, B, DIR, SRC, HALF>(bp.item[owner], blockIdx.x - bp.offsets[owner], S);
 }
 
 // One tile of 16 lines (conv: tile `tile` of the tile list; forward: lines 16 tile ..).
@@ -317,9 +322,10 @@ __global__ void __launch_bounds__(kThreads2) line2_batch_kernel(const __grid_con
 // spectrum lines (4 x Oz), twiddles (L).
 // NL = 8 (long lines): a CTA takes half a tile of the host's list (2 mirror groups of
 // 4 lines and their 2 octant lines), so the buffers fit in shared memory at L >= 1024.
-__host__ __device__ constexpr int conv_stage_pitch(int n_in) { return n_in | 1; }  // odd: lanes = lines
-__host__ __device__ constexpr size_t conv_pipe_smem(int A, int B, int n_in, int Oz, int NL = kLines2) {
-  return ((size_t)NL * line2_pitch(A, B) + (size_t)NL * conv_stage_pitch(n_in) + (size_t)(NL / 4) * Oz +
+// The staging pitch that holds rows a < conv_rows_in(A) of a line (odd: lanes = lines).
+__host__ __device__ constexpr int conv_stage_pitch(int A, int B) { return (B * conv_rows_in(A)) | 1; }
+__host__ __device__ constexpr size_t conv_pipe_smem(int A, int B, int Oz, int NL = kLines2) {
+  return ((size_t)NL * line2_pitch(A, B) + (size_t)NL * conv_stage_pitch(A, B) + (size_t)(NL / 4) * Oz +
           (size_t)A * B) *
          sizeof(float2);
 }
@@ -336,6 +342,8 @@ __global__ void __launch_bounds__(kThreads2)
   constexpr int L = A * B;
   constexpr int BP = line2_bpitch(B);
   constexpr int LP = line2_pitch(A, B);
+  constexpr int AH = conv_rows_in(A);
+  static_assert(B % 2 == 0, "the spectrum fold takes an even B");
   extern __shared__ float2 S[];
   const int Oz = p.Oz;  // shared by every plan of a batch group
   constexpr int NG = NL / 4;       // mirror groups per CTA tile
@@ -346,7 +354,6 @@ __global__ void __launch_bounds__(kThreads2)
   __shared__ long long line_of[2][NL];
   __shared__ int oct_of[2][NG];
   __shared__ const LineSweep* plan_of[2];
-  const float2 zero = make_float2(0.f, 0.f);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   // plan and local tile index of global tile t
@@ -410,18 +417,17 @@ __global__ void __launch_bounds__(kThreads2)
     float2* const data = q->data;
     const long long ld = q->ld;
     // forward step 1 from the staging buffer; the 16 lanes of a half-warp hold the 16
-    // lines (odd staging pitch), so every twiddle read is a broadcast
+    // lines (odd staging pitch), so every twiddle read is a broadcast.  The line is
+    // zero from n_in <= L / 2 on: only rows a < AH are read (the staging buffer holds
+    // zeros from n_in to B AH), and the DFT skips the rest.
     for (int tau = threadIdx.x; tau < NL * B; tau += blockDim.x) {
       const int line = tau & (NL - 1);
       const int b = tau >> LSH;
       const float2* src = I + line * NI;
       float2 v[A];
 #pragma unroll
-      for (int a = 0; a < A; ++a) {
-        const int n = B * a + b;
-        v[a] = n < NI ? src[n] : zero;  // the staging buffer holds zeros past n_in
-      }
-      dft_reg<A, false>(v);
+      for (int a = 0; a < AH; ++a) v[a] = src[B * a + b];
+      dft_reg_nz<A, false, AH>(v);
       float2* s = S + line * LP + b;
       s[0] = v[0];
 #pragma unroll
@@ -441,12 +447,12 @@ __global__ void __launch_bounds__(kThreads2)
       for (int b = 0; b < B; ++b) z[b] = s[b];
       dft_reg<B, false>(z);
       if (oct_of[cur][line >> 2] >= 0) {
-        const float2* kl = K + (line >> 2) * Oz;
+        // frequency f = k1 + A k2 folds to min(f, L - f): f itself below k2 = B / 2,
+        // L - f from there on (B is even), so both reads take constant offsets
+        const float2* lo = K + (line >> 2) * Oz + k1;
+        const float2* hi = K + (line >> 2) * Oz + (L - k1);
 #pragma unroll
-        for (int k2 = 0; k2 < B; ++k2) {
-          const int f = k1 + A * k2;
-          z[k2] = cmul(z[k2], kl[min(f, L - f)]);
-        }
+        for (int k2 = 0; k2 < B; ++k2) z[k2] = cmul(z[k2], 2 * k2 < B ? lo[A * k2] : hi[-A * k2]);
       }
       dft_reg<B, true>(z);
       s[0] = z[0];
@@ -464,12 +470,12 @@ __global__ void __launch_bounds__(kThreads2)
       const float2* s = S + line * LP + b;
 #pragma unroll
       for (int k1 = 0; k1 < A; ++k1) v[k1] = s[k1 * BP];
-      dft_reg<A, true>(v);
+      dft_reg<A, true>(v);  // rows a >= AH lie past n_out <= L / 2: never stored, not computed
       const long long l = line_of[cur][line];
       if (l >= 0) {
         float2* dst = data + l * ld;
 #pragma unroll
-        for (int a = 0; a < A; ++a) {
+        for (int a = 0; a < AH; ++a) {
           const int n = B * a + b;
           if (n < n_out) dst[n] = v[a];
         }

@@ -19,7 +19,7 @@ cudaError_t grant_smem(K kernel, size_t bytes, volatile int* granted) {
   return e;
 }
 
-template <int A, int B, int DIR, bool SRC>
+template <int A, int B, int DIR, bool SRC, bool HALF>
 cudaError_t col2_launch(const ColSweep& p, cudaStream_t s) {
   static volatile int granted[64] = {0};
   if constexpr (A * B > 512) {
@@ -29,7 +29,7 @@ cudaError_t col2_launch(const ColSweep& p, cudaStream_t s) {
     const long long blocks = (long long)((p.C + 7) / 8) * p.n_outer;
     if (blocks <= 0) return cudaSuccess;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    auto k = col2_kernel8<A, B, DIR, SRC>;
+    auto k = col2_kernel8<A, B, DIR, SRC, HALF>;
     cudaError_t e = grant_smem(k, smem, granted8);
     if (e != cudaSuccess) return e;
     k<<<(unsigned)blocks, kThreads2, smem, s>>>(p);
@@ -40,7 +40,7 @@ cudaError_t col2_launch(const ColSweep& p, cudaStream_t s) {
   const long long blocks = ncb * p.n_outer;
   if (blocks <= 0) return cudaSuccess;
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-  auto k = col2_kernel<A, B, DIR, SRC>;
+  auto k = col2_kernel<A, B, DIR, SRC, HALF>;
   cudaError_t e = grant_smem(k, smem, granted);
   if (e != cudaSuccess) return e;
   k<<<(unsigned)blocks, kThreads2, smem, s>>>(p);
@@ -61,11 +61,24 @@ cudaError_t line2_launch(const LineSweep& p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Whether a column sweep reads (forward) or writes (inverse) only the first half of its
+// columns: true for every sweep of the zero-padded convolution, false for the kernel
+// spectrum, whose lattice fills the whole embedding.
+inline bool col2_half(const ColSweep& p, int L, int dir) {
+  return dir == kForward ? 2 * p.rows_in <= L : 2 * p.rows_out <= L;
+}
+
 template <int A, int B>
 cudaError_t col2_dispatch(const ColSweep& p, int dir, bool src, cudaStream_t s) {
-  if (dir == kForward && src) return col2_launch<A, B, kForward, true>(p, s);
-  if (dir == kForward) return col2_launch<A, B, kForward, false>(p, s);
-  return col2_launch<A, B, kInverse, false>(p, s);
+  const bool half = col2_half(p, A * B, dir);
+  if (dir == kForward && src) {
+    // the source's grid is the embedded one: N <= M / 2 for every even M >= 2 N - 1
+    if (!half) return cudaErrorInvalidValue;
+    return col2_launch<A, B, kForward, true, true>(p, s);
+  }
+  if (dir == kForward) return half ? col2_launch<A, B, kForward, false, true>(p, s)
+                                   : col2_launch<A, B, kForward, false, false>(p, s);
+  return half ? col2_launch<A, B, kInverse, false, true>(p, s) : col2_launch<A, B, kInverse, false, false>(p, s);
 }
 
 // Persistent pipelined convolution sweep: one CTA per resident slot, tiles strided.
@@ -101,12 +114,15 @@ cudaError_t line2_conv_pipe_launch(const LineSweep& p, cudaStream_t s, bool* use
   static volatile int granted[64] = {0};
   static volatile int granted8[64] = {0};
   *used = false;
-  const int ni = conv_stage_pitch(p.n_in);
+  // the kernel reads and writes the first half of each line only (zero-padded input,
+  // cropped output); any other line goes to line2_kernel
+  if (2 * p.n_in > A * B || 2 * p.n_out > A * B) return cudaSuccess;
+  const int ni = conv_stage_pitch(A, B);
   static BatchParams<LineSweep> none{};  // unused by the single-plan form
   // tiles of 16 lines, or (long lines) half tiles of 8 lines when those fit more CTAs per
   // SM: at L = 640-864 one 16-line CTA fills an SM's shared memory, two 8-line CTAs fit;
   // from L = 1024 only the 8-line form fits at all
-  const size_t smem16 = conv_pipe_smem(A, B, p.n_in, p.Oz);
+  const size_t smem16 = conv_pipe_smem(A, B, p.Oz);
   int grid16 = 0, grid8 = 0;
   cudaError_t e;
   if (smem16 <= 200 * 1024) {
@@ -115,7 +131,7 @@ cudaError_t line2_conv_pipe_launch(const LineSweep& p, cudaStream_t s, bool* use
   }
   size_t smem8 = 0;
   if constexpr (A * B >= 640) {
-    smem8 = conv_pipe_smem(A, B, p.n_in, p.Oz, 8);
+    smem8 = conv_pipe_smem(A, B, p.Oz, 8);
     if (smem8 <= 200 * 1024) {
       e = resident_slots(line2_conv_pipe_kernel<A, B, false, 8>, smem8, granted8, &grid8);
       if (e != cudaSuccess) return e;
@@ -152,12 +168,12 @@ cudaError_t line2_dispatch(const LineSweep& p, int mode, cudaStream_t s) {
   return line2_launch<A, B, kForwardOnly>(p, s);
 }
 
-template <int A, int B, int DIR, bool SRC>
+template <int A, int B, int DIR, bool SRC, bool HALF>
 cudaError_t col2_batch_launch(const BatchParams<ColSweep>& bp, int total, cudaStream_t s) {
   static volatile int granted[64] = {0};
   const size_t smem = (size_t)kLines2 * col2_pitch(A * B) * sizeof(float2);
   if (total <= 0) return cudaSuccess;
-  auto k = col2_batch_kernel<A, B, DIR, SRC>;
+  auto k = col2_batch_kernel<A, B, DIR, SRC, HALF>;
   cudaError_t e = grant_smem(k, smem, granted);
   if (e != cudaSuccess) return e;
   k<<<(unsigned)total, kThreads2, smem, s>>>(bp);
@@ -166,20 +182,28 @@ cudaError_t col2_batch_launch(const BatchParams<ColSweep>& bp, int total, cudaSt
 
 template <int A, int B>
 cudaError_t col2_batch_dispatch(const BatchParams<ColSweep>& bp, int total, int dir, bool src, cudaStream_t s) {
-  if (dir == kForward && src) return col2_batch_launch<A, B, kForward, true>(bp, total, s);
-  if (dir == kForward) return col2_batch_launch<A, B, kForward, false>(bp, total, s);
-  return col2_batch_launch<A, B, kInverse, false>(bp, total, s);
+  bool half = true;
+  for (int i = 0; i < bp.count; ++i) half = half && col2_half(bp.item[i], A * B, dir);
+  if (dir == kForward && src) {
+    if (!half) return cudaErrorInvalidValue;
+    return col2_batch_launch<A, B, kForward, true, true>(bp, total, s);
+  }
+  if (dir == kForward) return half ? col2_batch_launch<A, B, kForward, false, true>(bp, total, s)
+                                   : col2_batch_launch<A, B, kForward, false, false>(bp, total, s);
+  return half ? col2_batch_launch<A, B, kInverse, false, true>(bp, total, s)
+              : col2_batch_launch<A, B, kInverse, false, false>(bp, total, s);
 }
 
 // Batched z sweep: the pipelined persistent kernel over every tile of the group when
 // its shared memory fits, else one CTA per tile.  first: any plan of the group (for the
-// shared twiddle table and octant length); ni_max: longest input line of the group.
+// shared twiddle table and octant length); ni_max: longest input or output line of the
+// group.
 template <int A, int B>
 cudaError_t line2_batch_dispatch(const LineSweep& first, int ni_max, const BatchParams<LineSweep>& bp, int total,
                                  cudaStream_t s) {
   if (total <= 0) return cudaSuccess;
-  const size_t psmem = conv_pipe_smem(A, B, ni_max, first.Oz);
-  if (psmem <= 200 * 1024) {
+  const size_t psmem = conv_pipe_smem(A, B, first.Oz);
+  if (psmem <= 200 * 1024 && 2 * ni_max <= A * B) {
     static volatile int pgranted[64] = {0};
     auto k = line2_conv_pipe_kernel<A, B, true>;
     int grid = 0;
@@ -187,7 +211,7 @@ cudaError_t line2_batch_dispatch(const LineSweep& first, int ni_max, const Batch
     if (e != cudaSuccess) return e;
     if (grid >= 1) {
       if (grid > total) grid = total;
-      k<<<(unsigned)grid, kThreads2, psmem, s>>>(first, bp, total, conv_stage_pitch(ni_max));
+      k<<<(unsigned)grid, kThreads2, psmem, s>>>(first, bp, total, conv_stage_pitch(A, B));
       return cudaGetLastError();
     }
   }

@@ -438,7 +438,7 @@ struct BatchChunk {
   vp::BatchParams<LineSweep> line;
   int total[5] = {0, 0, 0, 0, 0};
   LineSweep first{};  // any item's z-sweep parameters (shared twiddle table, octant length)
-  int ni_max = 0;     // longest z input line of the chunk
+  int ni_max = 0;     // longest z input or output line of the chunk
 };
 
 struct BatchGroup {
@@ -494,7 +494,7 @@ int build_group(vp_batch_s* b, BatchGroup& g) {
       ch->line.item[j] = l;
       ch->line.offsets[j] = (int)acc[2];
       acc[2] += l.nlines;
-      ch->ni_max = std::max(ch->ni_max, l.n_in);
+      ch->ni_max = std::max(ch->ni_max, std::max(l.n_in, l.n_out));
       if (j == 0) ch->first = l;
     }
     for (int w = 0; w < 5; ++w) {
