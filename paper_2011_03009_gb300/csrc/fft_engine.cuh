@@ -53,8 +53,20 @@ __device__ __forceinline__ long long vp_chk(long long i, long long n, int code, 
 #define VP_CHKX(i, n, code, a, b, c, d) (i)
 #endif
 
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// Complex add and subtract as one paired FP32 add (f32x2) each: per component the same
+// round-to-nearest add as the scalar form, in half the instruction issues.
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+// t + (-i) d and t - (-i) d (forward), t + i d and t - i d (inverse): the swapped
+// operand suits scalar adds, so these two stay scalar.
+template <bool INV>
+__device__ __forceinline__ float2 add_mi(float2 t, float2 d) {
+  return INV ? make_float2(t.x - d.y, t.y + d.x) : make_float2(t.x + d.y, t.y - d.x);
+}
+template <bool INV>
+__device__ __forceinline__ float2 sub_mi(float2 t, float2 d) {
+  return INV ? make_float2(t.x + d.y, t.y - d.x) : make_float2(t.x - d.y, t.y + d.x);
+}
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
@@ -87,11 +99,11 @@ __device__ __forceinline__ void dft2(float2& a, float2& b) {
 template <bool INV>
 __device__ __forceinline__ void dft4(float2& v0, float2& v1, float2& v2, float2& v3) {
   float2 t0 = cadd(v0, v2), t1 = csub(v0, v2);
-  float2 t2 = cadd(v1, v3), t3 = mul_mi<INV>(csub(v1, v3));
+  float2 t2 = cadd(v1, v3), d = csub(v1, v3);
   v0 = cadd(t0, t2);
   v2 = csub(t0, t2);
-  v1 = cadd(t1, t3);
-  v3 = csub(t1, t3);
+  v1 = add_mi<INV>(t1, d);
+  v3 = sub_mi<INV>(t1, d);
 }
 
 template <bool INV>
@@ -101,9 +113,9 @@ __device__ __forceinline__ void dft3(float2* v) {
   float2 d = csub(v[1], v[2]);
   float2 m = make_float2(fmaf(c, t.x, v[0].x), fmaf(c, t.y, v[0].y));
   v[0] = cadd(v[0], t);
-  float2 sd = mul_mi<INV>(cscale(d, s));
-  v[1] = cadd(m, sd);
-  v[2] = csub(m, sd);
+  float2 sd = cscale(d, s);
+  v[1] = add_mi<INV>(m, sd);
+  v[2] = sub_mi<INV>(m, sd);
 }
 
 template <bool INV>
@@ -119,11 +131,10 @@ __device__ __forceinline__ void dft5(float2* v) {
   float2 b1 = make_float2(s1 * d1.x + s2 * d2.x, s1 * d1.y + s2 * d2.y);
   float2 b2 = make_float2(s2 * d1.x - s1 * d2.x, s2 * d1.y - s1 * d2.y);
   v[0] = cadd(v[0], cadd(t1, t2));
-  float2 ib1 = mul_mi<INV>(b1), ib2 = mul_mi<INV>(b2);
-  v[1] = cadd(a1, ib1);
-  v[4] = csub(a1, ib1);
-  v[2] = cadd(a2, ib2);
-  v[3] = csub(a2, ib2);
+  v[1] = add_mi<INV>(a1, b1);
+  v[4] = sub_mi<INV>(a1, b1);
+  v[2] = add_mi<INV>(a2, b2);
+  v[3] = sub_mi<INV>(a2, b2);
 }
 
 template <bool INV>
@@ -133,15 +144,15 @@ __device__ __forceinline__ void dft8(float2* v) {
   dft4<INV>(v[0], v[2], v[4], v[6]);
   dft4<INV>(v[1], v[3], v[5], v[7]);
   float2 o1 = mul_const<INV>(v[3], c, -c);
-  float2 o2 = mul_mi<INV>(v[5]);
+  float2 o2 = v[5];  // times -i (forward) or i (inverse), taken by add_mi / sub_mi
   float2 o3 = mul_const<INV>(v[7], -c, -c);
   float2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6], o0 = v[1];
   v[0] = cadd(e0, o0);
   v[4] = csub(e0, o0);
   v[1] = cadd(e1, o1);
   v[5] = csub(e1, o1);
-  v[2] = cadd(e2, o2);
-  v[6] = csub(e2, o2);
+  v[2] = add_mi<INV>(e2, o2);
+  v[6] = sub_mi<INV>(e2, o2);
   v[3] = cadd(e3, o3);
   v[7] = csub(e3, o3);
 }

@@ -113,6 +113,17 @@ __device__ __forceinline__ float2 twiddle_const(float2 v, int k) {
   return mul_const<INV>(v, tab.c[k], -tab.s[k]);  // exp(-i theta) = (cos, -sin)
 }
 
+// acc + v * w_N^(k), k constant: the powers +-1 and +-i fold into the add.
+template <int N, bool INV>
+__device__ __forceinline__ float2 add_twiddled(float2 acc, float2 v, int k) {
+  k %= N;
+  if (k == 0) return cadd(acc, v);
+  if (2 * k == N) return csub(acc, v);
+  if (4 * k == N) return add_mi<INV>(acc, v);
+  if (4 * k == 3 * N) return sub_mi<INV>(acc, v);
+  return cadd(acc, twiddle_const<N, INV>(v, k));
+}
+
 template <int N, bool INV>
 __device__ __forceinline__ void dft_reg(float2* v) {
   if constexpr (N == 1) {
@@ -183,7 +194,7 @@ __device__ __forceinline__ void dft_reg_nz(float2* v) {
     for (int k = 0; k < N; ++k) {
       float2 acc = x[0];
 #pragma unroll
-      for (int n = 1; n < NZ; ++n) acc = cadd(acc, twiddle_const<N, INV>(x[n], n * k));
+      for (int n = 1; n < NZ; ++n) acc = add_twiddled<N, INV>(acc, x[n], n * k);
       v[k] = acc;
     }
   } else {
