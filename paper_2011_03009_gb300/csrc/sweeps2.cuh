@@ -317,9 +317,10 @@ __global__ void __launch_bounds__(kThreads2) line2_batch_kernel(const __grid_con
 // step 2, spectrum multiply and inverse step 2; the next tile's four octant lines of
 // the spectrum are copied while the current tile runs its inverse step 1.  The
 // twiddle table is staged once.  The compute phases then touch only registers and
-// shared memory.
+// shared memory.  Each tile's host record is read into registers before the tile ahead
+// of it runs its forward step 1, so its latency is hidden there.
 // Shared memory: transpose buffer (16 x line2_pitch), staging buffer (16 x ni),
-// spectrum lines (4 x Oz), twiddles (L).
+// spectrum lines (4 x Oz), twiddles (A x B).
 // NL = 8 (long lines): a CTA takes half a tile of the host's list (2 mirror groups of
 // 4 lines and their 2 octant lines), so the buffers fit in shared memory at L >= 1024.
 // The staging pitch that holds rows a < conv_rows_in(A) of a line (odd: lanes = lines).
@@ -356,66 +357,86 @@ __global__ void __launch_bounds__(kThreads2)
   __shared__ const LineSweep* plan_of[2];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-  // plan and local tile index of global tile t
-  auto resolve = [&](long long t, long long& local) -> const LineSweep* {
+  // The 20-int host record of a tile, read into registers one phase before it is used,
+  // so that the load latency hides behind the previous tile's forward step 1.
+  struct Rec {
+    const LineSweep* q;       // plan of the tile
+    long long line[NL / 8];   // the lines this warp stages: b = warp, warp + 8
+    long long my_line;        // line slot threadIdx.x (< NL)
+    int my_oct;               // octant id slot threadIdx.x (< NG)
+    int spec_oct;             // the octant line this warp stages: g = warp % NG
+  };
+  auto read_rec = [&](long long t) {
+    Rec r;
+    long long lt = t;
+    r.q = &p;
     if constexpr (BATCH) {
       const int i = batch_owner(bp, (int)t);
-      local = t - bp.offsets[i];
-      return &bp.item[i];
-    } else {
-      local = t;
-      return &p;
+      lt = t - bp.offsets[i];
+      r.q = &bp.item[i];
     }
+    const int* tiles = BATCH ? r.q->tiles : p.tiles;
+    // line slots and octant ids of local tile lt in the host's 20-int tile records
+    const long long lb = NL == 16 ? 20LL * lt : 20LL * (lt >> 1) + 8 * (lt & 1);
+    const long long ob = NL == 16 ? 20LL * lt + 16 : 20LL * (lt >> 1) + 16 + 2 * (lt & 1);
+#pragma unroll
+    for (int h = 0; h < NL / 8; ++h) r.line[h] = tiles[lb + warp + 8 * h];
+    r.my_line = threadIdx.x < NL ? tiles[lb + threadIdx.x] : -1;
+    r.my_oct = threadIdx.x < NG ? tiles[ob + threadIdx.x] : -1;
+    r.spec_oct = tiles[ob + warp % NG];
+    return r;
   };
-  // line slots and octant ids of local tile lt in the host's 20-int tile records
-  auto line_base = [&](long long lt) -> long long {
-    return NL == 16 ? 20LL * lt : 20LL * (lt >> 1) + 8 * (lt & 1);
-  };
-  auto oct_base = [&](long long lt) -> long long {
-    return NL == 16 ? 20LL * lt + 16 : 20LL * (lt >> 1) + 16 + 2 * (lt & 1);
-  };
-  auto fetch_lines = [&](long long t, int slot) {
-    long long lt = 0;
-    const LineSweep* q = resolve(t, lt);
-    const int* tiles = q->tiles;
-    const float2* data = q->data;
-    const long long ld = q->ld;
-    const int n_in = q->n_in;
-    const long long lb = line_base(lt), ob = oct_base(lt);
-    for (int b = warp; b < NL; b += kThreads2 / 32) {
-      const long long l = tiles[lb + b];
+  auto fetch_lines = [&](const Rec& r, int slot) {
+    const LineSweep& q = BATCH ? *r.q : p;
+    const float2* data = q.data;
+    const long long ld = q.ld;
+    const int n_in = q.n_in;
+#pragma unroll
+    for (int h = 0; h < NL / 8; ++h) {
+      const int b = warp + 8 * h;
+      const long long l = r.line[h];
       const float2* src = data + (l < 0 ? 0 : l * ld);
       for (int n = lane; n < NI; n += 32) cp_async8(&I[b * NI + n], &src[n < n_in ? n : 0], l >= 0 && n < n_in);
     }
-    if (threadIdx.x < NL) line_of[slot][threadIdx.x] = tiles[lb + threadIdx.x];
-    if (threadIdx.x < NG) oct_of[slot][threadIdx.x] = tiles[ob + threadIdx.x];
-    if (threadIdx.x == 0) plan_of[slot] = q;
+    if (threadIdx.x < NL) line_of[slot][threadIdx.x] = r.my_line;
+    if (threadIdx.x < NG) oct_of[slot][threadIdx.x] = r.my_oct;
+    if (threadIdx.x == 0) plan_of[slot] = r.q;
   };
-  auto fetch_spectrum = [&](long long t) {
-    long long lt = 0;
-    const LineSweep* q = resolve(t, lt);
+  auto fetch_spectrum = [&](const Rec& r) {
+    const float2* khat = BATCH ? r.q->khat : p.khat;
     const int g = warp % NG;
-    const int oc = q->tiles[oct_base(lt) + g];
-    const float2* kl = q->khat + (oc < 0 ? 0 : (long long)oc * Oz);
+    const int oc = r.spec_oct;
+    const float2* kl = khat + (oc < 0 ? 0 : (long long)oc * Oz);
     for (int i = (warp / NG) * 32 + lane; i < Oz; i += (kThreads2 / 32 / NG) * 32)
       cp_async8(&K[g * Oz + i], &kl[i], oc >= 0);
   };
+  static_assert(NL == 8 || NL == 16, "tiles of 8 or 16 lines, 8 warps");
 
-  for (int i = threadIdx.x; i < L; i += blockDim.x) cp_async8(&T[i], &p.ax.tw[i], true);
+  // inter-step twiddles laid out as T[k1 B + b] = w_L^(b k1): with either index fixed
+  // at compile time, every read is a register base plus a constant offset.  (A padded
+  // row pitch would spare step 2 a two-way bank conflict, but costs the kernel 26
+  // registers a thread and so its second CTA per SM.)
+  for (int i = threadIdx.x; i < L; i += blockDim.x) cp_async8(&T[i], &p.ax.tw[(i % B) * (i / B)], true);
   long long t = blockIdx.x;
   if (t < ntiles) {
-    fetch_lines(t, 0);
-    fetch_spectrum(t);
+    const Rec r0 = read_rec(t);
+    fetch_lines(r0, 0);
+    fetch_spectrum(r0);
   }
   asm volatile("cp.async.commit_group;\n" ::: "memory");
   for (int it = 0; t < ntiles; t += gridDim.x, ++it) {
     const int cur = it & 1;
+    const long long tn = t + gridDim.x;
+    // (the batched form reads the record where it is used: holding it over step 2
+    // would cost it its second CTA per SM)
+    Rec nrec{};
+    if (!BATCH && tn < ntiles) nrec = read_rec(tn);
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
-    const LineSweep* q = plan_of[cur];
-    const int n_out = q->n_out;
-    float2* const data = q->data;
-    const long long ld = q->ld;
+    const LineSweep& q = BATCH ? *plan_of[cur] : p;
+    const int n_out = q.n_out;
+    float2* const data = q.data;
+    const long long ld = q.ld;
     // forward step 1 from the staging buffer; the 16 lanes of a half-warp hold the 16
     // lines (odd staging pitch), so every twiddle read is a broadcast.  The line is
     // zero from n_in <= L / 2 on: only rows a < AH are read (the staging buffer holds
@@ -429,13 +450,14 @@ __global__ void __launch_bounds__(kThreads2)
       for (int a = 0; a < AH; ++a) v[a] = src[B * a + b];
       dft_reg_nz<A, false, AH>(v);
       float2* s = S + line * LP + b;
+      const float2* tw = T + b;
       s[0] = v[0];
 #pragma unroll
-      for (int k1 = 1; k1 < A; ++k1) s[k1 * BP] = cmul(v[k1], T[b * k1]);
+      for (int k1 = 1; k1 < A; ++k1) s[k1 * BP] = cmul(v[k1], tw[k1 * B]);
     }
     __syncthreads();
-    const long long tn = t + gridDim.x;
-    if (tn < ntiles) fetch_lines(tn, cur ^ 1);
+    if (BATCH && tn < ntiles) nrec = read_rec(tn);
+    if (tn < ntiles) fetch_lines(nrec, cur ^ 1);
     asm volatile("cp.async.commit_group;\n" ::: "memory");
     // forward step 2, spectrum multiply, inverse step 2 (lanes = lines again)
     for (int tau = threadIdx.x; tau < NL * A; tau += blockDim.x) {
@@ -455,12 +477,14 @@ __global__ void __launch_bounds__(kThreads2)
         for (int k2 = 0; k2 < B; ++k2) z[k2] = cmul(z[k2], 2 * k2 < B ? lo[A * k2] : hi[-A * k2]);
       }
       dft_reg<B, true>(z);
+      const float2* tw = T + k1 * B;
       s[0] = z[0];
 #pragma unroll
-      for (int b = 1; b < B; ++b) s[b] = cmulc(z[b], T[b * k1]);
+      for (int b = 1; b < B; ++b) s[b] = cmulc(z[b], tw[b]);
     }
     __syncthreads();
-    if (tn < ntiles) fetch_spectrum(tn);
+    if (BATCH && tn < ntiles) nrec = read_rec(tn);
+    if (tn < ntiles) fetch_spectrum(nrec);
     asm volatile("cp.async.commit_group;\n" ::: "memory");
     // inverse step 1 and store
     for (int tau = threadIdx.x; tau < NL * B; tau += blockDim.x) {
