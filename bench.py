@@ -3,8 +3,8 @@
 
 One step = one pass of the hot path over the workload's harmonics, through the
 C ABI: V_{k1}[p1] on the fundamental grid, then for each harmonic n >= 2 the
-restriction of the lower harmonics onto grid n, the fused source assembly and the
-volume potential.  Kernel spectra are built before timing (cached per plan, timed
+restriction of the lower harmonics onto grid n fused with the source products (one
+kernel), and the volume potential.  Kernel spectra are built before timing (cached per plan, timed
 separately); the incident field p1 is an input and is generated before timing.
 
 Default workload: harmonics 1-3 on nested 128^3 / 192^3 / 256^3 focal grids of a
@@ -194,14 +194,14 @@ def stored_traffic(kernel: str):
     return None
 
 
-def kernel_name(sweep: int, m, engine) -> str:
+def kernel_name(sweep: int, m, engine, fused_source: bool = True) -> str:
     """Name of the CUDA kernel that runs one sweep (two-level or radix-pass engine)."""
     axis = (0, 1, 2, 1, 0)[sweep]
     L = m[axis]
     if engine[axis]:
         if sweep == 2:
             return f"line2_conv_pipe_kernel (L={L})"
-        kind = ("forward, source" if sweep == 0 else "forward") if sweep < 2 else "inverse"
+        kind = ("forward, source" if sweep == 0 and fused_source else "forward") if sweep < 2 else "inverse"
         return f"col2_kernel {kind} (L={L})"
     if sweep == 2:
         return f"line_sweep_kernel<conv> (L={L})"
@@ -239,14 +239,15 @@ class GpuWorkload:
             self.plans[1] = vp.vp_plan(w.v1_grid, 1, w.bowl.f0, w.medium)
             self.outs[1] = torch.empty(w.v1_grid.n, dtype=c64, device=device)
         home = {1: w.p1_grid}
-        self.restrict_bufs = {}
+        # harmonics whose lower fields live on other grids: restriction and products in
+        # one kernel (vp_source_from_nested); the others fuse the products into the
+        # first sweep (vp_source_assemble)
+        self.nested = {}
         for st in w.steps:
             n = st.harmonic
             self.plans[n] = vp.vp_plan(st.grid, n, w.bowl.f0, w.medium)
             self.outs[n] = torch.empty(st.grid.n, dtype=c64, device=device)
-            for m in range(1, n):
-                if home[m] is not st.grid:
-                    self.restrict_bufs[(n, m)] = torch.empty(st.grid.n, dtype=c64, device=device)
+            self.nested[n] = any(home[m] is not st.grid for m in range(1, n))
             home[n] = st.grid
         self.grids = {st.harmonic: st.grid for st in w.steps}
         if w.v1_grid is not None:
@@ -263,8 +264,7 @@ class GpuWorkload:
         if 1 in self.plans and self.p1_v1 is not None:
             n += 5
         for st in self.w.steps:
-            n += 5
-        n += len(self.restrict_bufs)
+            n += 5 + (1 if self.nested[st.harmonic] else 0)
         return n
 
     def step(self, p1=None, p1_v1=None):
@@ -277,19 +277,46 @@ class GpuWorkload:
         fields = {1: (p1, w.p1_grid)}
         for st in w.steps:
             n = st.harmonic
-            lower = []
-            for m in range(1, n):
-                f, g = fields[m]
-                if g is st.grid:
-                    lower.append(f)
-                else:
-                    buf = self.restrict_bufs[(n, m)]
-                    vp.vp_restrict_to_nested_box(g, f, st.grid, buf)
-                    lower.append(buf)
             plan = self.plans[n]
-            plan.source_assemble(lower)
+            if self.nested[n]:
+                plan.source_from_nested([fields[m][1] for m in range(1, n)], [fields[m][0] for m in range(1, n)])
+            else:
+                plan.source_assemble([fields[m][0] for m in range(1, n)])
             plan.apply(None, self.outs[n])
             fields[n] = (self.outs[n], st.grid)
+
+    def time_nested_sources(self, flush, reps: int = 20):
+        """CUDA-event time of each nested-source kernel (restriction of every lower field
+        and the products, one launch) with its algorithmic bytes: the lower fields read
+        once, the source written once.  Outside the timed step; L2 flushed before each."""
+        import numpy as np
+        import torch
+        out = []
+        fields = {1: (self.p1, self.w.p1_grid)}
+        for st in self.w.steps:
+            n = st.harmonic
+            if self.nested[n]:
+                plan = self.plans[n]
+                grids = [fields[m][1] for m in range(1, n)]
+                lower = [fields[m][0] for m in range(1, n)]
+                f = torch.empty(st.grid.n, dtype=torch.complex64, device=self.p1.device)
+                ms = 0.0
+                for _ in range(reps):
+                    flush.zero_()
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record()
+                    plan.source_from_nested(grids, lower, f_out=f)
+                    b.record()
+                    torch.cuda.synchronize()
+                    ms += a.elapsed_time(b)
+                ms /= reps
+                by = 8 * (sum(int(np.prod(g.n)) for g in grids) + int(np.prod(st.grid.n)))
+                out.append({"harmonic": n, "kernel": "source_nested_tiled_kernel",
+                            "sources": [list(g.n) for g in grids], "n": list(st.grid.n),
+                            "ms_per_launch": round(ms, 5), "bytes_per_launch": by,
+                            "gbs": round(by / (ms * 1e-3) / 1e9, 1)})
+            fields[n] = (self.outs[n], st.grid)
+        return out
 
     def plan_geometry(self):
         out = {}
@@ -346,13 +373,14 @@ def run_ours(args, world, rank, local):
         p.profile_enable(False)
         ms, cnt = p.profile_read(reset=True)
         nn, mm, eng = geo[n]
-        fused = n >= 2
+        fused = n >= 2 and not gw.nested.get(n, False)
         by = sweep_bytes(nn, mm, n, fused)
         for s in range(5):
             if cnt[s] == 0:
                 continue
             per_launch_ms = ms[s] / cnt[s]
-            sweeps.append({"harmonic": n, "sweep": SWEEP_NAMES[s], "kernel": kernel_name(s, mm, eng),
+            name = SWEEP_NAMES[s] if s or fused else "x_forward"
+            sweeps.append({"harmonic": n, "sweep": name, "kernel": kernel_name(s, mm, eng, fused),
                            "n": list(nn), "m": list(mm),
                            "launches": cnt[s], "ms_per_launch": per_launch_ms, "bytes_per_launch": by[s],
                            "gbs": by[s] / (per_launch_ms * 1e-3) / 1e9, "total_ms": ms[s]})
@@ -381,6 +409,8 @@ def run_ours(args, world, rank, local):
         per_h[str(n)] = {"voxels": vox, "apply_ms": round(t, 4), "voxels_per_s": vox / (t * 1e-3),
                          "model_gbs": round(by / (t * 1e-3) / 1e9, 1), "hbm_frac": round(by / (t * 1e-3) / 1e9 / hbm_peak, 4)}
 
+    nested_sources = gw.time_nested_sources(flush)
+
     e2e = None
     if not args.no_e2e:
         e2e = measure_e2e(gw, args, world, voxels, flush)
@@ -404,7 +434,7 @@ def run_ours(args, world, rank, local):
                    "voxels_per_step": voxels, "bowl_points": w.n_points, "parallelism": f"replicas x{world}",
                    "l2": "flushed between steps (256 MiB write outside the timed events)",
                    "khat_build_ms": round(gw.khat_build_ms, 2), "incident_field": gw.incident},
-        "roofline": roofline, "per_harmonic": per_h, "sweeps": sweeps,
+        "roofline": roofline, "per_harmonic": per_h, "sweeps": sweeps, "nested_sources": nested_sources,
         "e2e": e2e, "cpu_baseline": cpu, "cufft_comparison": cufft, "clocks": clk,
         "gpu_launches": gw.launches_per_step() * args.steps, "wall_s_timed": round(t_wall, 4),
     }
@@ -623,16 +653,17 @@ def run_batch(args, world, rank, local):
         for p in it["plans"]:
             p.kernel_fft()
         it["u"] = [torch.empty(g.n, dtype=c64, device=dev) for g in (g1, g2, g3)]
-        it["r"] = [torch.empty(g3.n, dtype=c64, device=dev) for _ in range(2)]
+        it["f3"] = torch.empty(g3.n, dtype=c64, device=dev)
         items.append(it)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
 
-    def restrict_all():
+    # harmonic 3's source from p1 and p2 on grid 2: restriction and products in one
+    # kernel per instance (vp_source_from_nested), in both forms
+    def nested_all():
         for it in items:
             g1, g2, g3 = it["grids"]
-            vp.vp_restrict_to_nested_box(g2, it["p1_g2"], g3, it["r"][0])
-            vp.vp_restrict_to_nested_box(g2, it["u"][1], g3, it["r"][1])
+            it["plans"][2].source_from_nested([g2, g2], [it["p1_g2"], it["u"][1]], f_out=it["f3"])
 
     def plain_step():
         for it in items:
@@ -641,21 +672,18 @@ def run_batch(args, world, rank, local):
             p1.apply(it["p1_g1"], it["u"][0])
             p2.source_assemble([it["p1_g2"]])
             p2.apply(None, it["u"][1])
-            vp.vp_restrict_to_nested_box(g2, it["p1_g2"], g3, it["r"][0])
-            vp.vp_restrict_to_nested_box(g2, it["u"][1], g3, it["r"][1])
-            p3.source_assemble([it["r"][0], it["r"][1]])
+            p3.source_from_nested([g2, g2], [it["p1_g2"], it["u"][1]])
             p3.apply(None, it["u"][2])
 
     b1 = vp.Batch([it["plans"][0] for it in items], [it["u"][0] for it in items], fs=[it["p1_g1"] for it in items])
     b2 = vp.Batch([it["plans"][1] for it in items], [it["u"][1] for it in items],
                   lowers=[[it["p1_g2"]] for it in items])
-    b3 = vp.Batch([it["plans"][2] for it in items], [it["u"][2] for it in items],
-                  lowers=[[it["r"][0], it["r"][1]] for it in items])
+    b3 = vp.Batch([it["plans"][2] for it in items], [it["u"][2] for it in items], fs=[it["f3"] for it in items])
 
     def batched_step():
         b1.run()
         b2.run()
-        restrict_all()
+        nested_all()
         b3.run()
 
     def timeit(fn, reps):

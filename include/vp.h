@@ -177,6 +177,25 @@ VP_API int vp_kernel_spectrum_set(vp_plan_t p, const void* src_device, vp_stream
 VP_API int vp_source_assemble(vp_plan_t p, const void* const* lower, int n_lower, int flags,
                               void* f_out, vp_stream_t stream);
 
+/* ---- source assembly from lower harmonics on their own nested grids -----------------
+ * The source f_n of vp_source_assemble (Eq. 2.6) when p_m lives on a grid of its own
+ * (Section 6, steps 2a-2b): lower[m-1] is p_m on grids[m-1] (device pointer,
+ * grids[m-1].n voxels), for m = 1..n-1, n_lower = n - 1.  One kernel restricts every p_m
+ * to the plan's grid (the interpolation of vp_restrict_to_nested_box: linear, or
+ * quadratic with flags & VP_RESTRICT_QUADRATIC) and forms f_n from the restricted values
+ * there; the restricted fields are never stored.  Same result as
+ * vp_restrict_to_nested_box of each p_m followed by vp_source_assemble (up to the order
+ * of the FP32 sums).  Every plan voxel centre must lie within each source box, as for
+ * vp_restrict_to_nested_box without VP_RESTRICT_ZERO_OUTSIDE.
+ * f_out != NULL: write f_n (N voxels, complex64) there.
+ * f_out == NULL: stage f_n for the next vp_apply(p, NULL, u, ...) on the same stream
+ *   (its first FFT sweep runs here, from the plan's workspace).
+ * Errors: VP_ERR_ARG (null plan, array or field pointer, n_lower != n - 1, n < 2, a bad
+ * grid, unknown flags), VP_ERR_NOT_NESTED, VP_ERR_UNSUPPORTED (plan grid with more than
+ * 65535 voxels along x or y), VP_ERR_CUDA. */
+VP_API int vp_source_from_nested(vp_plan_t p, const vp_grid* grids, const void* const* lower, int n_lower,
+                                 int flags, void* f_out, vp_stream_t stream);
+
 /* ---- volume potential ----------------------------------------------------------
  * u = V_{k_n}[f] (Eq. 3.9 via the circulant embedding of Section 3.1): zero pad f to
  * M, forward 3-D FFT, multiply by the kernel spectrum, inverse FFT, crop to N.

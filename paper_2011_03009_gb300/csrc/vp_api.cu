@@ -854,11 +854,10 @@ VP_API int vp_apply(vp_plan_t p, const void* f, void* u, vp_stream_t stream) {
   return VP_OK;
 }
 
-VP_API int vp_restrict_to_nested_box(const vp_grid* src, const void* src_field, const vp_grid* dst,
-                                     void* dst_field, int flags, vp_stream_t stream) {
-  if (!grid_ok(src) || !grid_ok(dst) || !src_field || !dst_field) return VP_ERR_ARG;
-  if (flags & ~(VP_RESTRICT_ZERO_OUTSIDE | VP_RESTRICT_QUADRATIC)) return VP_ERR_ARG;
-  double a[3], b[3];
+namespace {
+// Axis maps t = a + i b (target index i -> source-voxel units) of a restriction from grid
+// src onto grid dst, with the range and nesting checks of vp_restrict_to_nested_box.
+int restrict_axes(const vp_grid* src, const vp_grid* dst, bool zero_outside, double a[3], double b[3]) {
   const double tol = 1e-9;
   for (int ax = 0; ax < 3; ++ax) {
     a[ax] = (dst->origin[ax] - src->origin[ax]) / src->h;
@@ -869,9 +868,51 @@ VP_API int vp_restrict_to_nested_box(const vp_grid* src, const void* src_field, 
     const double t0 = a[ax];
     const double t1 = std::fma((double)(dst->n[ax] - 1), b[ax], a[ax]);
     const double lo = std::min(t0, t1), hi = std::max(t0, t1);
-    if (!(flags & VP_RESTRICT_ZERO_OUTSIDE) && (lo < -tol || hi > (double)(src->n[ax] - 1) + tol))
-      return VP_ERR_NOT_NESTED;
+    if (!zero_outside && (lo < -tol || hi > (double)(src->n[ax] - 1) + tol)) return VP_ERR_NOT_NESTED;
   }
+  return VP_OK;
+}
+}  // namespace
+
+VP_API int vp_source_from_nested(vp_plan_t p, const vp_grid* grids, const void* const* lower, int n_lower,
+                                 int flags, void* f_out, vp_stream_t stream) {
+  if (!p || !grids || !lower || (flags & ~VP_RESTRICT_QUADRATIC)) return VP_ERR_ARG;
+  if (p->harmonic < 2 || n_lower != p->harmonic - 1 || n_lower > vp::kMaxLower) return VP_ERR_ARG;
+  vp_grid dst{};
+  for (int ax = 0; ax < 3; ++ax) {
+    dst.n[ax] = p->n[ax];
+    dst.origin[ax] = p->origin[ax];
+  }
+  dst.h = p->h;
+  vp::NestedSrcDesc d[vp::kMaxLower] = {};
+  for (int i = 0; i < n_lower; ++i) {
+    if (!lower[i] || !grid_ok(&grids[i])) return VP_ERR_ARG;
+    const int st = restrict_axes(&grids[i], &dst, false, d[i].a, d[i].b);
+    if (st != VP_OK) return st;
+    d[i].f = (const float2*)lower[i];
+    for (int ax = 0; ax < 3; ++ax) d[i].n[ax] = grids[i].n[ax];
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  // without f_out the source goes to the plan's second workspace buffer, which the first
+  // sweep reads before the second sweep writes it
+  float2* out = f_out ? (float2*)f_out : p->wsB;
+  cudaError_t e = vp::launch_source_nested(d, n_lower, (flags & VP_RESTRICT_QUADRATIC) ? 2 : 1, (float)p->cn, out,
+                                           p->n, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (f_out) return VP_OK;
+  const int st = run_sweep(p, 0, p->wsB, nullptr, nullptr, s);
+  if (st != VP_OK) return st;
+  p->staged = true;
+  return VP_OK;
+}
+
+VP_API int vp_restrict_to_nested_box(const vp_grid* src, const void* src_field, const vp_grid* dst,
+                                     void* dst_field, int flags, vp_stream_t stream) {
+  if (!grid_ok(src) || !grid_ok(dst) || !src_field || !dst_field) return VP_ERR_ARG;
+  if (flags & ~(VP_RESTRICT_ZERO_OUTSIDE | VP_RESTRICT_QUADRATIC)) return VP_ERR_ARG;
+  double a[3], b[3];
+  const int st = restrict_axes(src, dst, flags & VP_RESTRICT_ZERO_OUTSIDE, a, b);
+  if (st != VP_OK) return st;
   cudaError_t e = vp::launch_restrict((const float2*)src_field, src->n, (float2*)dst_field, dst->n, a, b,
                                       (flags & VP_RESTRICT_QUADRATIC) ? 2 : 1, flags & VP_RESTRICT_ZERO_OUTSIDE,
                                       (cudaStream_t)stream);

@@ -122,6 +122,17 @@ cudaError_t launch_octant_extract(const float2* scr, float2* oct, const int m[3]
                                   cudaStream_t s);
 cudaError_t launch_source_assemble(const float2* const* lower, int harmonic, float cn, float2* out,
                                    long long count, cudaStream_t s);
+// One lower harmonic of a nested source: field f on a grid of n voxels, and the target
+// axis maps t = a + i b in its voxel units (as vp_restrict_to_nested_box forms them).
+struct NestedSrcDesc {
+  const float2* f;
+  int n[3];
+  double a[3], b[3];
+};
+// f_n of harmonic ns + 1 on the nd grid from the ns lower harmonics, each restricted
+// (order 1 linear, 2 quadratic) inside the kernel.
+cudaError_t launch_source_nested(const NestedSrcDesc* d, int ns, int order, float cn, float2* dst, const int nd[3],
+                                 cudaStream_t s);
 cudaError_t launch_restrict(const float2* src, const int ns[3], float2* dst, const int nd[3],
                             const double a[3], const double b[3], int order, int zero_outside,
                             cudaStream_t s);

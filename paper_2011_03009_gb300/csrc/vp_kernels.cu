@@ -3,6 +3,9 @@
 // restriction between nested grids (Section 6) and the incident field (Eq. 3.10).
 #include <math.h>
 
+#include <algorithm>
+#include <cmath>
+
 #include "fft_engine.cuh"
 
 namespace vp {
@@ -196,6 +199,31 @@ __device__ __forceinline__ bool stencil(const AxisFix& m, int i, int& i0, float 
   return inside;
 }
 
+// The tensor-product stencil sum of one target, read from global memory.
+__device__ __forceinline__ float2 gather_stencil(const float2* __restrict__ src, int sny, int snz, int x0, int y0,
+                                                 int z0, const float (&wx)[3], const float (&wy)[3],
+                                                 const float (&wz)[3], int cx, int cy, int cz) {
+  const long long sy = snz, sx = (long long)sny * snz;
+  float2 acc = make_float2(0.f, 0.f);
+  for (int a = 0; a < cx; ++a) {
+    float2 py = make_float2(0.f, 0.f);
+    for (int b = 0; b < cy; ++b) {
+      const float2* row = src + (x0 + a) * sx + (y0 + b) * sy + z0;
+      float2 pz = make_float2(0.f, 0.f);
+      for (int c = 0; c < cz; ++c) {
+        const float2 v = __ldg(row + c);
+        pz.x = fmaf(wz[c], v.x, pz.x);
+        pz.y = fmaf(wz[c], v.y, pz.y);
+      }
+      py.x = fmaf(wy[b], pz.x, py.x);
+      py.y = fmaf(wy[b], pz.y, py.y);
+    }
+    acc.x = fmaf(wx[a], py.x, acc.x);
+    acc.y = fmaf(wx[a], py.y, acc.y);
+  }
+  return acc;
+}
+
 // Direct form: one thread per target, gathers from global memory (any spacing ratio).
 template <int ORD>
 __global__ void __launch_bounds__(128) restrict_kernel(const float2* __restrict__ src, int snx, int sny, int snz,
@@ -215,25 +243,7 @@ __global__ void __launch_bounds__(128) restrict_kernel(const float2* __restrict_
     dst[idx] = make_float2(0.f, 0.f);
     return;
   }
-  const long long sy = snz, sx = (long long)sny * snz;
-  float2 acc = make_float2(0.f, 0.f);
-  for (int a = 0; a < cx; ++a) {
-    float2 py = make_float2(0.f, 0.f);
-    for (int b = 0; b < cy; ++b) {
-      const float2* row = src + (x0 + a) * sx + (y0 + b) * sy + z0;
-      float2 pz = make_float2(0.f, 0.f);
-      for (int c = 0; c < cz; ++c) {
-        const float2 v = __ldg(row + c);
-        pz.x = fmaf(wz[c], v.x, pz.x);
-        pz.y = fmaf(wz[c], v.y, pz.y);
-      }
-      py.x = fmaf(wy[b], pz.x, py.x);
-      py.y = fmaf(wy[b], pz.y, py.y);
-    }
-    acc.x = fmaf(wx[a], py.x, acc.x);
-    acc.y = fmaf(wx[a], py.y, acc.y);
-  }
-  dst[idx] = acc;
+  dst[idx] = gather_stencil(src, sny, snz, x0, y0, z0, wx, wy, wz, cx, cy, cz);
 }
 
 // Shared-memory tiled form: one CTA computes a 1 x 16 x 64 block of targets (four rows
@@ -252,6 +262,95 @@ struct RStencil {
   float w[3];
 };
 
+// Stencils of one 1 x 16 x 64 target block into shared memory: threads 0..63 the z
+// stencils, 64..79 the y stencils, 80 the x stencil (targets past the grid's end reuse
+// the last target's stencil so that the source ranges stay valid).
+template <int ORD>
+__device__ __forceinline__ void block_stencils(const AxisFix& mx, const AxisFix& my, const AxisFix& mz, int ix,
+                                               int iy0, int iz0, int dny, int dnz, RStencil* sx_, RStencil* sy_,
+                                               RStencil* sz_) {
+  const int t = threadIdx.x;
+  RStencil r;
+  if (t < kRtZ) {
+    r.in = stencil<ORD>(mz, min(iz0 + t, dnz - 1), r.i0, r.w, r.cnt);
+    sz_[t] = r;
+  } else if (t < kRtZ + kRtY) {
+    r.in = stencil<ORD>(my, min(iy0 + t - kRtZ, dny - 1), r.i0, r.w, r.cnt);
+    sy_[t - kRtZ] = r;
+  } else if (t == kRtZ + kRtY) {
+    r.in = stencil<ORD>(mx, ix, r.i0, r.w, r.cnt);
+    sx_[0] = r;
+  }
+}
+
+// The source sub-block a target block touches (its x planes, at most FY x FZ source
+// voxels each; the host sizes FY, FZ from the spacing ratio), one warp per source row,
+// lanes along z, copied with cp.async: every copy is in flight at once, the caller
+// commits and waits.  Tile layout: [x plane][y row][z], plane = FY * FZ, pitch = FZ.
+template <int ORD>
+__device__ __forceinline__ void stage_block_async(const float2* __restrict__ src, int sny, int snz,
+                                                  const RStencil* sx_, const RStencil* sy_, const RStencil* sz_,
+                                                  float2* tile, int plane, int pitch) {
+  const int x0 = sx_[0].i0, cx = sx_[0].cnt;
+  const int ys = sy_[0].i0, zs = sz_[0].i0;
+  const int ny_r = min(sy_[kRtY - 1].i0 + sy_[kRtY - 1].cnt - 1, sny - 1) - ys + 1;
+  const int nz_r = min(sz_[kRtZ - 1].i0 + sz_[kRtZ - 1].cnt - 1, snz - 1) - zs + 1;
+  const long long sy = snz, sxs = (long long)sny * snz;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int r = warp; r < cx * ny_r; r += (int)(blockDim.x >> 5)) {
+    const int xi = r >= 2 * ny_r ? 2 : (r >= ny_r ? 1 : 0);
+    const int yy = r - xi * ny_r;
+    const float2* row = src + (x0 + xi) * sxs + (ys + yy) * sy + zs;
+    float2* trow = tile + xi * plane + yy * pitch;
+    for (int zz = lane; zz < nz_r; zz += 32) cp_async8(&trow[zz], &row[zz], true);
+  }
+}
+
+// One target from the staged sub-block; y0, z0 are its stencils' first rows within it.
+template <int ORD>
+__device__ __forceinline__ float2 interp_block(const float2* tile, int plane, int pitch, const RStencil& xst,
+                                               const RStencil& yst, const RStencil& zst, int y0, int z0) {
+  const float wx0 = xst.w[0], wx1 = xst.w[1], wx2 = xst.w[2];
+  const float2* t0 = tile + y0 * pitch + z0;
+  if (ORD == 1 && xst.cnt == 2 && yst.cnt == 2 && zst.cnt == 2) {
+    // interior of a linear restriction: the 2 x 2 x 2 stencil, straight-line
+    const float2* t1 = t0 + plane;
+    const float wz0 = zst.w[0], wz1 = zst.w[1], wy0 = yst.w[0], wy1 = yst.w[1];
+    const float2 a00 = t0[0], a01 = t0[1], a10 = t0[pitch], a11 = t0[pitch + 1];
+    const float2 b00 = t1[0], b01 = t1[1], b10 = t1[pitch], b11 = t1[pitch + 1];
+    float2 p0, p1;
+    p0.x = wy0 * fmaf(wz1, a01.x, wz0 * a00.x) + wy1 * fmaf(wz1, a11.x, wz0 * a10.x);
+    p0.y = wy0 * fmaf(wz1, a01.y, wz0 * a00.y) + wy1 * fmaf(wz1, a11.y, wz0 * a10.y);
+    p1.x = wy0 * fmaf(wz1, b01.x, wz0 * b00.x) + wy1 * fmaf(wz1, b11.x, wz0 * b10.x);
+    p1.y = wy0 * fmaf(wz1, b01.y, wz0 * b00.y) + wy1 * fmaf(wz1, b11.y, wz0 * b10.y);
+    return make_float2(fmaf(wx1, p1.x, wx0 * p0.x), fmaf(wx1, p1.y, wx0 * p0.y));
+  }
+  float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int a = 0; a <= ORD; ++a) {
+    if (a >= xst.cnt) break;
+    float2 py = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int b = 0; b <= ORD; ++b) {
+      if (b >= yst.cnt) break;
+      float2 pz = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int c = 0; c <= ORD; ++c) {
+        if (c >= zst.cnt) break;
+        const float2 v = t0[a * plane + b * pitch + c];
+        pz.x = fmaf(zst.w[c], v.x, pz.x);
+        pz.y = fmaf(zst.w[c], v.y, pz.y);
+      }
+      py.x = fmaf(yst.w[b], pz.x, py.x);
+      py.y = fmaf(yst.w[b], pz.y, py.y);
+    }
+    const float wxa = a == 0 ? wx0 : (a == 1 ? wx1 : wx2);
+    acc.x = fmaf(wxa, py.x, acc.x);
+    acc.y = fmaf(wxa, py.y, acc.y);
+  }
+  return acc;
+}
+
 template <int ORD>
 __global__ void __launch_bounds__(256) restrict_tiled_kernel(const float2* __restrict__ src, int snx, int sny,
                                                              int snz, float2* __restrict__ dst, int dnx, int dny,
@@ -262,45 +361,17 @@ __global__ void __launch_bounds__(256) restrict_tiled_kernel(const float2* __res
   const int ix = blockIdx.z, iy0 = blockIdx.y * kRtY, iz0 = blockIdx.x * kRtZ;
   (void)snx;
   (void)dnx;
-  {
-    // threads 0..63: z stencils; 64..79: y stencils; 80: x stencil (targets past the
-    // grid's end reuse the last target's stencil so that the source ranges stay valid)
-    const int t = threadIdx.x;
-    RStencil r;
-    if (t < kRtZ) {
-      r.in = stencil<ORD>(mz, min(iz0 + t, dnz - 1), r.i0, r.w, r.cnt);
-      sz_[t] = r;
-    } else if (t < kRtZ + kRtY) {
-      r.in = stencil<ORD>(my, min(iy0 + t - kRtZ, dny - 1), r.i0, r.w, r.cnt);
-      sy_[t - kRtZ] = r;
-    } else if (t == kRtZ + kRtY) {
-      r.in = stencil<ORD>(mx, ix, r.i0, r.w, r.cnt);
-      sx_[0] = r;
-    }
-  }
+  block_stencils<ORD>(mx, my, mz, ix, iy0, iz0, dny, dnz, sx_, sy_, sz_);
   __syncthreads();
-  const int x0 = sx_[0].i0, cx = sx_[0].cnt;
-  const int ys = sy_[0].i0, zs = sz_[0].i0;
-  const int ny_r = min(sy_[kRtY - 1].i0 + sy_[kRtY - 1].cnt - 1, sny - 1) - ys + 1;
-  const int nz_r = min(sz_[kRtZ - 1].i0 + sz_[kRtZ - 1].cnt - 1, snz - 1) - zs + 1;  // <= kRsY, kRsZ (host check)
-  const long long sy = snz, sxs = (long long)sny * snz;
-  // one warp per source row, lanes along z (coalesced, no index division)
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int r = warp; r < cx * ny_r; r += (int)(blockDim.x >> 5)) {
-    const int xi = r >= 2 * ny_r ? 2 : (r >= ny_r ? 1 : 0);
-    const int yy = r - xi * ny_r;
-    const float2* row = src + (x0 + xi) * sxs + (ys + yy) * sy + zs;
-    for (int zz = lane; zz < nz_r; zz += 32) tile[xi][yy][zz] = __ldg(&row[zz]);
-  }
+  stage_block_async<ORD>(src, sny, snz, sx_, sy_, sz_, &tile[0][0][0], kRsY * kRsZ, kRsZ);
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   __syncthreads();
   const int lz = threadIdx.x & (kRtZ - 1);
   const int iz = iz0 + lz;
   if (iz >= dnz) return;
-  const RStencil zst = sz_[lz];
-  const int z0 = zst.i0 - zs;
-  const float wx0 = sx_[0].w[0], wx1 = sx_[0].w[1], wx2 = sx_[0].w[2];
-  const bool inxz = sx_[0].in && zst.in;
-  const bool full2 = cx == 2 && zst.cnt == 2;  // the y count is checked per row
+  const RStencil xst = sx_[0], zst = sz_[lz];
+  const int z0 = zst.i0 - sz_[0].i0;
 #pragma unroll
   for (int k = 0; k < kRowsPerThread; ++k) {
     const int ly = (threadIdx.x / kRtZ) * kRowsPerThread + k;
@@ -308,51 +379,133 @@ __global__ void __launch_bounds__(256) restrict_tiled_kernel(const float2* __res
     if (iy >= dny) break;
     const RStencil yst = sy_[ly];
     const long long idx = ((long long)ix * dny + iy) * dnz + iz;
-    if (!(inxz && yst.in) && zero_outside) {
+    if (!(xst.in && zst.in && yst.in) && zero_outside) {
       dst[idx] = make_float2(0.f, 0.f);
       continue;
     }
-    const int y0 = yst.i0 - ys;
-    if (ORD == 1 && full2 && yst.cnt == 2) {
-      // interior of a linear restriction: the 2 x 2 x 2 stencil, straight-line
-      const float2* t0 = &tile[0][y0][z0];
-      const float2* t1 = &tile[1][y0][z0];
-      const float wz0 = zst.w[0], wz1 = zst.w[1], wy0 = yst.w[0], wy1 = yst.w[1];
-      const float2 a00 = t0[0], a01 = t0[1], a10 = t0[kRsZ], a11 = t0[kRsZ + 1];
-      const float2 b00 = t1[0], b01 = t1[1], b10 = t1[kRsZ], b11 = t1[kRsZ + 1];
-      float2 p0, p1;
-      p0.x = wy0 * fmaf(wz1, a01.x, wz0 * a00.x) + wy1 * fmaf(wz1, a11.x, wz0 * a10.x);
-      p0.y = wy0 * fmaf(wz1, a01.y, wz0 * a00.y) + wy1 * fmaf(wz1, a11.y, wz0 * a10.y);
-      p1.x = wy0 * fmaf(wz1, b01.x, wz0 * b00.x) + wy1 * fmaf(wz1, b11.x, wz0 * b10.x);
-      p1.y = wy0 * fmaf(wz1, b01.y, wz0 * b00.y) + wy1 * fmaf(wz1, b11.y, wz0 * b10.y);
-      dst[idx] = make_float2(fmaf(wx1, p1.x, wx0 * p0.x), fmaf(wx1, p1.y, wx0 * p0.y));
-      continue;
-    }
-    float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int a = 0; a <= ORD; ++a) {
-      if (a >= cx) break;
-      float2 py = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int b = 0; b <= ORD; ++b) {
-        if (b >= yst.cnt) break;
-        float2 pz = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int c = 0; c <= ORD; ++c) {
-          if (c >= zst.cnt) break;
-          const float2 v = tile[a][y0 + b][z0 + c];
-          pz.x = fmaf(zst.w[c], v.x, pz.x);
-          pz.y = fmaf(zst.w[c], v.y, pz.y);
-        }
-        py.x = fmaf(yst.w[b], pz.x, py.x);
-        py.y = fmaf(yst.w[b], pz.y, py.y);
-      }
-      const float wxa = a == 0 ? wx0 : (a == 1 ? wx1 : wx2);
-      acc.x = fmaf(wxa, py.x, acc.x);
-      acc.y = fmaf(wxa, py.y, acc.y);
-    }
-    dst[idx] = acc;
+    dst[idx] = interp_block<ORD>(&tile[0][0][0], kRsY * kRsZ, kRsZ, xst, yst, zst, yst.i0 - sy_[0].i0, z0);
   }
+}
+
+// ---- source on a nested grid: restriction fused with the Eq. 2.6 products -------------
+// Lower harmonic p_m (m = 1..NS) lives on its own grid q.s[m-1]; its value at a target
+// voxel is the restriction above (the same stencils and FP32 operations), and the target
+// gets f_n = C_n sum_{m=1}^{n-1} p_m p_{n-m}, n = NS + 1, summed over the pairs
+// m <= n - m with weight 2 off the diagonal (as the source prologue of the first sweep).
+// The restricted fields are never stored.
+template <int NS>
+struct NestedSrcs {
+  const float2* f[NS];
+  int sny[NS], snz[NS];
+  AxisFix m[NS][3];
+};
+
+template <int NS>
+__device__ __forceinline__ float2 pair_products(const float2 (&r)[NS], float cn) {
+  constexpr int n = NS + 1;
+  float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int m = 1; 2 * m <= n; ++m) {
+    const float w = ((2 * m == n) ? 1.f : 2.f) * cn;
+    const float2 xy = cmul(r[m - 1], r[n - m - 1]);
+    acc.x = fmaf(w, xy.x, acc.x);
+    acc.y = fmaf(w, xy.y, acc.y);
+  }
+  return acc;
+}
+
+// Tiled form (every source's sub-block fits the staging tile).  The stencils of every
+// source are computed first; the sources' sub-blocks are then staged with cp.async into
+// two tiles in turn, the next one in flight while the current one is interpolated.  Each
+// thread keeps its four targets' restricted values of every source in registers.  The
+// tiles are sized to the largest footprint of the sources (FY x FZ per x plane), so that
+// as many CTAs as possible share an SM.
+// Dynamic shared memory: two tiles, then NS x (1 + kRtY + kRtZ) stencils (x, y, z).
+constexpr int kStencilsPerSrc = 1 + kRtY + kRtZ;
+
+template <int ORD>
+size_t nested_tiled_smem(int ns, int fy, int fz) {
+  return 2 * sizeof(float2) * (size_t)(ORD + 1) * fy * fz + sizeof(RStencil) * (size_t)ns * kStencilsPerSrc;
+}
+
+template <int ORD, int NS>
+__global__ void __launch_bounds__(256) source_nested_tiled_kernel(const __grid_constant__ NestedSrcs<NS> q, float cn,
+                                                                  float2* __restrict__ dst, int dny, int dnz, int fy,
+                                                                  int fz) {
+  extern __shared__ float4 smem_raw[];
+  float2* tiles = reinterpret_cast<float2*>(smem_raw);
+  const int plane = fy * fz, tile_size = (ORD + 1) * plane;
+  RStencil* st = reinterpret_cast<RStencil*>(tiles + 2 * tile_size);  // source m: x, y[16], z[64]
+  const int ix = blockIdx.z, iy0 = blockIdx.y * kRtY, iz0 = blockIdx.x * kRtZ;
+  const int lz = threadIdx.x & (kRtZ - 1);
+  // stencils of every source (targets past the grid's end reuse the last target's)
+  for (int i = threadIdx.x; i < NS * kStencilsPerSrc; i += blockDim.x) {
+    const int m = i / kStencilsPerSrc, t = i - m * kStencilsPerSrc;
+    RStencil r;
+    if (t == 0) r.in = stencil<ORD>(q.m[m][0], ix, r.i0, r.w, r.cnt);
+    else if (t <= kRtY) r.in = stencil<ORD>(q.m[m][1], min(iy0 + t - 1, dny - 1), r.i0, r.w, r.cnt);
+    else r.in = stencil<ORD>(q.m[m][2], min(iz0 + t - 1 - kRtY, dnz - 1), r.i0, r.w, r.cnt);
+    st[i] = r;
+  }
+  __syncthreads();
+  auto stage = [&](int m) {
+    const RStencil* s0 = st + m * kStencilsPerSrc;
+    stage_block_async<ORD>(q.f[m], q.sny[m], q.snz[m], s0, s0 + 1, s0 + 1 + kRtY, tiles + (m & 1) * tile_size,
+                           plane, fz);
+  };
+  stage(0);
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  if (NS > 1) stage(1);
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  float2 r[kRowsPerThread][NS];
+#pragma unroll
+  for (int m = 0; m < NS; ++m) {
+    asm volatile("cp.async.wait_group 1;\n" ::: "memory");  // source m's group is complete
+    __syncthreads();
+    const RStencil* s0 = st + m * kStencilsPerSrc;
+    const RStencil xst = s0[0], zst = s0[1 + kRtY + lz];
+    const int z0 = zst.i0 - s0[1 + kRtY].i0;
+    const float2* tile = tiles + (m & 1) * tile_size;
+#pragma unroll
+    for (int k = 0; k < kRowsPerThread; ++k) {
+      const RStencil yst = s0[1 + (threadIdx.x / kRtZ) * kRowsPerThread + k];
+      r[k][m] = interp_block<ORD>(tile, plane, fz, xst, yst, zst, yst.i0 - s0[1].i0, z0);
+    }
+    if (m + 2 < NS) {
+      __syncthreads();  // every thread is done with this tile
+      stage(m + 2);
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  }
+  const int iz = iz0 + lz;
+  if (iz >= dnz) return;
+#pragma unroll
+  for (int k = 0; k < kRowsPerThread; ++k) {
+    const int iy = iy0 + (threadIdx.x / kRtZ) * kRowsPerThread + k;
+    if (iy >= dny) break;
+    dst[((long long)ix * dny + iy) * dnz + iz] = pair_products<NS>(r[k], cn);
+  }
+}
+
+// Direct form (any spacing ratio): one thread per target, gathers from global memory.
+template <int ORD, int NS>
+__global__ void __launch_bounds__(128) source_nested_kernel(const __grid_constant__ NestedSrcs<NS> q, float cn,
+                                                            float2* __restrict__ dst, int dny, int dnz) {
+  const int iz = blockIdx.x * blockDim.x + threadIdx.x;
+  const int iy = blockIdx.y;
+  const int ix = blockIdx.z;
+  if (iz >= dnz) return;
+  float2 r[NS];
+#pragma unroll
+  for (int m = 0; m < NS; ++m) {
+    int x0, y0, z0, cx, cy, cz;
+    float wx[3], wy[3], wz[3];
+    stencil<ORD>(q.m[m][0], ix, x0, wx, cx);
+    stencil<ORD>(q.m[m][1], iy, y0, wy, cy);
+    stencil<ORD>(q.m[m][2], iz, z0, wz, cz);
+    r[m] = gather_stencil(q.f[m], q.sny[m], q.snz[m], x0, y0, z0, wx, wy, wz, cx, cy, cz);
+  }
+  dst[((long long)ix * dny + iy) * dnz + iz] = pair_products<NS>(r, cn);
 }
 
 // Localisation measure of Section 5: Q(x) = log10(|f(x)| / max |f|).  The smallest box
@@ -562,20 +715,93 @@ cudaError_t launch_source_assemble(const float2* const* lower, int harmonic, flo
   return cudaGetLastError();
 }
 
+// t = a + i b in source-voxel units, as fixed point (the host rounding of a and b).
+AxisFix axis_fix(double a, double b, int n) {
+  AxisFix m;
+  m.A = llround(a * (double)(1LL << kFixBits));
+  m.B = llround(b * (double)(1LL << kFixBits));
+  m.n = n;
+  return m;
+}
+
+// Tiled form when the source footprint of a 16 x 64 (y, z) target block fits the staging
+// tile: (16 - 1) b_y + order + 2 <= kRsY and (64 - 1) b_z + order + 2 <= kRsZ source
+// voxels (b = target spacing / source spacing), with a margin for rounding.
+bool block_fits(const double b[3], int order) {
+  const double extra = order + 2.0;
+  return b[1] * (kRtY - 1) + extra <= kRsY && b[2] * (kRtZ - 1) + extra <= kRsZ;
+}
+
+// Source rows one 16 x 64 target block spans along y (z): at most ceil(15 b) (ceil(63 b))
+// stencil starts apart, plus the stencil width and one for rounding.
+int block_footprint(double b, int targets, int order) { return (int)std::ceil((targets - 1) * b) + order + 2; }
+
+template <int ORD, int NS>
+cudaError_t source_nested_launch(const NestedSrcDesc* d, float cn, float2* dst, const int nd[3], bool tiled,
+                                 cudaStream_t s) {
+  NestedSrcs<NS> q{};
+  for (int m = 0; m < NS; ++m) {
+    q.f[m] = d[m].f;
+    q.sny[m] = d[m].n[1];
+    q.snz[m] = d[m].n[2];
+    for (int i = 0; i < 3; ++i) q.m[m][i] = axis_fix(d[m].a[i], d[m].b[i], d[m].n[i]);
+  }
+  if (tiled) {
+    const dim3 grid((unsigned)((nd[2] + kRtZ - 1) / kRtZ), (unsigned)((nd[1] + kRtY - 1) / kRtY), (unsigned)nd[0]);
+    int fy = 1, fz = 1;
+    for (int m = 0; m < NS; ++m) {
+      fy = std::max(fy, std::min(kRsY, block_footprint(d[m].b[1], kRtY, ORD)));
+      fz = std::max(fz, std::min(kRsZ, block_footprint(d[m].b[2], kRtZ, ORD)));
+    }
+    const size_t smem = nested_tiled_smem<ORD>(NS, fy, fz);
+    static volatile bool granted = false;  // the largest size, once; a repeated grant is harmless
+    if (!granted) {
+      const cudaError_t e = cudaFuncSetAttribute(source_nested_tiled_kernel<ORD, NS>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)nested_tiled_smem<ORD>(NS, kRsY, kRsZ));
+      if (e != cudaSuccess) return e;
+      granted = true;
+    }
+    source_nested_tiled_kernel<ORD, NS><<<grid, 256, smem, s>>>(q, cn, dst, nd[1], nd[2], fy, fz);
+  } else {
+    const dim3 grid((unsigned)((nd[2] + 127) / 128), (unsigned)nd[1], (unsigned)nd[0]);
+    source_nested_kernel<ORD, NS><<<grid, 128, 0, s>>>(q, cn, dst, nd[1], nd[2]);
+  }
+  return cudaGetLastError();
+}
+
+template <int ORD>
+cudaError_t source_nested_order(const NestedSrcDesc* d, int ns, float cn, float2* dst, const int nd[3], bool tiled,
+                                cudaStream_t s) {
+  static_assert(kMaxLower == 8, "one instantiation per source count");
+  switch (ns) {
+    case 1: return source_nested_launch<ORD, 1>(d, cn, dst, nd, tiled, s);
+    case 2: return source_nested_launch<ORD, 2>(d, cn, dst, nd, tiled, s);
+    case 3: return source_nested_launch<ORD, 3>(d, cn, dst, nd, tiled, s);
+    case 4: return source_nested_launch<ORD, 4>(d, cn, dst, nd, tiled, s);
+    case 5: return source_nested_launch<ORD, 5>(d, cn, dst, nd, tiled, s);
+    case 6: return source_nested_launch<ORD, 6>(d, cn, dst, nd, tiled, s);
+    case 7: return source_nested_launch<ORD, 7>(d, cn, dst, nd, tiled, s);
+    case 8: return source_nested_launch<ORD, 8>(d, cn, dst, nd, tiled, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_source_nested(const NestedSrcDesc* d, int ns, int order, float cn, float2* dst, const int nd[3],
+                                 cudaStream_t s) {
+  if (nd[1] > 65535 || nd[0] > 65535) return cudaErrorInvalidConfiguration;
+  bool tiled = true;
+  for (int m = 0; m < ns; ++m) tiled = tiled && block_fits(d[m].b, order);
+  return order == 2 ? source_nested_order<2>(d, ns, cn, dst, nd, tiled, s)
+                    : source_nested_order<1>(d, ns, cn, dst, nd, tiled, s);
+}
+
 cudaError_t launch_restrict(const float2* src, const int ns[3], float2* dst, const int nd[3],
                             const double a[3], const double b[3], int order, int zero_outside, cudaStream_t s) {
   if (nd[1] > 65535 || nd[0] > 65535) return cudaErrorInvalidConfiguration;
   AxisFix m[3];
-  for (int i = 0; i < 3; ++i) {
-    m[i].A = llround(a[i] * (double)(1LL << kFixBits));
-    m[i].B = llround(b[i] * (double)(1LL << kFixBits));
-    m[i].n = ns[i];
-  }
-  // tiled form when the source footprint of a 16 x 64 (y, z) target block fits the
-  // staging tile: (16 - 1) b_y + order + 2 <= kRsY and (64 - 1) b_z + order + 2 <= kRsZ
-  // source voxels (b = target spacing / source spacing), with a margin for rounding
-  const double extra = order + 2.0;
-  if (b[1] * (kRtY - 1) + extra <= kRsY && b[2] * (kRtZ - 1) + extra <= kRsZ) {
+  for (int i = 0; i < 3; ++i) m[i] = axis_fix(a[i], b[i], ns[i]);
+  if (block_fits(b, order)) {
     const dim3 grid((unsigned)((nd[2] + kRtZ - 1) / kRtZ), (unsigned)((nd[1] + kRtY - 1) / kRtY), (unsigned)nd[0]);
     if (order == 2)
       restrict_tiled_kernel<2><<<grid, 256, 0, s>>>(src, ns[0], ns[1], ns[2], dst, nd[0], nd[1], nd[2], m[0], m[1],

@@ -239,7 +239,6 @@ class PlainCascade:
         shape = (n, n, n)
         self.f = {h: torch.empty(shape, dtype=c64, device=self.device) for h in range(1, 6)}
         self.p1_box = torch.empty(shape, dtype=c64, device=self.device)
-        self.r = [torch.empty(shape, dtype=c64, device=self.device) for _ in range(4)]
         self.box = {h: torch.empty(shape, dtype=c64, device=self.device) for h in range(2, 6)}
         self.plans = {}   # one plan per harmonic, re-targeted per instance (equal N)
 
@@ -268,14 +267,11 @@ class PlainCascade:
             else:
                 plan.retarget(g[h], h, bowl.f0, self.medium)
             plan.kernel_fft()
-            lower = []
-            for m in range(1, h):
-                if home[m] is g[h]:
-                    lower.append(self.f[m])
-                else:
-                    vp.vp_restrict_to_nested_box(home[m], self.f[m], g[h], self.r[m - 1])
-                    lower.append(self.r[m - 1])
-            plan.source_assemble(lower)
+            if all(home[m] is g[h] for m in range(1, h)):
+                plan.source_assemble([self.f[m] for m in range(1, h)])
+            else:
+                # restriction of the lower fields onto grid h and the products, one kernel
+                plan.source_from_nested([home[m] for m in range(1, h)], [self.f[m] for m in range(1, h)])
             plan.apply(None, self.f[h])
             home[h] = g[h]
         for h in range(2, 6):

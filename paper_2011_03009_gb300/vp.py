@@ -75,6 +75,7 @@ def _load():
         "vp_source_assemble": (I, [P, ctypes.POINTER(P), I, I, P, P]),
         "vp_apply": (I, [P, P, P, P]),
         "vp_restrict_to_nested_box": (I, [ctypes.POINTER(vp_grid), P, ctypes.POINTER(vp_grid), P, I, P]),
+        "vp_source_from_nested": (I, [P, ctypes.POINTER(vp_grid), ctypes.POINTER(P), I, I, P, P]),
         "vp_incident_field": (I, [ctypes.POINTER(vp_grid), P, I, D, D, D, D, ctypes.POINTER(vp_medium), P, P]),
         "vp_status_string": (ctypes.c_char_p, [I]),
         "vp_profile_enable": (I, [P, I]),
@@ -198,6 +199,14 @@ class Plan:
         _check(lib.vp_source_assemble(self._h, arr, len(lower), VP_SRC_CONJ if conj else 0, _ptr(f_out),
                                       _stream(stream)), "vp_source_assemble")
 
+    def source_from_nested(self, grids, lower, f_out=None, quadratic: bool = False, stream=None):
+        """Eq. 2.6 from lower = [p_1 .. p_{n-1}] given on their own grids (grids[m-1] holds
+        p_m): the restriction to this plan's grid and the products in one kernel."""
+        gs = (vp_grid * max(1, len(grids)))(*[g if isinstance(g, vp_grid) else grid_of(g) for g in grids])
+        arr = (ctypes.c_void_p * max(1, len(lower)))(*[_ptr(t).value for t in lower])
+        _check(lib.vp_source_from_nested(self._h, gs, arr, len(lower), VP_RESTRICT_QUADRATIC if quadratic else 0,
+                                         _ptr(f_out), _stream(stream)), "vp_source_from_nested")
+
     def apply(self, f, u, stream=None):
         _check(lib.vp_apply(self._h, _ptr(f), _ptr(u), _stream(stream)), "vp_apply")
 
@@ -280,6 +289,10 @@ def vp_kernel_fft(plan: Plan, stream=None):
 
 def vp_source_assemble(plan: Plan, lower, f_out=None, stream=None):
     plan.source_assemble(lower, f_out, stream)
+
+
+def vp_source_from_nested(plan: Plan, grids, lower, f_out=None, quadratic: bool = False, stream=None):
+    plan.source_from_nested(grids, lower, f_out, quadratic, stream)
 
 
 def vp_apply(plan: Plan, f, u, stream=None):

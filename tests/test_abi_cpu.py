@@ -108,6 +108,7 @@ def test_other_calls_reject_bad_arguments_on_the_host(vp):
     assert vp.lib.vp_vec_dot(4, P(64), None, 1, d2, None) == vp.VP_ERR_ARG
     assert vp.lib.vp_source_assemble(None, None, 1, 1, None, None) == vp.VP_ERR_ARG
     assert vp.lib.vp_source_assemble(None, None, 1, 4, None, None) == vp.VP_ERR_ARG  # unknown flag
+    assert vp.lib.vp_source_from_nested(None, None, None, 2, 0, None, None) == vp.VP_ERR_ARG
     n3 = (ctypes.c_int * 3)(4, 4, 4)
     box = (ctypes.c_int * 6)()
     assert vp.lib.vp_q0_box(n3, None, -1.0, box, None, None) == vp.VP_ERR_ARG
