@@ -320,14 +320,17 @@ __global__ void __launch_bounds__(kThreads2) line2_batch_kernel(const __grid_con
 // shared memory.  Each tile's host record is read into registers before the tile ahead
 // of it runs its forward step 1, so its latency is hidden there.
 // Shared memory: transpose buffer (16 x line2_pitch), staging buffer (16 x ni),
-// spectrum lines (4 x Oz), twiddles (A x B).
+// spectrum lines (4 x Oz), twiddles (A x conv_tw_pitch(B)).
 // NL = 8 (long lines): a CTA takes half a tile of the host's list (2 mirror groups of
 // 4 lines and their 2 octant lines), so the buffers fit in shared memory at L >= 1024.
 // The staging pitch that holds rows a < conv_rows_in(A) of a line (odd: lanes = lines).
 __host__ __device__ constexpr int conv_stage_pitch(int A, int B) { return (B * conv_rows_in(A)) | 1; }
+// Row pitch of the z sweep's twiddle table: 8 elements past B, so that rows k1 and k1 + 1
+// start 16 banks apart.
+__host__ __device__ constexpr int conv_tw_pitch(int B) { return B + 8; }
 __host__ __device__ constexpr size_t conv_pipe_smem(int A, int B, int Oz, int NL = kLines2) {
   return ((size_t)NL * line2_pitch(A, B) + (size_t)NL * conv_stage_pitch(A, B) + (size_t)(NL / 4) * Oz +
-          (size_t)A * B) *
+          (size_t)A * conv_tw_pitch(B)) *
          sizeof(float2);
 }
 
@@ -344,6 +347,7 @@ __global__ void __launch_bounds__(kThreads2)
   constexpr int BP = line2_bpitch(B);
   constexpr int LP = line2_pitch(A, B);
   constexpr int AH = conv_rows_in(A);
+  constexpr int TP = conv_tw_pitch(B);
   static_assert(B % 2 == 0, "the spectrum fold takes an even B");
   extern __shared__ float2 S[];
   const int Oz = p.Oz;  // shared by every plan of a batch group
@@ -412,11 +416,13 @@ __global__ void __launch_bounds__(kThreads2)
   };
   static_assert(NL == 8 || NL == 16, "tiles of 8 or 16 lines, 8 warps");
 
-  // inter-step twiddles laid out as T[k1 B + b] = w_L^(b k1): with either index fixed
-  // at compile time, every read is a register base plus a constant offset.  (A padded
-  // row pitch would spare step 2 a two-way bank conflict, but costs the kernel 26
-  // registers a thread and so its second CTA per SM.)
-  for (int i = threadIdx.x; i < L; i += blockDim.x) cp_async8(&T[i], &p.ax.tw[(i % B) * (i / B)], true);
+  // inter-step twiddles laid out as T[k1 TP + b] = w_L^(b k1), TP = B + 8: with either
+  // index fixed at compile time, every read is a register base plus a constant offset,
+  // and the two k1 rows a warp reads in step 2 fall on different banks
+  for (int i = threadIdx.x; i < A * TP; i += blockDim.x) {
+    const int k1 = i / TP, b = i - k1 * TP;
+    cp_async8(&T[i], &p.ax.tw[b < B ? b * k1 : 0], true);
+  }
   long long t = blockIdx.x;
   if (t < ntiles) {
     const Rec r0 = read_rec(t);
@@ -453,7 +459,7 @@ __global__ void __launch_bounds__(kThreads2)
       const float2* tw = T + b;
       s[0] = v[0];
 #pragma unroll
-      for (int k1 = 1; k1 < A; ++k1) s[k1 * BP] = cmul(v[k1], tw[k1 * B]);
+      for (int k1 = 1; k1 < A; ++k1) s[k1 * BP] = cmul(v[k1], tw[k1 * TP]);
     }
     __syncthreads();
     if (BATCH && tn < ntiles) nrec = read_rec(tn);
@@ -477,7 +483,7 @@ __global__ void __launch_bounds__(kThreads2)
         for (int k2 = 0; k2 < B; ++k2) z[k2] = cmul(z[k2], 2 * k2 < B ? lo[A * k2] : hi[-A * k2]);
       }
       dft_reg<B, true>(z);
-      const float2* tw = T + k1 * B;
+      const float2* tw = T + k1 * TP;
       s[0] = z[0];
 #pragma unroll
       for (int b = 1; b < B; ++b) s[b] = cmulc(z[b], tw[b]);
