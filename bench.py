@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="nested3",
-                    choices=["small", "nested3", "nested5", "batch64", "vie", "fullcascade", "q0"])
+                    choices=["small", "nested3", "nested5", "batch64", "vie", "fullcascade", "q0", "nw"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT comparison timing")
@@ -941,6 +941,42 @@ def run_q0(args):
           {"workload": "q0_study_h3_256cube_nested3", "q0": q0s, "grid": list(g3.n)}, rows=rows, cpu_baseline=cpu)
 
 
+def run_nw(args):
+    """Section 3's mesh refinement: p2 of the H131 transducer in liver on meshes of
+    h = lambda / (2 n_w), n_w = 5..25 (odd), over one box around the focus, against
+    n_w = 35; Deserno-spaced monopoles (4096)."""
+    import numpy as np
+    import torch
+    from paper_2011_03009_gb300 import domain, synth
+    bowl, med = synth.H131, synth.LIVER
+    lam = synth.wavelength(med.c0, bowl.f0, 1)
+    q = (12, 5, 5)  # box: 6 x 2.5 x 2.5 fundamental wavelengths
+    x0 = bowl.l - 4 * lam
+    n_ws = tuple(range(5, 26, 2))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = domain.nw_study(bowl, med, n_ws, 35, q, x0, n_points=4096)
+    sec = time.perf_counter() - t0
+    voxels = sum(int(np.prod(r["grid"])) for r in res["rows"]) + int(np.prod(res["ref_grid"]))
+    cpu = None
+    if not args.no_cpu_baseline:
+        from oracle import cascade, rayleigh
+        # the oracle's p1 and p2 on the n_w = 5 mesh of the same box, from its own call
+        g = domain.nw_grid(bowl, med, 5, q, x0)
+        pts = synth.deserno_cap_points(bowl, 4096)
+        t1 = time.perf_counter()
+        p1 = rayleigh.incident_field(g, pts, bowl, med)
+        cascade.harmonic(2, [p1], g.h, bowl.f0, med)
+        dt = time.perf_counter() - t1
+        cpu = {"value": g.voxels / dt, "unit": "voxels/s (p1 and p2)", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"FP64 oracle p1 (4096 points) and p2 on the n_w = 5 mesh {list(g.n)}, {dt:.2f} s"}
+    _line("mesh-refinement study time", sec, "s", sec * 1e3, 1, 0, False,
+          {"workload": "nw_study_p2_H131_liver", "q_half_wavelengths": list(q), "n_w": list(n_ws), "n_w_ref": 35,
+           "points": res["points"], "voxels": voxels},
+          rows=res["rows"], order=res["order"], order_coarse=res["order_coarse"], ref_grid=res["ref_grid"],
+          ref_ms=res["ref_ms"], cpu_baseline=cpu)
+
+
 def main():
     args = parse()
     world, rank, local = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), \
@@ -951,11 +987,11 @@ def main():
     world, rank, local = dist_init(args)
     if args.workload == "batch64":
         run_batch(args, world, rank, local)
-    elif args.workload in ("vie", "fullcascade", "q0"):
+    elif args.workload in ("vie", "fullcascade", "q0", "nw"):
         import torch
         torch.cuda.set_device(local)
         if rank == 0:
-            {"vie": run_vie, "fullcascade": run_fullcascade, "q0": run_q0}[args.workload](args)
+            {"vie": run_vie, "fullcascade": run_fullcascade, "q0": run_q0, "nw": run_nw}[args.workload](args)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

@@ -38,6 +38,8 @@ class Medium:
 WATER = Medium()
 # soft-tissue-like inclusion for the inhomogeneous-medium equations (Section 7)
 TISSUE = Medium(c0=1540.0, rho0=1000.0, beta=4.5, alpha0=5.0, eta=1.1)
+# liver as listed in Table 2 (alpha0 in dB/m/MHz^eta under the same units reading)
+LIVER = Medium(c0=1590.0, rho0=1060.0, beta=4.4, alpha0=90.0, eta=1.1)
 
 
 @dataclasses.dataclass(frozen=True)
@@ -62,6 +64,12 @@ class Grid:
 
     def axis(self, a: int) -> np.ndarray:
         return self.origin[a] + self.h * np.arange(self.n[a], dtype=np.float64)
+
+
+# Table 1's transducers (f0, focal length l, outer radius R); the surface pressure is
+# this module's choice (the paper prescribes a radiated power instead)
+H101 = Bowl(l=0.0632, R=0.032, f0=1.1e6, p0=1.0e6)
+H131 = Bowl(l=0.035, R=0.0165, f0=1.1e6, p0=1.0e6)
 
 
 def wavelength(c0: float, f0: float, n: int) -> float:
@@ -101,6 +109,37 @@ def sample_bowl_points(bowl: Bowl, n_points: int, seed: int) -> np.ndarray:
     pts[:, 1] = bowl.l * st * np.cos(phi)
     pts[:, 2] = bowl.l * st * np.sin(phi)
     return pts
+
+
+def deserno_cap_points(bowl: Bowl, n_target: int) -> np.ndarray:
+    """About n_target evenly spaced points on the bowl's spherical cap (Section 3 places
+    the monopoles after Deserno's construction for the sphere).
+
+    On the unit sphere each point is to carry the area a = 2 pi (1 - cos theta_max) /
+    n_target, d = sqrt(a).  The polar range [0, theta_max] (seen from the focus,
+    measured from -x) is cut into M_theta = round(theta_max / d) rings of width
+    d_theta = theta_max / M_theta; ring m sits at theta_m = (m + 1/2) d_theta and holds
+    M_phi = round(2 pi sin(theta_m) / d_phi) points at phi = 2 pi k / M_phi, with
+    d_phi = a / d_theta.  Deterministic; returns an (n, 3) float64 array, n close to
+    n_target.
+    """
+    th_max = math.asin(min(1.0, bowl.R / bowl.l))
+    a = 2.0 * math.pi * (1.0 - math.cos(th_max)) / n_target
+    d = math.sqrt(a)
+    m_th = max(1, int(round(th_max / d)))
+    d_th = th_max / m_th
+    d_ph = a / d_th
+    rings = []
+    for m in range(m_th):
+        th = (m + 0.5) * d_th
+        m_ph = max(1, int(round(2.0 * math.pi * math.sin(th) / d_ph)))
+        ph = 2.0 * math.pi * np.arange(m_ph, dtype=np.float64) / m_ph
+        ring = np.empty((m_ph, 3), dtype=np.float64)
+        ring[:, 0] = bowl.l * (1.0 - math.cos(th))
+        ring[:, 1] = bowl.l * math.sin(th) * np.cos(ph)
+        ring[:, 2] = bowl.l * math.sin(th) * np.sin(ph)
+        rings.append(ring)
+    return np.concatenate(rings, axis=0)
 
 
 def random_field(n: Sequence[int], seed: int, scale: float = 1.0) -> np.ndarray:

@@ -272,6 +272,24 @@ def test_incident_field_converges_to_on_axis_closed_form():
     assert errs[-1] < 0.35 * errs[0], errs
 
 
+def test_incident_field_from_evenly_spaced_points_converges_faster():
+    """The Deserno-spaced monopoles of Section 3 make Eq. 3.10 a near-regular quadrature
+    of the Rayleigh integral: 4000 of them are within 1e-2 of the on-axis closed form,
+    which random points reach only with ~100x more, and 8x more points gain > 5x."""
+    bowl = synth.Bowl(l=0.02, R=0.01, f0=1.0e6, p0=0.5e6)
+    k = physics.wavenumber(1, bowl.f0, synth.WATER)
+    zs = [0.6 * bowl.l, 0.9 * bowl.l, bowl.l, 1.15 * bowl.l]
+    xyz = np.array([[z, 0.0, 0.0] for z in zs])
+    ref = np.array([_on_axis_closed_form(bowl, k, z) for z in zs])
+    errs = []
+    for npts in (500, 4000):
+        pts = synth.deserno_cap_points(bowl, npts)
+        got = rayleigh.incident_field_at(xyz, pts, bowl, synth.WATER)
+        errs.append(np.max(np.abs(got - ref) / np.abs(ref)))
+    assert errs[1] < 1e-2, errs
+    assert errs[1] < errs[0] / 5, errs
+
+
 # ----------------------------------------------------------------------------- interpolation
 
 def test_trilinear_restriction_is_exact_on_trilinear_fields_and_identity():
