@@ -754,13 +754,17 @@ cudaError_t source_nested_launch(const NestedSrcDesc* d, float cn, float2* dst, 
       fz = std::max(fz, std::min(kRsZ, block_footprint(d[m].b[2], kRtZ, ORD)));
     }
     const size_t smem = nested_tiled_smem<ORD>(NS, fy, fz);
-    static volatile bool granted = false;  // the largest size, once; a repeated grant is harmless
-    if (!granted) {
-      const cudaError_t e = cudaFuncSetAttribute(source_nested_tiled_kernel<ORD, NS>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)nested_tiled_smem<ORD>(NS, kRsY, kRsZ));
+    // the largest size, once per device; a repeated grant is harmless
+    static volatile int granted[64] = {0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!granted[dev]) {
+      e = cudaFuncSetAttribute(source_nested_tiled_kernel<ORD, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)nested_tiled_smem<ORD>(NS, kRsY, kRsZ));
       if (e != cudaSuccess) return e;
-      granted = true;
+      granted[dev] = 1;
     }
     source_nested_tiled_kernel<ORD, NS><<<grid, 256, smem, s>>>(q, cn, dst, nd[1], nd[2], fy, fz);
   } else {
