@@ -43,3 +43,21 @@ def test_box_grid_and_axis_line():
     assert sub.n == (8, 7, 7)
     assert sub.origin[0] == pytest.approx(0.01 + 3e-4) and sub.origin[1] == pytest.approx(-3e-4)
     assert domain.axis_line(g) == (5, 4)
+
+
+def test_refinement_meshes_cover_one_box():
+    """Every n_w mesh of the refinement study covers the same box, with the x axis on a
+    voxel line (host logic, no GPU)."""
+    domain = _domain()
+    bowl, med = synth.H131, synth.LIVER
+    lam = synth.wavelength(med.c0, bowl.f0, 1)
+    x0 = bowl.l - 2 * lam
+    for n_w in (5, 9, 21, 35):
+        g = domain.nw_grid(bowl, med, n_w, (6, 3, 3), x0)
+        assert g.n == (6 * n_w, 3 * n_w, 3 * n_w)
+        assert math.isclose(g.h, lam / (2 * n_w), rel_tol=1e-15)
+        lo = [g.origin[a] - 0.5 * g.h for a in range(3)]
+        hi = [g.origin[a] + (g.n[a] - 0.5) * g.h for a in range(3)]
+        assert math.isclose(lo[0], x0, abs_tol=1e-12) and math.isclose(hi[0], x0 + 3 * lam, rel_tol=1e-12)
+        assert math.isclose(hi[1], 0.75 * lam, rel_tol=1e-12) and math.isclose(lo[1], -0.75 * lam, rel_tol=1e-12)
+        assert abs(g.origin[1] + (g.n[1] - 1) // 2 * g.h) < 1e-15  # the axis is a voxel line

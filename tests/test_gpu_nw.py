@@ -39,19 +39,6 @@ def test_second_harmonic_on_a_refinement_mesh_matches_oracle(modules):
     assert np.linalg.norm(got2 - ref_p2) / np.linalg.norm(ref_p2) <= 1e-5
 
 
-def test_refinement_meshes_cover_one_box(modules):
-    domain, _ = modules
-    lam = synth.wavelength(MEDIUM.c0, BOWL.f0, 1)
-    x0 = BOWL.l - 2 * lam
-    for n_w in (5, 9, 21):
-        g = domain.nw_grid(BOWL, MEDIUM, n_w, (6, 3, 3), x0)
-        lo = [g.origin[a] - 0.5 * g.h for a in range(3)]
-        hi = [g.origin[a] + (g.n[a] - 0.5) * g.h for a in range(3)]
-        assert math.isclose(lo[0], x0, abs_tol=1e-12) and math.isclose(hi[0], x0 + 3 * lam, rel_tol=1e-12)
-        assert math.isclose(hi[1], 0.75 * lam, rel_tol=1e-12) and math.isclose(lo[1], -0.75 * lam, rel_tol=1e-12)
-        assert abs(g.origin[1] + (g.n[1] - 1) // 2 * g.h) < 1e-15  # the axis is a voxel line
-
-
 def test_second_harmonic_converges_at_second_order(modules):
     domain, _ = modules
     lam = synth.wavelength(MEDIUM.c0, BOWL.f0, 1)
