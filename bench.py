@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="nested3",
-                    choices=["small", "nested3", "nested5", "batch64", "vie", "fullcascade", "q0", "nw"])
+                    choices=["small", "nested3", "nested5", "batch64", "vie", "fullcascade", "q0", "nw", "restrict"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT comparison timing")
@@ -941,6 +941,40 @@ def run_q0(args):
           {"workload": "q0_study_h3_256cube_nested3", "q0": q0s, "grid": list(g3.n)}, rows=rows, cpu_baseline=cpu)
 
 
+def run_restrict(args):
+    """The standalone restriction (Section 6, step 2a) of the default workload: a field on
+    the 192^3 grid of harmonic 2 onto the 256^3 grid of harmonic 3, linear and quadratic;
+    CUDA events, L2 flushed before each launch."""
+    import numpy as np
+    import torch
+    from paper_2011_03009_gb300 import synth, vp
+    wl = synth.WORKLOADS["nested3"]()
+    g2, g3 = wl.steps[0].grid, wl.steps[1].grid
+    f = torch.from_numpy(synth.random_field(g2.n, seed=1).astype(np.complex64)).cuda()
+    out = torch.empty(g3.n, dtype=torch.complex64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    reps = max(3, min(args.steps, 50))
+    rows = {}
+    for quad in (False, True):
+        for _ in range(max(3, args.warmup)):
+            vp.vp_restrict_to_nested_box(g2, f, g3, out, quadratic=quad)
+        ms = 0.0
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            vp.vp_restrict_to_nested_box(g2, f, g3, out, quadratic=quad)
+            b.record()
+            torch.cuda.synchronize()
+            ms += a.elapsed_time(b)
+        ms /= reps
+        by = 8 * (g2.voxels + g3.voxels)
+        rows["quadratic" if quad else "linear"] = {"ms": round(ms, 5), "model_gbs": round(by / (ms * 1e-3) / 1e9, 1)}
+    _line("restricted voxels/s", g3.voxels / (rows["linear"]["ms"] * 1e-3), "voxels/s", rows["linear"]["ms"], reps,
+          max(3, args.warmup), True, {"workload": "restrict_192to256_nested3", "src": list(g2.n), "dst": list(g3.n)},
+          orders=rows)
+
+
 def run_nw(args):
     """Section 3's mesh refinement: p2 of the H131 transducer in liver on meshes of
     h = lambda / (2 n_w), n_w = 5..25 (odd), over one box around the focus, against
@@ -987,11 +1021,12 @@ def main():
     world, rank, local = dist_init(args)
     if args.workload == "batch64":
         run_batch(args, world, rank, local)
-    elif args.workload in ("vie", "fullcascade", "q0", "nw"):
+    elif args.workload in ("vie", "fullcascade", "q0", "nw", "restrict"):
         import torch
         torch.cuda.set_device(local)
         if rank == 0:
-            {"vie": run_vie, "fullcascade": run_fullcascade, "q0": run_q0, "nw": run_nw}[args.workload](args)
+            {"vie": run_vie, "fullcascade": run_fullcascade, "q0": run_q0, "nw": run_nw,
+             "restrict": run_restrict}[args.workload](args)
     else:
         run_ours(args, world, rank, local)
     if world > 1:
