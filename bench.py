@@ -40,7 +40,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="nested3",
-                    choices=["small", "nested3", "nested5", "batch64", "vie", "fullcascade", "q0", "nw", "restrict"])
+                    choices=["small", "nested3", "nested5", "batch64", "vie", "fullcascade", "q0", "nw", "restrict",
+                             "fno"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT comparison timing")
@@ -975,6 +976,29 @@ def run_restrict(args):
           orders=rows)
 
 
+def run_fno(args):
+    """Surrogate inference (4 layers, width 48, projection 128, 32 x 32 x 16 modes) on the
+    128^3 focal box against the plain cascade it would replace (kernel spectra, nested
+    sources and potentials of harmonics 2..5 from p1 on the device); CUDA events.  The
+    inference time does not depend on the weights' values (random initialisation)."""
+    import torch
+    from paper_2011_03009_gb300 import fno as F
+    n = 128
+    cfg = F.FnoConfig(n=n, width=48, hidden=128, layers=4, modes=(32, 32, 16))
+    model = F.Fno(cfg, seed=0)
+    casc = F.PlainCascade(n, 512)
+    bowl = F.draw_bowls(1, 7)[0]
+    casc.incident(bowl, 0)
+    x = torch.view_as_real(casc.p1_box / casc.p1_box.abs().max()).reshape(-1, 2).float().contiguous()
+    y = torch.empty((n ** 3, 8), dtype=torch.float32, device="cuda")
+    reps = max(3, min(args.steps, 20))
+    t_inf = _dev_timeit(lambda: model.infer(x, y), reps, args.warmup)
+    t_plain = _dev_timeit(lambda: casc.harmonics(bowl), reps, args.warmup)
+    _line("surrogate fields/s", 1e3 / t_inf, "fields/s", t_inf, reps, max(1, args.warmup), True,
+          {"workload": "fno_infer_128cube_w48_l4_m32x32x16", "params": model.count},
+          plain_cascade={"fields_per_s": 1e3 / t_plain, "ms": t_plain})
+
+
 def run_nw(args):
     """Section 3's mesh refinement: p2 of the H131 transducer in liver on meshes of
     h = lambda / (2 n_w), n_w = 5..25 (odd), over one box around the focus, against
@@ -1021,12 +1045,12 @@ def main():
     world, rank, local = dist_init(args)
     if args.workload == "batch64":
         run_batch(args, world, rank, local)
-    elif args.workload in ("vie", "fullcascade", "q0", "nw", "restrict"):
+    elif args.workload in ("vie", "fullcascade", "q0", "nw", "restrict", "fno"):
         import torch
         torch.cuda.set_device(local)
         if rank == 0:
             {"vie": run_vie, "fullcascade": run_fullcascade, "q0": run_q0, "nw": run_nw,
-             "restrict": run_restrict}[args.workload](args)
+             "restrict": run_restrict, "fno": run_fno}[args.workload](args)
     else:
         run_ours(args, world, rank, local)
     if world > 1:
