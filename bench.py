@@ -618,6 +618,27 @@ def cpu_baseline(w, gw=None):
         got = ud.cpu().numpy().astype(np.complex128)
         out["rel_l2_vs_oracle"] = {"harmonic": n_h, "grid": list(g.n),
                                    "value": float(np.linalg.norm(got - u_ref) / np.linalg.norm(u_ref))}
+        # every other harmonic of the run at its full size, where the oracle's padded
+        # cube (M^3 complex128) stays within 2 GiB: the plan's apply on a synthetic
+        # smooth source against the oracle's (not timed)
+        from oracle import physics
+        from paper_2011_03009_gb300 import synth
+        per_h = []
+        for st in w.steps:
+            n, gs = st.harmonic, st.grid
+            if np.prod([2 * v for v in gs.n]) > 512 ** 3:
+                continue
+            kn = physics.wavenumber(n, w.bowl.f0, w.medium)
+            fs = synth.smooth_blob_field(gs, (w.bowl.l, 0.0, 0.0), 20 * gs.h, kn.real)
+            ref = potential.apply_fft(fs, gs.h, kn)
+            fd = torch.from_numpy(np.ascontiguousarray(fs).astype(np.complex64)).to(gw.dev)
+            ud = torch.empty_like(fd)
+            gw.plans[n].apply(fd, ud)
+            got = ud.cpu().numpy().astype(np.complex128)
+            per_h.append({"harmonic": n, "grid": list(gs.n),
+                          "value": float(np.linalg.norm(got - ref) / np.linalg.norm(ref))})
+        if per_h:
+            out["rel_l2_vs_oracle_per_harmonic"] = per_h
     return out
 
 
