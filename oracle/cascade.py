@@ -36,13 +36,18 @@ def harmonic(n: int, lower: Sequence[np.ndarray], h: float, f0: float, medium,
     return potential.apply_fft(f, h, physics.wavenumber(n, f0, medium), m)
 
 
-def nested_run(p1_on_first: np.ndarray, grids: Dict[int, object], f0: float, medium) -> Dict[int, np.ndarray]:
+def nested_run(p1_on_first: np.ndarray, grids: Dict[int, object], f0: float, medium,
+               restrict=None) -> Dict[int, np.ndarray]:
     """Section 6 loop for harmonics 2..max(grids).
 
     ``grids[n]`` is the grid of harmonic n (objects with .n, .origin, .h);
     ``p1_on_first`` is p1 evaluated on grids[2].  Every p_m with m >= 2 lives on
-    grids[m]; p1 lives on grids[2].  Returns {n: p_n on grids[n]}.
+    grids[m]; p1 lives on grids[2].  ``restrict`` is the inter-mesh interpolation
+    (default: trilinear, as Section 6 uses; interp.restrict_quadratic is the higher-order
+    option it recommends).  Returns {n: p_n on grids[n]}.
     """
+    if restrict is None:
+        restrict = interp.restrict_trilinear
     fields = {1: p1_on_first}
     home = {1: grids[2]}
     for n in sorted(grids):
@@ -55,7 +60,7 @@ def nested_run(p1_on_first: np.ndarray, grids: Dict[int, object], f0: float, med
             if src_grid is g:
                 lower.append(fields[m])
             else:
-                lower.append(interp.restrict_trilinear(fields[m], src_grid, g))
+                lower.append(restrict(fields[m], src_grid, g))
         fields[n] = harmonic(n, lower, g.h, f0, medium)
         home[n] = g
     return {n: v for n, v in fields.items() if n >= 2}

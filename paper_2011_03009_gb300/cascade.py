@@ -1,5 +1,9 @@
-"""Full harmonic cascade with conjugate terms (Eq. 2.5) by fixed-point iteration, on one
-grid, through the C ABI (include/vp.h).
+"""Harmonic cascades through the C ABI (include/vp.h).
+
+NestedCascade: the weakly nonlinear cascade of Section 6 on nested per-harmonic grids.
+
+FullCascade: the full harmonic cascade with conjugate terms (Eq. 2.5) by fixed-point
+iteration, on one grid.
 
 The weakly nonlinear cascade (Eq. 2.6) keeps only the products p_m p_{n-m}, m < n;
 Eq. 2.5 also keeps 2 p_m conj(p_{m-n}) for m > n, so every harmonic, the fundamental
@@ -10,11 +14,52 @@ started from the weakly nonlinear solution.  Every step runs in libvp.so's kerne
 """
 from __future__ import annotations
 
-from typing import List
+from typing import Dict, List
 
 import torch
 
 from . import vp
+
+
+class NestedCascade:
+    """Section 6's loop: p1 on the grid of harmonic 2, then for n = 2..N each p_n on its
+    own grid from the source of the lower harmonics (Eq. 2.6), every p_m restricted from
+    its grid to grid n inside the source kernel (vp_source_from_nested) where it lives
+    elsewhere, and the volume potential (vp_apply).
+
+    grids: {n: grid of harmonic n} for n = 2..N.  One plan per harmonic, its kernel
+    spectrum built once; run() reuses them for any p1 on grids[2]."""
+
+    def __init__(self, grids: Dict[int, object], f0: float, medium, quadratic: bool = False, device="cuda"):
+        self.grids = {int(n): g for n, g in grids.items()}
+        if not self.grids or min(self.grids) != 2 or sorted(self.grids) != list(range(2, max(self.grids) + 1)):
+            raise ValueError("grids must hold harmonics 2..N")
+        self.quadratic = quadratic
+        self.plans = {n: vp.vp_plan(g, n, f0, medium) for n, g in self.grids.items()}
+        for p in self.plans.values():
+            p.kernel_fft()
+        self.out = {n: torch.empty(tuple(int(v) for v in g.n), dtype=torch.complex64, device=device)
+                    for n, g in self.grids.items()}
+
+    def run(self, p1: torch.Tensor, stream=None) -> Dict[int, torch.Tensor]:
+        """p_n on grids[n] for n = 2..N from p1 on grids[2] (the returned tensors are the
+        cascade's own buffers, overwritten by the next run)."""
+        fields = {1: (p1, self.grids[2])}
+        for n in sorted(self.grids):
+            g, plan = self.grids[n], self.plans[n]
+            lower = [fields[m] for m in range(1, n)]
+            if all(h is g for _, h in lower):  # all on grid n: no restriction
+                plan.source_assemble([f for f, _ in lower], stream=stream)
+            else:
+                plan.source_from_nested([h for _, h in lower], [f for f, _ in lower], quadratic=self.quadratic,
+                                        stream=stream)
+            plan.apply(None, self.out[n], stream=stream)
+            fields[n] = (self.out[n], g)
+        return self.out
+
+    def close(self):
+        for p in self.plans.values():
+            p.close()
 
 
 class FullCascade:
