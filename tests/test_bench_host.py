@@ -23,7 +23,38 @@ def test_kernel_names_follow_the_engine():
     assert bench.kernel_name(2, (512, 512, 512), (1, 1, 1)).startswith("line2_conv_pipe_kernel")
     assert bench.kernel_name(2, (200, 200, 200), (0, 0, 0)).startswith("line_sweep_kernel")
     assert "source" in bench.kernel_name(0, (512, 512, 512), (1, 1, 1))
+    # after a nested source the first sweep reads f: the plain forward sweep
+    assert "source" not in bench.kernel_name(0, (512, 512, 512), (1, 1, 1), fused_source=False)
     assert bench.kernel_name(3, (200, 512, 200), (0, 1, 0)).startswith("col2_kernel inverse")
+
+
+def test_nested_source_bytes_read_one_field():
+    """With the source formed by the nested-source kernel the first sweep reads f once."""
+    N = 64
+    fused = bench.sweep_bytes((N, N, N), (2 * N, 2 * N, 2 * N), 3, fused_source=True)
+    plain = bench.sweep_bytes((N, N, N), (2 * N, 2 * N, 2 * N), 3, fused_source=False)
+    assert fused[0] - plain[0] == 8 * N ** 3 and fused[1:] == plain[1:]
+
+
+def test_reference_arm_prints_the_contract_line():
+    """bench.py --impl reference times the FP64 oracle on the host (no GPU) and prints one
+    JSON line with the contract's keys."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "3",
+                        "--warmup", "3"], capture_output=True, text=True, timeout=600, cwd=root)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] > 0 and d["steps"] == 3
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
 
 
 def _free_port():
