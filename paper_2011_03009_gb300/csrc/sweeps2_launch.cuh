@@ -3,6 +3,7 @@
 #pragma once
 
 #include "sweeps2.cuh"
+#include "sweeps2_pair.cuh"
 
 namespace vp {
 namespace {
@@ -84,7 +85,7 @@ cudaError_t col2_dispatch(const ColSweep& p, int dir, bool src, cudaStream_t s) 
 // Persistent pipelined convolution sweep: one CTA per resident slot, tiles strided.
 // Resident CTAs per SM for a given shared-memory size, cached per (device, size).
 template <typename K>
-cudaError_t resident_slots(K kernel, size_t smem, volatile int* granted, int* grid_out) {
+cudaError_t resident_slots(K kernel, size_t smem, volatile int* granted, int* grid_out, int threads = kThreads2) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
@@ -103,7 +104,7 @@ cudaError_t resident_slots(K kernel, size_t smem, volatile int* granted, int* gr
     sms[dev] = v;
   }
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads2, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
   if (e != cudaSuccess) return e;
   *grid_out = per_sm * sms[dev];
   return cudaSuccess;
@@ -118,6 +119,25 @@ cudaError_t line2_conv_pipe_launch(const LineSweep& p, cudaStream_t s, bool* use
   // cropped output); any other line goes to line2_kernel
   if (2 * p.n_in > A * B || 2 * p.n_out > A * B) return cudaSuccess;
   const int ni = conv_stage_pitch(A, B);
+  if constexpr (A == 32 && B == 40) {
+    // L = 1280: the pair-split half-tile form, 16 warps a CTA (at L = 1024 the halves'
+    // rows share banks and it measured slower)
+    static volatile int grantedp[64] = {0};
+    const size_t smemp = conv_pair8_smem(A, B, p.Oz);
+    int gridp = 0;
+    if (smemp <= 200 * 1024) {
+      cudaError_t e = resident_slots(line2_conv_pair8_kernel<A, B>, smemp, grantedp, &gridp, kThreadsPair);
+      if (e != cudaSuccess) return e;
+    }
+    if (gridp >= 1) {
+      *used = true;
+      if (p.nlines <= 0) return cudaSuccess;
+      const long long halves = 2LL * p.nlines;
+      const int grid = (int)(gridp > halves ? halves : gridp);
+      line2_conv_pair8_kernel<A, B><<<(unsigned)grid, kThreadsPair, smemp, s>>>(p, halves, ni);
+      return cudaGetLastError();
+    }
+  }
   static BatchParams<LineSweep> none{};  // unused by the single-plan form
   // tiles of 16 lines, or (long lines) half tiles of 8 lines when those fit more CTAs per
   // SM: at L = 640-864 one 16-line CTA fills an SM's shared memory, two 8-line CTAs fit;
