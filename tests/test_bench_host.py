@@ -89,3 +89,12 @@ def test_replica_timing_takes_the_max_over_ranks():
         assert total == pytest.approx(20.0)
         # whole-job throughput: units of all ranks / slowest rank's time
         assert value == pytest.approx(1000 * 5 * world / 0.020)
+
+
+def test_contended_harmonics_are_those_started_before_the_side_stream_ended():
+    import bench
+    # step 0: V_k1 ends at 0.2 ms, harmonic 2 starts at 0, harmonic 3 at 0.5
+    # step 1: V_k1 ends at 0.6 ms (a slow step): harmonic 3 began at 0.55, inside it
+    assert bench.contended_harmonics([0.2], [{2: 0.0, 3: 0.5}]) == {2}
+    assert bench.contended_harmonics([0.2, 0.6], [{2: 0.0, 3: 0.5}, {2: 0.0, 3: 0.55}]) == {2, 3}
+    assert bench.contended_harmonics([], []) == set()

@@ -35,3 +35,24 @@ def test_overlapped_step_equals_serial_calls(gw):
     torch.cuda.synchronize()
     for n, t in gw.outs.items():
         assert torch.equal(t, got[n]), n
+
+
+def test_step_marks_show_the_first_harmonic_overlapping_v_k1(gw):
+    """The events a timed step records: harmonic 2 starts beside V_{k1} (its spans are
+    then re-timed alone); the outputs equal those of an unmarked step."""
+    import bench
+    gw.step()
+    torch.cuda.synchronize()
+    ref = {n: t.clone() for n, t in gw.outs.items()}
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    marks = {"side_end": ev(), "start": {st.harmonic: ev() for st in gw.w.steps}}
+    a = ev()
+    a.record()
+    gw.step(marks=marks)
+    torch.cuda.synchronize()
+    side_end = a.elapsed_time(marks["side_end"])
+    starts = {n: a.elapsed_time(e) for n, e in marks["start"].items()}
+    assert side_end > 0 and all(t >= 0 for t in starts.values())
+    assert 2 in bench.contended_harmonics([side_end], [starts])
+    for n, t in gw.outs.items():
+        assert torch.equal(t, ref[n]), n
