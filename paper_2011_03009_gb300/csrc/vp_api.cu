@@ -439,6 +439,10 @@ struct BatchChunk {
   int total[5] = {0, 0, 0, 0, 0};
   LineSweep first{};  // any item's z-sweep parameters (shared twiddle table, octant length)
   int ni_max = 0;     // longest z input or output line of the chunk
+  // every item's z sweep gives each resident CTA (two per SM) four tiles or more: the
+  // items then run the single-plan z kernel one after another, which reads each tile's
+  // record a phase ahead (the batched kernel reads it at use to keep two CTAs per SM)
+  bool z_per_item = false;
 };
 
 struct BatchGroup {
@@ -501,6 +505,13 @@ int build_group(vp_batch_s* b, BatchGroup& g) {
       if (acc[w] > 0x7fffffffLL) return VP_ERR_SIZE;
       ch->total[w] = (int)acc[w];
     }
+    long long min_tiles = -1;
+    for (int j = 0; j < n; ++j)
+      min_tiles = min_tiles < 0 ? ch->line.item[j].nlines : std::min(min_tiles, (long long)ch->line.item[j].nlines);
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return VP_ERR_CUDA;
+    ch->z_per_item = min_tiles >= 8LL * sms;
     for (int q = 0; q < 4; ++q) ch->col[q].offsets[n] = ch->total[q < 2 ? q : q + 1];
     ch->line.offsets[n] = ch->total[2];
     g.chunks.push_back(std::move(ch));
@@ -1074,7 +1085,13 @@ VP_API int vp_batch_run(vp_batch_t b, vp_stream_t stream) {
       const BatchChunk& ch = *chp;
       cudaError_t e = col2_batch(g.m[0], ch.col[0], ch.total[0], vp::kForward, g.src, s);
       if (e == cudaSuccess) e = col2_batch(g.m[1], ch.col[1], ch.total[1], vp::kForward, false, s);
-      if (e == cudaSuccess) e = line2_batch(g.m[2], ch.first, ch.ni_max, ch.line, ch.total[2], s);
+      if (e == cudaSuccess) {
+        if (ch.z_per_item) {
+          for (int j = 0; j < ch.line.count && e == cudaSuccess; ++j) e = vp::launch_line_any(ch.line.item[j], vp::kConv, s);
+        } else {
+          e = line2_batch(g.m[2], ch.first, ch.ni_max, ch.line, ch.total[2], s);
+        }
+      }
       if (e == cudaSuccess) e = col2_batch(g.m[1], ch.col[2], ch.total[3], vp::kInverse, false, s);
       if (e == cudaSuccess) e = col2_batch(g.m[0], ch.col[3], ch.total[4], vp::kInverse, false, s);
       if (e != cudaSuccess) return cuda_status(e);

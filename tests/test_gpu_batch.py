@@ -80,3 +80,38 @@ def test_batch_rejects_a_plan_listed_twice(vp):
         vp.Batch([p, p], [u, u], fs=[f, f])
     assert e.value.status == vp.VP_ERR_ARG
     p.close()
+
+
+def test_batch_of_large_items(vp):
+    """Items whose z sweeps fill the GPU several times over (96^3 and 96 x 96 x 90, M =
+    192: 2304 tiles of 16 lines each) run the single-plan z kernel one after another
+    inside the batch; the fields equal the single-plan ones and the oracle's."""
+    specs = [((96, 96, 96), 2), ((96, 96, 90), 2)]
+    plans, us, lowers, los = [], [], [], []
+    for i, (n, h) in enumerate(specs):
+        g = synth.Grid(n, (0.0, 0.0, 0.0), 9e-5)
+        p = vp.vp_plan(g, h, 1.1e6, synth.WATER)
+        assert tuple(p.info().m) == (192, 192, 192)
+        p.kernel_fft()
+        plans.append(p)
+        us.append(torch.empty(n, dtype=torch.complex64, device="cuda"))
+        lo = [synth.random_field(n, 700 + i)]
+        los.append(lo)
+        lowers.append([dev(x) for x in lo])
+    batch = vp.Batch(plans, us, lowers=lowers)
+    batch.run()
+    torch.cuda.synchronize()
+    for i, (n, h) in enumerate(specs):
+        got = us[i].cpu().numpy().astype(np.complex128)
+        u1 = torch.empty(n, dtype=torch.complex64, device="cuda")
+        plans[i].source_assemble(lowers[i])
+        plans[i].apply(None, u1)
+        torch.cuda.synchronize()
+        single = u1.cpu().numpy().astype(np.complex128)
+        assert np.linalg.norm(got - single) <= 1e-6 * np.linalg.norm(single), i
+        g = synth.Grid(n, (0.0, 0.0, 0.0), 9e-5)
+        ref = cascade.harmonic(h, los[i], g.h, 1.1e6, synth.WATER)
+        assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref), i
+    batch.close()
+    for p in plans:
+        p.close()
