@@ -287,7 +287,10 @@ VP_API int vp_incident_field(const vp_grid* g, const double* points, int n_point
  * the two-level engine on every axis and agree on f vs source form one group; each
  * group runs as one launch per FFT sweep over all its items (each CTA finds its item
  * in a per-sweep offset table), so a batch of uneven grids needs a handful of
- * launches instead of five per item.  Other items run one plan at a time.  All
+ * launches instead of five per item.  In a group whose items each give the z sweep
+ * at least 8 tiles of 16 lines per SM, that sweep runs item by item with the
+ * single-plan kernel (the column sweeps stay grouped).  Other items run one plan at a
+ * time.  All
  * pointers are device pointers bound at creation; vp_batch_run recomputes from their
  * current contents, so a stream capture of vp_batch_run replays correctly.  A plan may
  * appear at most once per batch (items share nothing but read-only inputs); kernel
