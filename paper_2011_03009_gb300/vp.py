@@ -136,12 +136,29 @@ def _stream(stream) -> ctypes.c_void_p:
     return ctypes.c_void_p(int(stream.cuda_stream))
 
 
-def _ptr(t) -> ctypes.c_void_p:
+def _voxels(grid) -> int:
+    """Voxel count of a grid (vp_grid or any object with .n)."""
+    c = 1
+    for v in grid.n:
+        c *= int(v)
+    return c
+
+
+def _need(t, n: int, what: str) -> None:
+    """The C ABI takes bare pointers: a buffer shorter than the call reads or writes would
+    be accessed out of bounds on the device, so the binding refuses it first."""
+    if t is not None and t.numel() < n:
+        raise ValueError(f"{what}: {t.numel()} elements, the call uses {n}")
+
+
+def _ptr(t, n: Optional[int] = None, what: str = "field") -> ctypes.c_void_p:
     import torch
     if t is None:
         return ctypes.c_void_p(0)
     if not (t.is_cuda and t.dtype == torch.complex64 and t.is_contiguous()):
         raise ValueError("fields must be contiguous torch.complex64 CUDA tensors")
+    if n is not None:
+        _need(t, n, what)
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -187,35 +204,50 @@ class Plan:
         _check(lib.vp_kernel_fft(self._h, _stream(stream)), "vp_kernel_fft")
 
     def kernel_spectrum_get(self, dst, stream=None):
-        _check(lib.vp_kernel_spectrum_get(self._h, _ptr(dst), _stream(stream)), "vp_kernel_spectrum_get")
+        _check(lib.vp_kernel_spectrum_get(self._h, _ptr(dst, self._octant(), "dst"), _stream(stream)),
+               "vp_kernel_spectrum_get")
 
     def kernel_spectrum_set(self, src, stream=None):
-        _check(lib.vp_kernel_spectrum_set(self._h, _ptr(src), _stream(stream)), "vp_kernel_spectrum_set")
+        _check(lib.vp_kernel_spectrum_set(self._h, _ptr(src, self._octant(), "src"), _stream(stream)),
+               "vp_kernel_spectrum_set")
+
+    def _octant(self) -> int:
+        m = self.info().m
+        return (m[0] // 2 + 1) * (m[1] // 2 + 1) * (m[2] // 2 + 1)
 
     def source_assemble(self, lower, f_out=None, stream=None, conj: bool = False):
         """Eq. 2.6 from lower = [p_1 .. p_{n-1}], or with conj=True the full source of
         Eq. 2.5 from lower = [p_1 .. p_{N_h}] (all entries are read)."""
-        arr = (ctypes.c_void_p * max(1, len(lower)))(*[_ptr(t).value for t in lower])
-        _check(lib.vp_source_assemble(self._h, arr, len(lower), VP_SRC_CONJ if conj else 0, _ptr(f_out),
+        nv = _voxels(self._g)
+        arr = (ctypes.c_void_p * max(1, len(lower)))(*[_ptr(t, nv, "lower field").value for t in lower])
+        _check(lib.vp_source_assemble(self._h, arr, len(lower), VP_SRC_CONJ if conj else 0, _ptr(f_out, nv, "f_out"),
                                       _stream(stream)), "vp_source_assemble")
 
     def source_from_nested(self, grids, lower, f_out=None, quadratic: bool = False, stream=None):
         """Eq. 2.6 from lower = [p_1 .. p_{n-1}] given on their own grids (grids[m-1] holds
         p_m): the restriction to this plan's grid and the products in one kernel."""
-        gs = (vp_grid * max(1, len(grids)))(*[g if isinstance(g, vp_grid) else grid_of(g) for g in grids])
-        arr = (ctypes.c_void_p * max(1, len(lower)))(*[_ptr(t).value for t in lower])
+        if len(grids) != len(lower):
+            raise ValueError("source_from_nested: one grid per lower field")
+        gl = [g if isinstance(g, vp_grid) else grid_of(g) for g in grids]
+        gs = (vp_grid * max(1, len(gl)))(*gl)
+        arr = (ctypes.c_void_p * max(1, len(lower)))(
+            *[_ptr(t, _voxels(gl[i]), "lower field").value for i, t in enumerate(lower)])
         _check(lib.vp_source_from_nested(self._h, gs, arr, len(lower), VP_RESTRICT_QUADRATIC if quadratic else 0,
-                                         _ptr(f_out), _stream(stream)), "vp_source_from_nested")
+                                         _ptr(f_out, _voxels(self._g), "f_out"), _stream(stream)),
+               "vp_source_from_nested")
 
     def apply(self, f, u, stream=None):
-        _check(lib.vp_apply(self._h, _ptr(f), _ptr(u), _stream(stream)), "vp_apply")
+        nv = _voxels(self._g)
+        _check(lib.vp_apply(self._h, _ptr(f, nv, "f"), _ptr(u, nv, "u"), _stream(stream)), "vp_apply")
 
     def vie_solve(self, q, b, x, tol: float = 1e-6, max_iter: int = 200, stream=None):
         """Solve x - V[q x] = b (Section 7) by BiCGStab in the library; x holds the initial
         guess and receives the solution.  Returns (iterations, relative residual)."""
         it = ctypes.c_int(0)
         res = ctypes.c_double(0.0)
-        _check(lib.vp_vie_solve(self._h, _ptr(q), _ptr(b), _ptr(x), float(tol), int(max_iter), ctypes.byref(it),
+        nv = _voxels(self._g)
+        _check(lib.vp_vie_solve(self._h, _ptr(q, nv, "q"), _ptr(b, nv, "b"), _ptr(x, nv, "x"), float(tol),
+                                int(max_iter), ctypes.byref(it),
                                 ctypes.byref(res), _stream(stream)), "vp_vie_solve")
         return it.value, res.value
 
@@ -248,16 +280,17 @@ class Batch:
         self._keep = (list(plans), list(us), fs, lowers)  # keep tensors and plans alive
         P = ctypes.c_void_p
         pa = (P * count)(*[p._h.value for p in plans])
-        ua = (P * count)(*[_ptr(t).value for t in us])
+        nv = [_voxels(p._g) for p in plans]
+        ua = (P * count)(*[_ptr(t, nv[i], "u").value for i, t in enumerate(us)])
         fa = None
         if fs is not None:
-            fa = (P * count)(*[(_ptr(t).value if t is not None else None) for t in fs])
+            fa = (P * count)(*[(_ptr(t, nv[i], "f").value if t is not None else None) for i, t in enumerate(fs)])
         la = None
         if lowers is not None:
             flat = []
             for i in range(count):
                 row = list(lowers[i] or [])
-                flat += [_ptr(t).value for t in row] + [None] * (MAX_LOWER - len(row))
+                flat += [_ptr(t, nv[i], "lower field").value for t in row] + [None] * (MAX_LOWER - len(row))
             la = (P * (count * MAX_LOWER))(*flat)
         self._h = P(0)
         _check(lib.vp_batch_create(count, pa, fa, la, ua, ctypes.byref(self._h)), "vp_batch_create")
@@ -304,25 +337,30 @@ def vp_restrict_to_nested_box(src_grid, src, dst_grid, dst, zero_outside: bool =
     gs = src_grid if isinstance(src_grid, vp_grid) else grid_of(src_grid)
     gd = dst_grid if isinstance(dst_grid, vp_grid) else grid_of(dst_grid)
     flags = (VP_RESTRICT_ZERO_OUTSIDE if zero_outside else 0) | (VP_RESTRICT_QUADRATIC if quadratic else 0)
-    _check(lib.vp_restrict_to_nested_box(ctypes.byref(gs), _ptr(src), ctypes.byref(gd), _ptr(dst), flags,
+    _check(lib.vp_restrict_to_nested_box(ctypes.byref(gs), _ptr(src, _voxels(gs), "src"), ctypes.byref(gd),
+                                         _ptr(dst, _voxels(gd), "dst"), flags,
                                          _stream(stream)), "vp_restrict_to_nested_box")
 
 
 def vp_vec_axpby(a, x, b, y, out, stream=None):
     """out = a x + b y (complex scalars; y may be None)."""
     a, b = complex(a), complex(b)
-    _check(lib.vp_vec_axpby(x.numel(), a.real, a.imag, _ptr(x), b.real, b.imag, _ptr(y), _ptr(out), _stream(stream)),
+    n = x.numel()
+    _check(lib.vp_vec_axpby(n, a.real, a.imag, _ptr(x), b.real, b.imag, _ptr(y, n, "y"), _ptr(out, n, "out"),
+                            _stream(stream)),
            "vp_vec_axpby")
 
 
 def vp_vec_mul(x, y, out, stream=None):
-    _check(lib.vp_vec_mul(x.numel(), _ptr(x), _ptr(y), _ptr(out), _stream(stream)), "vp_vec_mul")
+    n = x.numel()
+    _check(lib.vp_vec_mul(n, _ptr(x), _ptr(y, n, "y"), _ptr(out, n, "out"), _stream(stream)), "vp_vec_mul")
 
 
 def vp_vec_dot(x, y, conj_x: bool = True, stream=None) -> complex:
     """sum conj(x) y (or sum x y), accumulated in FP64."""
     out = (ctypes.c_double * 2)()
-    _check(lib.vp_vec_dot(x.numel(), _ptr(x), _ptr(y), 1 if conj_x else 0, out, _stream(stream)), "vp_vec_dot")
+    n = x.numel()
+    _check(lib.vp_vec_dot(n, _ptr(x), _ptr(y, n, "y"), 1 if conj_x else 0, out, _stream(stream)), "vp_vec_dot")
     return complex(out[0], out[1])
 
 
@@ -339,13 +377,14 @@ def vp_q0_box(field, q0: float, stream=None):
 def vp_incident_field(grid, points, bowl, medium, out, stream=None):
     """p1 on `grid` (Eq. 3.10); points: (n_p, 3) float64 CUDA tensor."""
     import torch
-    if not (points.is_cuda and points.dtype == torch.float64 and points.is_contiguous()):
+    if not (points.is_cuda and points.dtype == torch.float64 and points.is_contiguous()
+            and points.dim() == 2 and points.shape[1] == 3):
         raise ValueError("points must be a contiguous float64 CUDA tensor of shape (n_p, 3)")
     g = grid if isinstance(grid, vp_grid) else grid_of(grid)
     med = medium if isinstance(medium, vp_medium) else make_medium(medium)
     _check(lib.vp_incident_field(ctypes.byref(g), ctypes.c_void_p(points.data_ptr()), int(points.shape[0]),
                                  float(bowl.l), float(bowl.R), float(bowl.f0), float(bowl.p0), ctypes.byref(med),
-                                 _ptr(out), _stream(stream)), "vp_incident_field")
+                                 _ptr(out, _voxels(g), "out"), _stream(stream)), "vp_incident_field")
 
 
 VP_STATIC_MAX_N = 64
@@ -359,7 +398,9 @@ def vp_apply_static(grid, harmonic: int, f0: float, medium, f, u, stream=None):
     not overlap on the GPU."""
     g = grid if isinstance(grid, vp_grid) else grid_of(grid)
     med = medium if isinstance(medium, vp_medium) else make_medium(medium)
-    _check(lib.vp_apply_static(ctypes.byref(g), int(harmonic), float(f0), ctypes.byref(med), _ptr(f), _ptr(u),
+    nv = _voxels(g)
+    _check(lib.vp_apply_static(ctypes.byref(g), int(harmonic), float(f0), ctypes.byref(med), _ptr(f, nv, "f"),
+                               _ptr(u, nv, "u"),
                                _stream(stream)), "vp_apply_static")
 
 

@@ -160,3 +160,121 @@ def test_fno_descriptor_checks_on_the_host(vp):
     assert fno.lib.vp_fno_adam(-1, P(64), P(64), P(64), P(64), P(64), 1e-3, 0.9, 0.999, 1e-8, 0.1, 0.001, 1.0,
                                None) == vp.VP_ERR_ARG
     assert fno.lib.vp_fno_to_bf16(4, None, P(64), None) == vp.VP_ERR_ARG
+
+
+def test_binding_refuses_buffers_shorter_than_the_call_uses(vp):
+    """The ABI takes bare pointers; the binding checks lengths before any call, so a short
+    buffer never reaches a kernel (host-only: the check runs on CPU tensors here)."""
+    import torch
+    from paper_2011_03009_gb300 import synth
+    g = synth.Grid((4, 5, 6), (0.0, 0.0, 0.0), 1e-4)
+    assert vp._voxels(g) == 120 and vp._voxels(vp.grid_of(g)) == 120
+    vp._need(torch.empty(120, dtype=torch.complex64), 120, "u")
+    vp._need(torch.empty(200, dtype=torch.complex64), 120, "u")  # longer is fine
+    vp._need(None, 120, "f")
+    with pytest.raises(ValueError, match="119 elements"):
+        vp._need(torch.empty(119, dtype=torch.complex64), 120, "u")
+
+
+class _FakeField:
+    """Stands in for a contiguous complex64 CUDA tensor (no GPU on the host)."""
+
+    def __init__(self, n, dtype=None, shape=None):
+        import torch
+        self.dtype = dtype or torch.complex64
+        self._n = n
+        self.shape = shape or (n,)
+        self.is_cuda = True
+
+    def is_contiguous(self):
+        return True
+
+    def numel(self):
+        return self._n
+
+    def data_ptr(self):
+        return 4096
+
+    def dim(self):
+        return len(self.shape)
+
+
+class _FakeLib:
+    """Records each ABI call and returns VP_OK (vp_plan_get_info fills m = 2N)."""
+
+    def __init__(self):
+        self.calls = []
+
+    def __getattr__(self, name):
+        def call(*args):
+            self.calls.append(name)
+            if name == "vp_plan_get_info":
+                info = args[1]._obj
+                for a in range(3):
+                    info.m[a] = 2 * (a + 4)
+            return 0
+        return call
+
+
+def test_binding_marshals_every_call_with_length_checks(vp, monkeypatch):
+    """Every binding entry point that takes fields, run against a fake library: correct
+    lengths pass through to the ABI, a buffer one element short is refused first."""
+    import torch
+    from paper_2011_03009_gb300 import synth
+    fake = _FakeLib()
+    monkeypatch.setattr(vp, "lib", fake)
+    monkeypatch.setattr(vp, "_stream", lambda stream: ctypes.c_void_p(0))
+    g = synth.Grid((4, 5, 6), (0.0, 0.0, 0.0), 1e-4)
+    gl = synth.Grid((3, 3, 3), (0.0, 0.0, 0.0), 2e-4)
+    nv, nl = 120, 27
+    plan = object.__new__(vp.Plan)
+    plan._h, plan._g, plan.n = ctypes.c_void_p(1), vp.grid_of(g), g.n
+    F = _FakeField
+    batch = None
+    try:
+        octant = 5 * 6 * 7  # m = 8, 10, 12 from the fake info
+        plan.kernel_spectrum_get(F(octant))
+        plan.kernel_spectrum_set(F(octant))
+        plan.source_assemble([F(nv), F(nv)], f_out=F(nv))
+        plan.source_from_nested([gl, g], [F(nl), F(nv)], f_out=F(nv))
+        plan.apply(F(nv), F(nv))
+        plan.apply(None, F(nv))
+        plan.vie_solve(F(nv), F(nv), F(nv))
+        vp.vp_restrict_to_nested_box(gl, F(nl), g, F(nv))
+        vp.vp_vec_axpby(1, F(nv), 2, F(nv), F(nv))
+        vp.vp_vec_mul(F(nv), F(nv), F(nv))
+        vp.vp_vec_dot(F(nv), F(nv))
+        pts = F(30, dtype=torch.float64, shape=(10, 3))
+        bowl = synth.Bowl(l=0.06, R=0.03, f0=1.1e6, p0=1e6)
+        vp.vp_incident_field(g, pts, bowl, synth.WATER, F(nv))
+        vp.vp_apply_static(g, 2, 1.1e6, synth.WATER, F(nv), F(nv))
+        batch = vp.Batch([plan], [F(nv)], fs=[None], lowers=[[F(nv)]])
+        batch.run()
+        for name in ("vp_kernel_spectrum_get", "vp_source_from_nested", "vp_apply", "vp_vie_solve",
+                     "vp_restrict_to_nested_box", "vp_vec_dot", "vp_incident_field", "vp_apply_static",
+                     "vp_batch_create", "vp_batch_run"):
+            assert name in fake.calls, name
+        short = [
+            lambda: plan.kernel_spectrum_get(F(octant - 1)),
+            lambda: plan.source_assemble([F(nv), F(nv - 1)]),
+            lambda: plan.source_from_nested([gl, g], [F(nl - 1), F(nv)]),
+            lambda: plan.source_from_nested([gl], [F(nl), F(nv)]),
+            lambda: plan.apply(F(nv), F(nv - 1)),
+            lambda: plan.vie_solve(F(nv), F(nv - 1), F(nv)),
+            lambda: vp.vp_restrict_to_nested_box(gl, F(nl), g, F(nv - 1)),
+            lambda: vp.vp_vec_mul(F(nv), F(nv - 1), F(nv)),
+            lambda: vp.vp_incident_field(g, F(30, dtype=torch.float64, shape=(30,)), bowl, synth.WATER, F(nv)),
+            lambda: vp.vp_apply_static(g, 2, 1.1e6, synth.WATER, F(nv - 1), F(nv)),
+            lambda: vp.Batch([plan], [F(nv - 1)], fs=[F(nv)]),
+        ]
+        for i, bad in enumerate(short):
+            before = len(fake.calls)
+            with pytest.raises(ValueError):
+                bad()
+            # refused before the ABI call (only the plan-info query may have run)
+            assert set(fake.calls[before:]) <= {"vp_plan_get_info"}, (i, fake.calls[before:])
+    finally:
+        # the handles are fake: keep the destructors away from the real library
+        plan._h = ctypes.c_void_p(0)
+        if batch is not None:
+            batch._h = ctypes.c_void_p(0)
