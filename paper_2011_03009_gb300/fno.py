@@ -64,6 +64,18 @@ def _p(t) -> P:
     return P(t.data_ptr()) if t is not None else P(0)
 
 
+def _rows(t, n: int, cols: int, what: str) -> P:
+    """Pointer to a [n^3][cols] FP32 activation; the ABI takes bare pointers, so a tensor of
+    the wrong type or shorter than the call reads or writes is refused here."""
+    if t is None:
+        return P(0)
+    if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise ValueError(f"{what}: a contiguous float32 CUDA tensor is required")
+    if t.numel() < n ** 3 * cols:
+        raise ValueError(f"{what}: {t.numel()} elements, the call uses {n ** 3 * cols}")
+    return P(t.data_ptr())
+
+
 def _s(stream=None) -> P:
     stream = stream or torch.cuda.current_stream()
     return P(int(stream.cuda_stream))
@@ -163,16 +175,20 @@ class Fno:
 
     # ---- passes ---------------------------------------------------------------------
     def forward(self, x: torch.Tensor, y: Optional[torch.Tensor] = None):
-        _check(lib.vp_fno_forward(ctypes.byref(self.d), _p(self.params), _p(self.params_bf16), _p(x), _p(y),
-                                  _p(self.ws), _s()), "vp_fno_forward")
+        n = self.cfg.n
+        _check(lib.vp_fno_forward(ctypes.byref(self.d), _p(self.params), _p(self.params_bf16), _rows(x, n, 2, "x"),
+                                  _rows(y, n, 8, "y"), _p(self.ws), _s()), "vp_fno_forward")
 
     def loss(self, target: torch.Tensor) -> torch.Tensor:
-        _check(lib.vp_fno_loss(ctypes.byref(self.d), _p(target), _p(self.sums), _p(self.ws), _s()), "vp_fno_loss")
+        _check(lib.vp_fno_loss(ctypes.byref(self.d), _rows(target, self.cfg.n, 8, "target"), _p(self.sums),
+                               _p(self.ws), _s()), "vp_fno_loss")
         return self.sums
 
     def backward(self, x: torch.Tensor, target: torch.Tensor):
-        _check(lib.vp_fno_backward(ctypes.byref(self.d), _p(self.params), _p(self.params_bf16), _p(x), _p(target),
-                                   _p(self.grads), _p(self.ws), _s()), "vp_fno_backward")
+        n = self.cfg.n
+        _check(lib.vp_fno_backward(ctypes.byref(self.d), _p(self.params), _p(self.params_bf16), _rows(x, n, 2, "x"),
+                                   _rows(target, n, 8, "target"), _p(self.grads), _p(self.ws), _s()),
+               "vp_fno_backward")
 
     def adam(self, lr: float, grad_scale: float = 1.0, b1=0.9, b2=0.999, eps=1e-8):
         self.step_count += 1
@@ -197,8 +213,9 @@ class Fno:
 
     def infer(self, x: torch.Tensor, y: torch.Tensor):
         """Inference only (no activations kept): y [N^3][8] from x [N^3][2]."""
-        _check(lib.vp_fno_infer(ctypes.byref(self.d), _p(self.params), _p(self.params_bf16), _p(x), _p(y),
-                                _p(self.ws), _s()), "vp_fno_infer")
+        n = self.cfg.n
+        _check(lib.vp_fno_infer(ctypes.byref(self.d), _p(self.params), _p(self.params_bf16), _rows(x, n, 2, "x"),
+                                _rows(y, n, 8, "y"), _p(self.ws), _s()), "vp_fno_infer")
 
     def predict(self, x: torch.Tensor, y: torch.Tensor):
         self.infer(x, y)

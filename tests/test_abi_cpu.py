@@ -278,3 +278,31 @@ def test_binding_marshals_every_call_with_length_checks(vp, monkeypatch):
         plan._h = ctypes.c_void_p(0)
         if batch is not None:
             batch._h = ctypes.c_void_p(0)
+
+
+def test_surrogate_binding_checks_activation_buffers(vp, monkeypatch):
+    """The surrogate's forward, loss, backward and inference against a fake library:
+    [N^3][2] inputs and [N^3][8] outputs/targets pass, a short or FP64 buffer is refused."""
+    import torch
+    from paper_2011_03009_gb300 import fno
+    fake = _FakeLib()
+    monkeypatch.setattr(fno, "lib", fake)
+    monkeypatch.setattr(fno, "_s", lambda stream=None: ctypes.c_void_p(0))
+    m = object.__new__(fno.Fno)
+    m.cfg = fno.FnoConfig(n=4, width=4, hidden=8, layers=1, modes=(2, 2, 2))
+    m.d = ctypes.c_int(0)
+    m.params = m.params_bf16 = m.ws = m.grads = m.sums = torch.zeros(4)
+    x, y = _FakeField(128, dtype=torch.float32), _FakeField(512, dtype=torch.float32)
+    m.forward(x, y)
+    m.forward(x)
+    m.loss(y)
+    m.backward(x, y)
+    m.infer(x, y)
+    assert fake.calls == ["vp_fno_forward", "vp_fno_forward", "vp_fno_loss", "vp_fno_backward", "vp_fno_infer"]
+    for bad in (lambda: m.forward(_FakeField(127, dtype=torch.float32)),
+                lambda: m.infer(x, _FakeField(511, dtype=torch.float32)),
+                lambda: m.loss(_FakeField(512, dtype=torch.float64)),
+                lambda: m.backward(x, _FakeField(100, dtype=torch.float32))):
+        with pytest.raises(ValueError):
+            bad()
+    assert len(fake.calls) == 5
