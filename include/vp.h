@@ -56,7 +56,8 @@ extern "C" {
 #define VP_ERR_CUDA        -4  /* a CUDA runtime call or kernel launch failed              */
 #define VP_ERR_NOT_NESTED  -5  /* restriction target not inside the source grid           */
 #define VP_ERR_STATE       -6  /* call out of order (no staged source; spectrum not built) */
-#define VP_ERR_TIMEOUT     -7  /* a bounded device wait expired                            */
+#define VP_ERR_TIMEOUT     -7  /* reserved: no call of this build returns it (no kernel
+                                  waits on another launch or on the host)                  */
 #define VP_ERR_UNSUPPORTED -8  /* valid request outside what this build implements        */
 
 typedef void* vp_stream_t; /* cudaStream_t */
@@ -311,22 +312,24 @@ VP_API int vp_batch_destroy(vp_batch_t b);
  * it, and latency-bound loops that cannot afford the device-wide synchronisation of
  * cudaMalloc/cudaFree.
  *
- * vp_apply_static computes u = V_{k_n}[f] exactly like vp_plan (default embedding and
- * radix schedule) + vp_kernel_fft + vp_apply, for grids of at most VP_STATIC_MAX_N
- * voxels per axis, keeping every intermediate in one fixed-size __device__ array inside
- * libvp.so (about 18.2 MiB, held by every GPU that loads the library until the process
- * exits).  It calls no cudaMalloc, cudaFree or other allocating routine.  The caller
- * passes f and u (device pointers, complex64, N voxels each, not aliased); the
- * kernel spectrum is rebuilt on every call.
- * - The first call on a device looks up the array's device address
- *   (cudaGetSymbolAddress) with that device current; make that first call before any
- *   stream capture.
+ * vp_apply_static computes the same u = V_{k_n}[f] as vp_plan + vp_kernel_fft + vp_apply,
+ * for grids of at most VP_STATIC_MAX_N voxels per axis, on the smallest even 5-smooth
+ * embedding M >= 2N with the radix-pass FFT engine (vp_plan may pick another embedding
+ * and engine), so the two agree to FP32 rounding, not bit for bit.  Every intermediate
+ * lives in one fixed-size __device__ array inside libvp.so (about 18.2 MiB, held by
+ * every GPU that loads the library until the process exits).  It calls no cudaMalloc,
+ * cudaFree or other allocating routine.  The caller passes f and u (device pointers,
+ * complex64, N voxels each, not aliased); the kernel spectrum is rebuilt on every call.
+ * - The first call in a CUDA context looks up the array's device address
+ *   (cudaGetSymbolAddress) with the device current, and caches it for that device and
+ *   context; make that first call before any stream capture (again after a
+ *   cudaDeviceReset, which gives the device a new context).
  * - Every call on a device shares the array and rewrites everything it later reads,
  *   so no state carries over between calls; calls whose GPU work overlaps (other
  *   streams, other host threads) race on the array and must be serialised.
  * Errors: VP_ERR_ARG (null pointers, n[i] < 1, h <= 0, harmonic < 1, f0 <= 0, c0 <= 0,
- * rho0 <= 0, alpha0 < 0), VP_ERR_SIZE (an axis longer than VP_STATIC_MAX_N),
- * VP_ERR_CUDA. */
+ * rho0 <= 0, alpha0 < 0, or a non-finite h, f0, c0, rho0, alpha0, beta or eta),
+ * VP_ERR_SIZE (an axis longer than VP_STATIC_MAX_N), VP_ERR_CUDA. */
 #define VP_STATIC_MAX_N 64
 VP_API int vp_apply_static(const vp_grid* g, int harmonic_n, double f0_hz, const vp_medium* m,
                            const void* f, void* u, vp_stream_t stream);
@@ -344,7 +347,8 @@ VP_API const char* vp_status_string(int status);
 VP_API int vp_profile_enable(vp_plan_t p, int on);
 VP_API int vp_profile_read(vp_plan_t p, double ms[5], int count[5], int reset);
 
-/* Library build identification string (static). */
+/* Library build identification string (static): "libvp <version> sm_103a src <digest>",
+ * where <digest> is the SHA-256 prefix of the sources the library was built from. */
 VP_API const char* vp_version(void);
 
 #ifdef __cplusplus

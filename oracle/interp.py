@@ -13,9 +13,15 @@ clamped to [0, N-2]; weight w = t - i0; the value is the tensor product of the
 Quadratic (the higher-order option Section 6 mentions): per axis the Lagrange
 polynomial through the three nearest source centres c - 1, c, c + 1 with
 c = floor(t + 1/2) clamped to [1, N-2], evaluated at u = t - c.  At a half-integer t
-two stencils are equally near; which one is used is decided on t held as an exact
-40-bit fixed-point number (the positions the C interface defines), so that both
-implementations take the same decision.
+two stencils are equally near and the paper does not say which to take; both are
+valid.  Two ways of locating the targets are offered:
+- positions="float": t from the plain FP64 formula; at a target within TIE_TOL of a
+  half-integer the caller picks the stencil below (tie="down") or above (tie="up");
+- positions="fixed" (default): t held as an exact 40-bit fixed-point number (the
+  positions the C interface defines), so that a cascade compared voxel by voxel sees
+  the same stencil decision on both sides.  The pins check that the fixed positions
+  give the float positions' stencil and weights away from ties, and one of the two
+  valid stencils at a tie.
 """
 from __future__ import annotations
 
@@ -90,10 +96,14 @@ def _fixed_positions(src_origin: float, src_h: float, dst_origin: float, dst_h: 
     return np.array([A + i * B for i in range(count)], dtype=object)
 
 
-def _axis_quadratic(src_origin: float, src_h: float, src_n: int, dst_coords: np.ndarray, T=None):
+TIE_TOL = 1.0e-9
+
+
+def _axis_quadratic(src_origin: float, src_h: float, src_n: int, dst_coords: np.ndarray, T=None, tie="down"):
     """Indices (k, 3) and weights (k, 3) of the quadratic Lagrange interpolant through the
     three source centres nearest to each target; a two-centre axis stays linear and a
-    one-centre axis takes its only value.  T: exact fixed-point positions (optional)."""
+    one-centre axis takes its only value.  T: exact fixed-point positions (optional);
+    without them, t within TIE_TOL of a half-integer takes the stencil ``tie`` names."""
     t = (dst_coords - src_origin) / src_h
     k = len(t)
     if src_n < 3:
@@ -104,7 +114,10 @@ def _axis_quadratic(src_origin: float, src_h: float, src_n: int, dst_coords: np.
     if np.any(t < -TOL) or np.any(t > (src_n - 1) + TOL):
         raise ValueError("target outside the source grid")
     if T is None:
-        c = np.clip(np.floor(t + 0.5).astype(np.int64), 1, src_n - 2)
+        lo = np.floor(t).astype(np.int64)
+        at_tie = np.abs(t - lo - 0.5) <= TIE_TOL
+        c = np.where(at_tie, lo + (1 if tie == "up" else 0), np.floor(t + 0.5).astype(np.int64))
+        c = np.clip(c, 1, src_n - 2)
         u = t - c
     else:
         half = 1 << (FIX_BITS - 1)
@@ -117,14 +130,33 @@ def _axis_quadratic(src_origin: float, src_h: float, src_n: int, dst_coords: np.
     return np.stack([c - 1, c, c + 1], axis=1), np.stack([l_m, l_0, l_p], axis=1)
 
 
-def restrict_quadratic(src: np.ndarray, src_grid, dst_grid) -> np.ndarray:
-    """Values of the tensor-product quadratic interpolant of ``src`` at dst_grid's centres."""
+def tie_axes(src_grid, dst_grid):
+    """Per axis, a boolean mask of the targets within TIE_TOL of a half-integer source
+    position (where two quadratic stencils are equally near)."""
+    out = []
+    for a in range(3):
+        coords = dst_grid.origin[a] + dst_grid.h * np.arange(dst_grid.n[a], dtype=np.float64)
+        t = (coords - src_grid.origin[a]) / src_grid.h
+        out.append(np.abs(t - np.floor(t) - 0.5) <= TIE_TOL if src_grid.n[a] >= 3 else np.zeros(len(t), bool))
+    return out
+
+
+def restrict_quadratic(src: np.ndarray, src_grid, dst_grid, positions: str = "fixed", tie=("down",) * 3) -> np.ndarray:
+    """Values of the tensor-product quadratic interpolant of ``src`` at dst_grid's centres.
+
+    positions="fixed": the stencil centres from the exact fixed-point positions;
+    positions="float": from the FP64 positions, with tie[a] ("down" or "up") choosing the
+    stencil on axis a at half-integer positions."""
     src = np.asarray(src, dtype=np.complex128)
+    if positions not in ("fixed", "float"):
+        raise ValueError("positions must be 'fixed' or 'float'")
     idx, wts = [], []
     for a in range(3):
         coords = dst_grid.origin[a] + dst_grid.h * np.arange(dst_grid.n[a], dtype=np.float64)
-        T = _fixed_positions(src_grid.origin[a], src_grid.h, dst_grid.origin[a], dst_grid.h, dst_grid.n[a])
-        i, w = _axis_quadratic(src_grid.origin[a], src_grid.h, src_grid.n[a], coords, T)
+        T = None
+        if positions == "fixed":
+            T = _fixed_positions(src_grid.origin[a], src_grid.h, dst_grid.origin[a], dst_grid.h, dst_grid.n[a])
+        i, w = _axis_quadratic(src_grid.origin[a], src_grid.h, src_grid.n[a], coords, T, tie[a])
         idx.append(i)
         wts.append(w)
     out = np.zeros(tuple(dst_grid.n), dtype=np.complex128)

@@ -5,6 +5,9 @@ self-cell integral.  Two evaluations:
 
 - ``apply_bruteforce``: the double sum written out, distances taken from the voxel
   centres, O(N^2).  It does not use ``greens.kernel_lattice``.
+- ``apply_sparse``: the same sum at chosen target voxels for a source that is zero
+  outside a list of voxels, O(targets x sources); it serves grids too large for the
+  other two.
 - ``apply_fft``: the same sum as a 3-level Toeplitz matrix-vector product, embedded in
   a circulant of size M >= 2N - 1 per axis and evaluated with FFTs (Section 3.1;
   Section 6 uses M = 2N).  Offsets d in (-N, N) sit at index d mod M; any
@@ -50,6 +53,27 @@ def apply_bruteforce(f: np.ndarray, h: float, k: complex, targets=None) -> np.nd
         out[s:s + chunk] = w @ fv
     if targets is None:
         return out.reshape(n)
+    return out
+
+
+def apply_sparse(src_idx, src_val, h: float, k: complex, targets) -> np.ndarray:
+    """Eq. 3.9 at the target voxels ``targets`` ((T, 3) ints) for the source that equals
+    ``src_val[j]`` at voxel ``src_idx[j]`` ((S, 3) ints) and zero elsewhere:
+    u(t) = sum_j w(t - s_j) f_j with w = h^3 G_k(h |t - s_j|) off the diagonal and the
+    self-cell integral on it.  The grid's extent does not enter."""
+    s = np.asarray(src_idx, dtype=np.float64).reshape(-1, 3)
+    f = np.asarray(src_val, dtype=np.complex128).reshape(-1)
+    t = np.asarray(targets, dtype=np.float64).reshape(-1, 3)
+    self_w = greens.self_cell(k, h)
+    out = np.empty(len(t), dtype=np.complex128)
+    chunk = max(1, 4_000_000 // max(1, len(s)))
+    for a in range(0, len(t), chunk):
+        d = t[a:a + chunk, None, :] - s[None, :, :]
+        r = h * np.sqrt(np.sum(d * d, axis=2))
+        same = r == 0.0
+        r_safe = np.where(same, 1.0, r)
+        w = np.where(same, self_w, h ** 3 * np.exp(1j * k * r_safe) / (4.0 * math.pi * r_safe))
+        out[a:a + chunk] = w @ f
     return out
 
 

@@ -593,7 +593,11 @@ VP_API const char* vp_status_string(int status) {
   }
 }
 
-VP_API const char* vp_version(void) { return "libvp 0.1 sm_103a"; }
+#ifndef VP_SOURCE_DIGEST
+#define VP_SOURCE_DIGEST "unknown"
+#endif
+// The digest of the sources the library was built from (set by the build script).
+VP_API const char* vp_version(void) { return "libvp 0.2 sm_103a src " VP_SOURCE_DIGEST; }
 
 VP_API int vp_plan(const vp_grid* g, int harmonic_n, double f0_hz, const vp_medium* med,
                    const vp_plan_opts* opts, vp_stream_t stream, vp_plan_t* out) {

@@ -14,6 +14,7 @@
 // exits.  All calls on a device share the array and every call rewrites all of it
 // that it reads, so nothing carries over from one call to the next; two calls whose
 // GPU work overlaps (different streams, or different host threads) race on it.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -54,21 +55,58 @@ static_assert(kCubeBytes >= ((size_t)kStaticMaxM * kStaticMaxN * kStaticMaxN +
 // host-side shadow, not device memory): it goes through cudaGetSymbolAddress below.
 static __device__ __align__(256) unsigned char g_static_scratch[kScratchBytes];
 
-std::mutex g_addr_mu;
-void* g_addr[64] = {nullptr};
+// The array's device address belongs to the CUDA context that loaded the module: after
+// cudaDeviceReset, or once the primary context is released and created again, the
+// module is loaded anew and the array may sit elsewhere.  The address is therefore
+// cached per device together with the context it was taken in, and looked up again
+// whenever the current context differs.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
 
-// Device address of the scratch for the current device, looked up once per device.
+CtxGetCurrentFn ctx_get_current() {
+  static CtxGetCurrentFn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return (CtxGetCurrentFn)f;
+  }();
+  return fn;
+}
+
+// The context current on this thread, or nullptr if none is (or it cannot be read).
+CUcontext current_context() {
+  CtxGetCurrentFn get = ctx_get_current();
+  CUcontext c = nullptr;
+  if (!get || get(&c) != CUDA_SUCCESS) return nullptr;
+  return c;
+}
+
+struct ScratchAddr {
+  CUcontext ctx;
+  void* ptr;
+};
+std::mutex g_addr_mu;
+ScratchAddr g_addr[64] = {};
+
+// Device address of the scratch for the current device and context.  The lookup runs
+// on the first call in each context; later calls in that context read the cache.
 int scratch_address(void** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return VP_ERR_CUDA;
   if (dev < 0 || dev >= 64) return VP_ERR_UNSUPPORTED;
   std::lock_guard<std::mutex> lk(g_addr_mu);
-  if (!g_addr[dev]) {
+  CUcontext ctx = current_context();
+  if (!ctx || g_addr[dev].ctx != ctx || !g_addr[dev].ptr) {
     void* ptr = nullptr;
+    // cudaGetSymbolAddress makes the device's primary context current if none is
     if (cudaGetSymbolAddress(&ptr, g_static_scratch) != cudaSuccess || !ptr) return VP_ERR_CUDA;
-    g_addr[dev] = ptr;
+    ctx = current_context();
+    g_addr[dev] = ScratchAddr{ctx, ctx ? ptr : nullptr};  // without a context handle: no caching
+    *out = ptr;
+    return VP_OK;
   }
-  *out = g_addr[dev];
+  *out = g_addr[dev].ptr;
   return VP_OK;
 }
 
@@ -177,7 +215,9 @@ __global__ void static_tables_kernel(StaticTables t) {
 extern "C" VP_API int vp_apply_static(const vp_grid* g, int harmonic_n, double f0_hz, const vp_medium* med,
                                       const void* f, void* u, vp_stream_t stream) {
   if (!g || !med || !f || !u || harmonic_n < 1 || !(f0_hz > 0) || !std::isfinite(f0_hz) ||
-      !(g->h > 0) || !std::isfinite(g->h) || !(med->c0 > 0) || !(med->rho0 > 0) || !(med->alpha0 >= 0))
+      !(g->h > 0) || !std::isfinite(g->h) || !(med->c0 > 0) || !(med->rho0 > 0) || !(med->alpha0 >= 0) ||
+      !std::isfinite(med->c0) || !std::isfinite(med->rho0) || !std::isfinite(med->alpha0) ||
+      !std::isfinite(med->beta) || !std::isfinite(med->eta))
     return VP_ERR_ARG;
   for (int a = 0; a < 3; ++a) {
     if (g->n[a] < 1) return VP_ERR_ARG;

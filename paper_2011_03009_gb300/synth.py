@@ -159,6 +159,34 @@ def smooth_blob_field(grid: Grid, centre: Sequence[float], width: float, k: floa
     return amp * np.exp(-r2 / (width * width)) * np.exp(1j * k * (x - centre[0]))
 
 
+def sparse_block_source(n: Sequence[int], side: int, seed: int):
+    """Seeded source that is non-zero on few voxels of a large grid: a cube of side^3
+    voxels (clipped to the grid) at a seeded position with standard normal complex
+    values, plus the grid's two opposite corner voxels (the longest offsets the
+    embedding holds).  Returns (idx (S, 3) int64, values (S,) complex128)."""
+    rng = np.random.default_rng(seed)
+    n = tuple(int(v) for v in n)
+    lo = [int(rng.integers(0, max(1, n[a] - side + 1))) for a in range(3)]
+    ax = [np.arange(lo[a], min(n[a], lo[a] + side)) for a in range(3)]
+    block = np.stack(np.meshgrid(*ax, indexing="ij"), axis=-1).reshape(-1, 3)
+    corners = np.array([[0, 0, 0], [n[0] - 1, n[1] - 1, n[2] - 1]])
+    idx = np.unique(np.concatenate([block, corners]), axis=0).astype(np.int64)
+    vals = rng.standard_normal(len(idx)) + 1j * rng.standard_normal(len(idx))
+    return idx, vals
+
+
+def sample_targets(n: Sequence[int], idx: np.ndarray, count: int, seed: int) -> np.ndarray:
+    """Seeded target voxels: `count` uniform over the grid, the 8 corners, and up to 256
+    voxels among and next to the given source voxels.  (T, 3) int64."""
+    rng = np.random.default_rng(seed)
+    n = tuple(int(v) for v in n)
+    uni = np.stack([rng.integers(0, n[a], size=count) for a in range(3)], axis=1)
+    corners = np.array([(x, y, z) for x in (0, n[0] - 1) for y in (0, n[1] - 1) for z in (0, n[2] - 1)])
+    pick = idx[rng.choice(len(idx), size=min(256, len(idx)), replace=False)]
+    near = np.clip(pick + rng.integers(-2, 3, size=pick.shape), 0, np.array(n) - 1)
+    return np.concatenate([uni, corners, near]).astype(np.int64)
+
+
 # --------------------------------------------------------------------------------------
 # Workload recipes (the synthetic bowl-transducer configurations).
 # --------------------------------------------------------------------------------------

@@ -96,6 +96,11 @@ def _load():
         fn = getattr(lib, name)
         fn.restype = res
         fn.argtypes = args
+    # the library must have been built from the sources in this tree
+    from . import build as _build
+    built = lib.vp_version().decode().rsplit(" ", 1)[-1]
+    if built not in (_build.source_digest(False), _build.source_digest(True)):
+        raise ImportError(f"libvp.so was built from other sources (digest {built}); run __graft_entry__.build()")
     return lib
 
 

@@ -199,6 +199,30 @@ def test_restriction_tiles_and_direct_form(vp, case, quadratic):
     assert rel_l2(host(out), ref) <= 1e-6
 
 
+def test_quadratic_restriction_matches_plain_positions_up_to_ties(vp):
+    """Against the oracle's plain FP64 target positions: every voxel equals the
+    quadratic interpolant for one valid stencil choice per axis (two equally near
+    stencils at a half-integer position, one elsewhere).  Spacing ratio 2/3 with even
+    voxel counts, as between the nested 192^3 and 256^3 grids: every third target sits
+    on a half-integer on each axis."""
+    c = (0.06, 0.0, 0.0)
+    src = synth.centred_grid((24, 24, 24), 3.0e-4, c)
+    dst = synth.centred_grid((28, 28, 28), 2.0e-4, c)
+    ties = interp.tie_axes(src, dst)
+    assert all(t.sum() >= 9 for t in ties)
+    f = synth.random_field(src.n, seed=21)
+    out = torch.empty(dst.n, dtype=torch.complex64, device="cuda")
+    vp.vp_restrict_to_nested_box(src, dev(f), dst, out, quadratic=True)
+    got = host(out)
+    err = np.full(dst.n, np.inf)
+    for tx in ("down", "up"):
+        for ty in ("down", "up"):
+            for tz in ("down", "up"):
+                ref = interp.restrict_quadratic(f, src, dst, positions="float", tie=(tx, ty, tz))
+                err = np.minimum(err, np.abs(got - ref))
+    assert np.max(err) <= 2e-6 * np.max(np.abs(f))
+
+
 def test_quadratic_restriction_exact_on_triquadratic_field(vp):
     src = synth.Grid((21, 19, 23), (0.01, -0.003, -0.0032), 3.1e-4)
     dst = synth.centred_grid((30, 27, 33), 1.7e-4, (0.0131, -0.0001, 0.0002))

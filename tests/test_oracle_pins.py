@@ -240,6 +240,80 @@ def test_cascade_scaling_laws():
         assert np.linalg.norm(tb[n] - t ** (n - 1) * v) <= 1e-12 * np.linalg.norm(v) * t ** (n - 1)
 
 
+def test_sparse_sum_equals_the_dense_double_sum():
+    """apply_sparse (targets x listed sources) against apply_bruteforce on the dense
+    field that is zero off the listed voxels, every target voxel of a 9 x 7 x 8 grid."""
+    n = (9, 7, 8)
+    rng = np.random.default_rng(31)
+    src = np.array([[0, 0, 0], [8, 6, 7], [4, 3, 2], [4, 3, 3], [1, 5, 6]])
+    val = rng.standard_normal(5) + 1j * rng.standard_normal(5)
+    f = np.zeros(n, dtype=np.complex128)
+    f[tuple(src.T)] = val
+    h, k = 2.1e-4, physics.wavenumber(3, 1.1e6, synth.WATER)
+    tg = np.indices(n).reshape(3, -1).T
+    got = potential.apply_sparse(src, val, h, k, tg)
+    want = potential.apply_bruteforce(f, h, k).reshape(-1)
+    assert np.max(np.abs(got - want)) <= 1e-13 * np.max(np.abs(want))
+
+
+def test_nested_run_follows_the_section_6_loop_step_by_step():
+    """Harmonics 2-4 built by hand on three different nested grids with the brute-force
+    double sum of Eq. 3.9 (no FFT): p1 lives on the grid of harmonic 2 and is restricted
+    from there to every later grid; p2 from grid 2; p3 from grid 3.  A loop that
+    restricted p1 from a grid it never lived on, took a lower harmonic unrestricted, or
+    looked up the wrong home grid would not match."""
+    bowl = synth.Bowl(l=0.02, R=0.01, f0=1.0e6, p0=0.5e6)
+    med = synth.WATER
+    grids = {n: synth.focus_grid(bowl, (s, s, s), n, med) for n, s in ((2, 7), (3, 8), (4, 9))}
+    pts = synth.sample_bowl_points(bowl, 200, seed=11)
+    p1 = rayleigh.incident_field(grids[2], pts, bowl, med)
+    got = cascade.nested_run(p1, grids, bowl.f0, med)
+    g2, g3, g4 = grids[2], grids[3], grids[4]
+    k = {n: physics.wavenumber(n, bowl.f0, med) for n in (2, 3, 4)}
+    R = interp.restrict_trilinear
+    p2 = potential.apply_bruteforce(cascade.source_term(2, [p1], bowl.f0, med), g2.h, k[2])
+    p3 = potential.apply_bruteforce(cascade.source_term(3, [R(p1, g2, g3), R(p2, g2, g3)], bowl.f0, med),
+                                    g3.h, k[3])
+    p4 = potential.apply_bruteforce(
+        cascade.source_term(4, [R(p1, g2, g4), R(p2, g2, g4), R(p3, g3, g4)], bowl.f0, med), g4.h, k[4])
+    for n, want in ((2, p2), (3, p3), (4, p4)):
+        assert got[n].shape == want.shape
+        assert np.linalg.norm(got[n] - want) <= 1e-11 * np.linalg.norm(want), n
+    # the pin separates the plausible slips: p1 for harmonic 4 restricted via grid 3
+    slip = potential.apply_bruteforce(
+        cascade.source_term(4, [R(R(p1, g2, g3), g3, g4), R(p2, g2, g4), R(p3, g3, g4)], bowl.f0, med), g4.h, k[4])
+    assert np.linalg.norm(slip - p4) > 1e-6 * np.linalg.norm(p4)
+
+
+def test_quadratic_fixed_positions_match_plain_positions():
+    """The 40-bit fixed-point target positions of the quadratic restriction give, on
+    every axis, the stencil and weights of the plain FP64 positions wherever the
+    position is not a half-integer, and one of the two equally near stencils where it
+    is.  The nested 192^3 -> 256^3 pair (spacing ratio 2/3) has ties on every axis."""
+    w = synth.WORKLOADS["nested3"]()
+    pairs = [(w.steps[0].grid, w.steps[1].grid),
+             (synth.Grid((21, 19, 23), (0.01, -0.003, -0.0032), 3.1e-4),
+              synth.centred_grid((30, 27, 33), 1.7e-4, (0.0131, -0.0001, 0.0002)))]
+    ties_seen = 0
+    for src, dst in pairs:
+        tie_masks = interp.tie_axes(src, dst)
+        for a in range(3):
+            coords = dst.origin[a] + dst.h * np.arange(dst.n[a], dtype=np.float64)
+            T = interp._fixed_positions(src.origin[a], src.h, dst.origin[a], dst.h, dst.n[a])
+            i_f, w_f = interp._axis_quadratic(src.origin[a], src.h, src.n[a], coords, T)
+            i_d, w_d = interp._axis_quadratic(src.origin[a], src.h, src.n[a], coords, None, "down")
+            i_u, w_u = interp._axis_quadratic(src.origin[a], src.h, src.n[a], coords, None, "up")
+            tie = tie_masks[a]
+            ties_seen += int(tie.sum())
+            same_d = np.all(i_f == i_d, axis=1) & np.all(np.abs(w_f - w_d) <= 1e-9, axis=1)
+            same_u = np.all(i_f == i_u, axis=1) & np.all(np.abs(w_f - w_u) <= 1e-9, axis=1)
+            assert np.all(same_d[~tie] & same_u[~tie])
+            assert np.all(same_d[tie] | same_u[tie])
+            # at a tie the two stencils really differ
+            assert np.all(np.any(i_d[tie] != i_u[tie], axis=1))
+    assert ties_seen > 0
+
+
 # ----------------------------------------------------------------------------- incident field
 
 def _on_axis_closed_form(bowl, k, z):
