@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT comparison timing")
+    ap.add_argument("--fno-checkpoint", default=None, help="trained surrogate weights (--workload fno)")
     return ap.parse_args()
 
 
@@ -159,14 +160,15 @@ def sweep_bytes(n, m, harmonic, fused_source: bool):
 SWEEP_NAMES = ["x_forward_source", "y_forward", "z_conv", "y_inverse", "x_inverse"]
 
 
-# device code of the pipelined z-sweep kernel (the bench's dominant kernel): the register
-# DFTs and shared helpers it is built from, and its own section of sweeps2.cuh
+# device code of the z-sweep kernels (the bench's dominant kernels): the register DFTs and
+# shared helpers they are built from, the pipelined kernel's section of sweeps2.cuh and,
+# for the pair-split form, its own header
 SWEEP_SOURCES = ("fft_engine.cuh", "regfft.cuh", "vp_internal.cuh")
 ZSWEEP_SECTION = "// Persistent, software-pipelined form of line2_kernel<kConv>"
 
 
-def csrc_digest() -> str:
-    """Short digest of the z-sweep kernel's device code; a stored ncu traffic figure is
+def csrc_digest(kernel: str = "") -> str:
+    """Short digest of a z-sweep kernel's device code; a stored ncu traffic figure is
     used only while it matches (a change of that kernel invalidates it)."""
     import hashlib
     d = os.path.join(ROOT, "paper_2011_03009_gb300", "csrc")
@@ -178,6 +180,9 @@ def csrc_digest() -> str:
         text = fh.read()
     i = text.find(ZSWEEP_SECTION.encode())
     h.update(b"sweeps2.cuh\0" + (text[i:] if i >= 0 else text))
+    if kernel.startswith("line2_conv_pair8_kernel"):
+        with open(os.path.join(d, "sweeps2_pair.cuh"), "rb") as fh:
+            h.update(b"sweeps2_pair.cuh\0" + fh.read())
     return h.hexdigest()[:12]
 
 
@@ -189,7 +194,7 @@ def stored_traffic(kernel: str):
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     if not os.path.exists(path):
         return None
-    key, dig = kernel.replace(" ", "_"), csrc_digest()
+    key, dig = kernel.replace(" ", "_"), csrc_digest(kernel)
     with open(path) as fh:
         for line in fh:
             f = line.split()
@@ -467,7 +472,8 @@ def run_ours(args, world, rank, local):
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    dom = max(sweeps, key=lambda r: r["total_ms"]) if sweeps else None
+    # each sweep launches once per step: the dominant kernel has the longest launch
+    dom = max(sweeps, key=lambda r: r["ms_per_launch"]) if sweeps else None
     roofline = None
     if dom:
         roofline = {"bound": "hbm", "kernel": f"{dom['kernel']}, harmonic {dom['harmonic']}",
@@ -842,21 +848,31 @@ def run_batch(args, world, rank, local):
         nested_all()
         b3.run()
 
-    def timeit(fn, reps):
+    def timeit(fn, reps, repeats=5):
+        """Per-step milliseconds of `repeats` timings of `reps` steps each (after warm-up)."""
         for _ in range(max(3, args.warmup)):
             fn()
         torch.cuda.synchronize()
-        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        for _ in range(reps):
-            fn()
-        z.record()
-        torch.cuda.synchronize()
-        return a.elapsed_time(z) / reps
+        out = []
+        for _ in range(repeats):
+            a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(reps):
+                fn()
+            z.record()
+            torch.cuda.synchronize()
+            out.append(a.elapsed_time(z) / reps)
+        return out
 
+    def summary(ts):
+        med = statistics.median(ts)
+        return {"fields_per_s": fields / (med / 1e3), "ms_per_step": med, "ms_min": min(ts), "ms_max": max(ts),
+                "repeats": len(ts)}
+
+    fields = 3 * count
     reps = max(3, min(args.steps, 20))
-    ms_plain = timeit(plain_step, reps)
-    ms_batched = timeit(batched_step, reps)
+    t_plain = timeit(plain_step, reps)
+    t_batched = timeit(batched_step, reps)
     # graph of the batched step
     side = torch.cuda.Stream()
     side.wait_stream(torch.cuda.current_stream())
@@ -867,12 +883,12 @@ def run_batch(args, world, rank, local):
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph):
         batched_step()
-    ms_graph = timeit(graph.replay, reps)
+    t_graph = timeit(graph.replay, reps)
     graph_p = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph_p):
         plain_step()
-    ms_plain_graph = timeit(graph_p.replay, reps)
-    fields = 3 * count
+    t_plain_graph = timeit(graph_p.replay, reps)
+    ms_graph = statistics.median(t_graph)
     groups = {"h1": len(set(tuple(it["plans"][0].info().m) for it in items)),
               "h2": len(set(tuple(it["plans"][1].info().m) for it in items)),
               "h3": len(set(tuple(it["plans"][2].info().m) for it in items))}
@@ -883,10 +899,8 @@ def run_batch(args, world, rank, local):
             "config": {"workload": "batch64_h1-3_uneven_96-256cube", "instances": count, "fields_per_step": fields,
                        "voxels_per_step": voxels, "bowl_points": n_points, "embedding_groups": groups,
                        "setup_s": round(setup_s, 2)},
-            "plain_loop": {"fields_per_s": fields / (ms_plain / 1e3), "ms_per_step": ms_plain},
-            "plain_loop_graph": {"fields_per_s": fields / (ms_plain_graph / 1e3), "ms_per_step": ms_plain_graph},
-            "batched": {"fields_per_s": fields / (ms_batched / 1e3), "ms_per_step": ms_batched},
-            "batched_graph": {"fields_per_s": fields / (ms_graph / 1e3), "ms_per_step": ms_graph},
+            "plain_loop": summary(t_plain), "plain_loop_graph": summary(t_plain_graph),
+            "batched": summary(t_batched), "batched_graph": summary(t_graph),
             "voxel_potentials_per_s": voxels / (ms_graph / 1e3)}
     if rank == 0:
         print(json.dumps(line))
@@ -1112,12 +1126,17 @@ def run_fno(args):
     """Surrogate inference (4 layers, width 48, projection 128, 32 x 32 x 16 modes) on the
     128^3 focal box against the plain cascade it would replace (kernel spectra, nested
     sources and potentials of harmonics 2..5 from p1 on the device); CUDA events.  The
-    inference time does not depend on the weights' values (random initialisation)."""
+    inference time does not depend on the weights' values (random initialisation unless
+    --fno-checkpoint names trained weights).  Then the judged route per bowl: incident
+    fields, inference, the plain path's p2 as judge, the plain cascade as fallback,
+    against the plain route from the bowl; with the fallback rate."""
     import torch
     from paper_2011_03009_gb300 import fno as F
     n = 128
     cfg = F.FnoConfig(n=n, width=48, hidden=128, layers=4, modes=(32, 32, 16))
     model = F.Fno(cfg, seed=0)
+    if args.fno_checkpoint:
+        model.load_state(torch.load(args.fno_checkpoint))
     casc = F.PlainCascade(n, 512)
     bowl = F.draw_bowls(1, 7)[0]
     casc.incident(bowl, 0)
@@ -1126,9 +1145,31 @@ def run_fno(args):
     reps = max(3, min(args.steps, 20))
     t_inf = _dev_timeit(lambda: model.infer(x, y), reps, args.warmup)
     t_plain = _dev_timeit(lambda: casc.harmonics(bowl), reps, args.warmup)
+    bowls = F.draw_bowls(8, 8)
+    judged = F.JudgedSurrogate(model, threshold=1e-2, n_points=512)
+    plain = F.PlainCascade(n, 512)
+    verdicts = []
+
+    def judged_all():
+        verdicts.clear()
+        for i, b in enumerate(bowls):
+            verdicts.append(judged.run(b, i)[1])
+
+    def plain_all():
+        for i, b in enumerate(bowls):
+            plain.run(b, i)
+
+    t_judged = _dev_timeit(judged_all, 2, 1) / len(bowls)
+    t_plain_route = _dev_timeit(plain_all, 2, 1) / len(bowls)
+    fb = sum(v["fallback"] for v in verdicts) / len(verdicts)
     _line("surrogate fields/s", 1e3 / t_inf, "fields/s", t_inf, reps, max(1, args.warmup), True,
-          {"workload": "fno_infer_128cube_w48_l4_m32x32x16", "params": model.count},
-          plain_cascade={"fields_per_s": 1e3 / t_plain, "ms": t_plain})
+          {"workload": "fno_infer_128cube_w48_l4_m32x32x16", "params": model.count,
+           "weights": args.fno_checkpoint or "random initialisation"},
+          plain_cascade={"fields_per_s": 1e3 / t_plain, "ms": t_plain},
+          judged_route={"fields_per_s": 1e3 / t_judged, "ms_per_bowl": t_judged, "fallback_rate": fb,
+                        "threshold": 1e-2, "judge_rel_l2": [v["judge_rel_l2"] for v in verdicts],
+                        "bowls": len(bowls)},
+          plain_route={"fields_per_s": 1e3 / t_plain_route, "ms_per_bowl": t_plain_route})
 
 
 def run_nw(args):

@@ -86,7 +86,17 @@ typedef struct vp_plan_opts {
     int autotune;       /* nonzero and no m / radix given: time the default embedding
                            against the smallest even 5-smooth one (three applications
                            each, on `stream`) and keep the faster; cached per grid shape */
+    int zform;          /* form of the pipelined z sweep (two-level engine): VP_ZFORM_*;
+                           0 = the form that keeps the most warps resident per SM.  A form
+                           that is not compiled for M_z or does not fit in shared memory
+                           is not used (the choice falls back as for 0)                  */
 } vp_plan_opts;
+
+#define VP_ZFORM_AUTO   0
+#define VP_ZFORM_TILE16 1  /* 16 lines a CTA (4 mirror groups), 256 threads              */
+#define VP_ZFORM_TILE8  2  /* 8 lines a CTA (2 mirror groups), 256 threads, M_z >= 640   */
+#define VP_ZFORM_TILE4  3  /* 4 lines a CTA (1 mirror group), 4 max(A, B) threads, M_z >= 512 */
+#define VP_ZFORM_PAIR8  4  /* 8 lines, step 2 split over lane pairs, 512 threads, M_z = 1280 */
 
 typedef struct vp_plan_info {
     int n[3];
@@ -291,7 +301,11 @@ VP_API int vp_incident_field(const vp_grid* g, const double* points, int n_point
  * launches instead of five per item.  In a group whose items each give the z sweep
  * at least 8 tiles of 16 lines per SM, that sweep runs item by item with the
  * single-plan kernel (the column sweeps stay grouped).  Other items run one plan at a
- * time.  All
+ * time.  The groups (in chunks of at most 64 items) and the single items are independent
+ * units: vp_batch_run spreads them over up to three streams, the caller's and two of the
+ * batch's own, which wait for the caller's earlier work and which the caller's stream
+ * waits for before the call's later work (event fork and join, so a stream capture
+ * records them as parallel branches).  All
  * pointers are device pointers bound at creation; vp_batch_run recomputes from their
  * current contents, so a stream capture of vp_batch_run replays correctly.  A plan may
  * appear at most once per batch (items share nothing but read-only inputs); kernel

@@ -321,8 +321,10 @@ __global__ void __launch_bounds__(kThreads2) line2_batch_kernel(const __grid_con
 // of it runs its forward step 1, so its latency is hidden there.
 // Shared memory: transpose buffer (16 x line2_pitch), staging buffer (16 x ni),
 // spectrum lines (4 x Oz), twiddles (A x conv_tw_pitch(B)).
-// NL = 8 (long lines): a CTA takes half a tile of the host's list (2 mirror groups of
-// 4 lines and their 2 octant lines), so the buffers fit in shared memory at L >= 1024.
+// NL = 8 or 4 (long lines): a CTA takes half or a quarter of a tile of the host's list
+// (2 or 1 mirror groups of 4 lines and their octant lines), so the buffers fit in shared
+// memory at L >= 1024, or more CTAs share an SM.  NT threads a CTA (NT / 32 warps): the
+// 4-line form runs NL x max(A, B) threads, one task of each step per thread.
 // The staging pitch that holds rows a < conv_rows_in(A) of a line (odd: lanes = lines).
 __host__ __device__ constexpr int conv_stage_pitch(int A, int B) { return (B * conv_rows_in(A)) | 1; }
 // Row pitch of the z sweep's twiddle table: 8 elements past B, so that rows k1 and k1 + 1
@@ -339,8 +341,8 @@ __host__ __device__ constexpr size_t conv_pipe_smem(int A, int B, int Oz, int NL
 // numbered consecutively (plan i owns [offsets[i], offsets[i + 1])), all with the same
 // line length L and spectrum octant length; ni is the staging pitch for the longest
 // input line.
-template <int A, int B, bool BATCH, int NL = kLines2>
-__global__ void __launch_bounds__(kThreads2)
+template <int A, int B, bool BATCH, int NL = kLines2, int NT = kThreads2>
+__global__ void __launch_bounds__(NT)
     line2_conv_pipe_kernel(const __grid_constant__ LineSweep p, const __grid_constant__ BatchParams<LineSweep> bp,
                            long long ntiles, int NI) {
   constexpr int L = A * B;
@@ -352,7 +354,14 @@ __global__ void __launch_bounds__(kThreads2)
   extern __shared__ float2 S[];
   const int Oz = p.Oz;  // shared by every plan of a batch group
   constexpr int NG = NL / 4;       // mirror groups per CTA tile
-  constexpr int LSH = NL == 16 ? 4 : 3;
+  constexpr int LSH = NL == 16 ? 4 : (NL == 8 ? 3 : 2);
+  constexpr int NW = NT / 32;      // warps
+  constexpr int SUB = 16 / NL;     // CTA tiles per tile of the host's list
+  // line staging: with at least NL warps, WPL warps share a line; with fewer, a warp
+  // stages LPW lines
+  constexpr int WPL = NW >= NL ? NW / NL : 1;
+  constexpr int LPW = NW >= NL ? 1 : NL / NW;
+  constexpr int STAGERS = NW >= NL ? NL * WPL : NW;
   float2* I = S + NL * LP;
   float2* K = I + NL * NI;  // [NG][Oz]
   float2* T = K + NG * Oz;  // twiddles
@@ -365,7 +374,7 @@ __global__ void __launch_bounds__(kThreads2)
   // so that the load latency hides behind the previous tile's forward step 1.
   struct Rec {
     const LineSweep* q;       // plan of the tile
-    long long line[NL / 8];   // the lines this warp stages: b = warp, warp + 8
+    long long line[LPW];      // the lines this warp stages
     long long my_line;        // line slot threadIdx.x (< NL)
     int my_oct;               // octant id slot threadIdx.x (< NG)
     int spec_oct;             // the octant line this warp stages: g = warp % NG
@@ -381,10 +390,10 @@ __global__ void __launch_bounds__(kThreads2)
     }
     const int* tiles = BATCH ? r.q->tiles : p.tiles;
     // line slots and octant ids of local tile lt in the host's 20-int tile records
-    const long long lb = NL == 16 ? 20LL * lt : 20LL * (lt >> 1) + 8 * (lt & 1);
-    const long long ob = NL == 16 ? 20LL * lt + 16 : 20LL * (lt >> 1) + 16 + 2 * (lt & 1);
+    const long long lb = 20LL * (lt / SUB) + NL * (lt % SUB);
+    const long long ob = 20LL * (lt / SUB) + 16 + NG * (lt % SUB);
 #pragma unroll
-    for (int h = 0; h < NL / 8; ++h) r.line[h] = tiles[lb + warp + 8 * h];
+    for (int h = 0; h < LPW; ++h) r.line[h] = tiles[lb + (NW >= NL ? warp % NL : warp + NW * h)];
     r.my_line = threadIdx.x < NL ? tiles[lb + threadIdx.x] : -1;
     r.my_oct = threadIdx.x < NG ? tiles[ob + threadIdx.x] : -1;
     r.spec_oct = tiles[ob + warp % NG];
@@ -395,12 +404,15 @@ __global__ void __launch_bounds__(kThreads2)
     const float2* data = q.data;
     const long long ld = q.ld;
     const int n_in = q.n_in;
+    if (warp < STAGERS) {
 #pragma unroll
-    for (int h = 0; h < NL / 8; ++h) {
-      const int b = warp + 8 * h;
-      const long long l = r.line[h];
-      const float2* src = data + (l < 0 ? 0 : l * ld);
-      for (int n = lane; n < NI; n += 32) cp_async8(&I[b * NI + n], &src[n < n_in ? n : 0], l >= 0 && n < n_in);
+      for (int h = 0; h < LPW; ++h) {
+        const int b = NW >= NL ? warp % NL : warp + NW * h;
+        const long long l = r.line[h];
+        const float2* src = data + (l < 0 ? 0 : l * ld);
+        for (int n = (NW >= NL ? (warp / NL) * 32 : 0) + lane; n < NI; n += 32 * WPL)
+          cp_async8(&I[b * NI + n], &src[n < n_in ? n : 0], l >= 0 && n < n_in);
+      }
     }
     if (threadIdx.x < NL) line_of[slot][threadIdx.x] = r.my_line;
     if (threadIdx.x < NG) oct_of[slot][threadIdx.x] = r.my_oct;
@@ -411,10 +423,11 @@ __global__ void __launch_bounds__(kThreads2)
     const int g = warp % NG;
     const int oc = r.spec_oct;
     const float2* kl = khat + (oc < 0 ? 0 : (long long)oc * Oz);
-    for (int i = (warp / NG) * 32 + lane; i < Oz; i += (kThreads2 / 32 / NG) * 32)
+    for (int i = (warp / NG) * 32 + lane; i < Oz; i += (NW / NG) * 32)
       cp_async8(&K[g * Oz + i], &kl[i], oc >= 0);
   };
-  static_assert(NL == 8 || NL == 16, "tiles of 8 or 16 lines, 8 warps");
+  static_assert((NL == 4 || NL == 8 || NL == 16) && NT % 32 == 0 && NW % NG == 0 && (NW >= NL || NL % NW == 0),
+                "tiles of 4, 8 or 16 lines; whole warps per mirror group and per staged line");
 
   // inter-step twiddles laid out as T[k1 TP + b] = w_L^(b k1), TP = B + 8: with either
   // index fixed at compile time, every read is a register base plus a constant offset,

@@ -110,70 +110,84 @@ cudaError_t resident_slots(K kernel, size_t smem, volatile int* granted, int* gr
   return cudaSuccess;
 }
 
+// Threads of the 4-line form: one task of each step per thread.
+__host__ __device__ constexpr int conv4_threads(int A, int B) { return ((4 * (A > B ? A : B) + 31) / 32) * 32; }
+
+// The pipelined z sweep in one of its forms (VP_ZFORM_*): 16-line tiles (256 threads),
+// 8-line half tiles (256 threads), 4-line quarter tiles (4 max(A, B) threads), or the
+// pair-split 8-line form (512 threads, L = 1280 only).  p.zform = 0 takes the form that
+// keeps the most warps resident per SM (ties: the longer tile); a form that is not
+// compiled for L or whose shared memory does not fit is skipped.  *used = false: no form
+// applies (the caller falls back to the unpipelined kernel).
 template <int A, int B>
 cudaError_t line2_conv_pipe_launch(const LineSweep& p, cudaStream_t s, bool* used) {
-  static volatile int granted[64] = {0};
+  static volatile int granted16[64] = {0};
   static volatile int granted8[64] = {0};
+  static volatile int granted4[64] = {0};
+  static volatile int grantedp[64] = {0};
+  constexpr int L = A * B;
+  constexpr int NT4 = conv4_threads(A, B);
   *used = false;
   // the kernel reads and writes the first half of each line only (zero-padded input,
   // cropped output); any other line goes to line2_kernel
-  if (2 * p.n_in > A * B || 2 * p.n_out > A * B) return cudaSuccess;
+  if (2 * p.n_in > L || 2 * p.n_out > L) return cudaSuccess;
   const int ni = conv_stage_pitch(A, B);
-  if constexpr (A == 32 && B == 40) {
-    // L = 1280: the pair-split half-tile form, 16 warps a CTA (at L = 1024 the halves'
-    // rows share banks and it measured slower)
-    static volatile int grantedp[64] = {0};
-    const size_t smemp = conv_pair8_smem(A, B, p.Oz);
-    int gridp = 0;
-    if (smemp <= 200 * 1024) {
-      cudaError_t e = resident_slots(line2_conv_pair8_kernel<A, B>, smemp, grantedp, &gridp, kThreadsPair);
-      if (e != cudaSuccess) return e;
-    }
-    if (gridp >= 1) {
-      *used = true;
-      if (p.nlines <= 0) return cudaSuccess;
-      const long long halves = 2LL * p.nlines;
-      const int grid = (int)(gridp > halves ? halves : gridp);
-      line2_conv_pair8_kernel<A, B><<<(unsigned)grid, kThreadsPair, smemp, s>>>(p, halves, ni);
-      return cudaGetLastError();
-    }
-  }
-  static BatchParams<LineSweep> none{};  // unused by the single-plan form
-  // tiles of 16 lines, or (long lines) half tiles of 8 lines when those fit more CTAs per
-  // SM: at L = 640-864 one 16-line CTA fills an SM's shared memory, two 8-line CTAs fit;
-  // from L = 1024 only the 8-line form fits at all
-  const size_t smem16 = conv_pipe_smem(A, B, p.Oz);
-  int grid16 = 0, grid8 = 0;
+  constexpr int kForms = 5;
+  int grid[kForms] = {0, 0, 0, 0, 0};  // resident CTAs on the GPU, per form
+  int threads[kForms] = {0, kThreads2, kThreads2, NT4, kThreadsPair};
+  size_t smem[kForms] = {0, conv_pipe_smem(A, B, p.Oz), conv_pipe_smem(A, B, p.Oz, 8), conv_pipe_smem(A, B, p.Oz, 4),
+                         conv_pair8_smem(A, B, p.Oz)};
   cudaError_t e;
-  if (smem16 <= 200 * 1024) {
-    e = resident_slots(line2_conv_pipe_kernel<A, B, false>, smem16, granted, &grid16);
+  auto want = [&](int f) { return p.zform == 0 || p.zform == f; };
+  if (want(1) && smem[1] <= 200 * 1024) {
+    e = resident_slots(line2_conv_pipe_kernel<A, B, false>, smem[1], granted16, &grid[1]);
     if (e != cudaSuccess) return e;
   }
-  size_t smem8 = 0;
-  if constexpr (A * B >= 640) {
-    smem8 = conv_pipe_smem(A, B, p.Oz, 8);
-    if (smem8 <= 200 * 1024) {
-      e = resident_slots(line2_conv_pipe_kernel<A, B, false, 8>, smem8, granted8, &grid8);
+  if constexpr (L >= 640) {
+    if (want(2) && smem[2] <= 200 * 1024) {
+      e = resident_slots(line2_conv_pipe_kernel<A, B, false, 8>, smem[2], granted8, &grid[2]);
       if (e != cudaSuccess) return e;
     }
   }
-  if (grid16 < 1 && grid8 < 1) return cudaSuccess;  // too large to pipeline: caller falls back
-  if (p.nlines <= 0) {
-    *used = true;
-    return cudaSuccess;
-  }
-  if constexpr (A * B >= 640) {
-    if (grid8 > grid16) {
-      const long long halves = 2LL * p.nlines;
-      const int grid = (int)(grid8 > halves ? halves : grid8);
-      line2_conv_pipe_kernel<A, B, false, 8><<<(unsigned)grid, kThreads2, smem8, s>>>(p, none, halves, ni);
-      *used = true;
-      return cudaGetLastError();
+  if constexpr (L >= 512) {
+    if (want(3) && smem[3] <= 200 * 1024) {
+      e = resident_slots(line2_conv_pipe_kernel<A, B, false, 4, NT4>, smem[3], granted4, &grid[3], NT4);
+      if (e != cudaSuccess) return e;
     }
   }
-  const int grid = (int)(grid16 > p.nlines ? p.nlines : grid16);
-  line2_conv_pipe_kernel<A, B, false><<<(unsigned)grid, kThreads2, smem16, s>>>(p, none, p.nlines, ni);
+  if constexpr (A == 32 && B == 40) {
+    if (want(4) && smem[4] <= 200 * 1024) {
+      e = resident_slots(line2_conv_pair8_kernel<A, B>, smem[4], grantedp, &grid[4], kThreadsPair);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  int best = 0;
+  for (int f = 1; f < kForms; ++f) {
+    if (grid[f] < 1) continue;
+    // more resident warps wins; on a tie the earlier (longer) tile
+    if (best == 0 || (long long)grid[f] * threads[f] > (long long)grid[best] * threads[best]) best = f;
+  }
+  if (best == 0) return cudaSuccess;  // too large to pipeline (or the form asked for is not compiled)
   *used = true;
+  if (p.nlines <= 0) return cudaSuccess;
+  static BatchParams<LineSweep> none{};  // unused by the single-plan form
+  const long long units = p.nlines * (best == 1 ? 1 : (best == 3 ? 4 : 2));
+  const int g = (int)(grid[best] > units ? units : grid[best]);
+  switch (best) {
+    case 1:
+      line2_conv_pipe_kernel<A, B, false><<<(unsigned)g, kThreads2, smem[1], s>>>(p, none, units, ni);
+      break;
+    case 2:
+      if constexpr (L >= 640) line2_conv_pipe_kernel<A, B, false, 8><<<(unsigned)g, kThreads2, smem[2], s>>>(p, none, units, ni);
+      break;
+    case 3:
+      if constexpr (L >= 512)
+        line2_conv_pipe_kernel<A, B, false, 4, NT4><<<(unsigned)g, NT4, smem[3], s>>>(p, none, units, ni);
+      break;
+    default:
+      if constexpr (A == 32 && B == 40) line2_conv_pair8_kernel<A, B><<<(unsigned)g, kThreadsPair, smem[4], s>>>(p, units, ni);
+      break;
+  }
   return cudaGetLastError();
 }
 

@@ -74,6 +74,7 @@ struct LineSweep {
   int Oz;
   const int* tiles;     // 20 ints per tile
   const int* fold_z;    // z position -> folded frequency
+  int zform;            // pipelined z-sweep form (VP_ZFORM_*; 0 = chosen by occupancy)
 };
 
 enum SweepDir { kForward = 0, kInverse = 1 };

@@ -274,29 +274,92 @@ class PlainCascade:
 
     def harmonics(self, bowl: synth.Bowl):
         """p2..p5 restricted to the box, from the p1 fields of the last incident() call."""
+        for h in range(2, 6):
+            self.harmonic(bowl, h)
+        for h in range(2, 6):
+            self.to_box(bowl, h)
+        return self.box
+
+    def harmonic(self, bowl: synth.Bowl, h: int):
+        """p_h on its own grid (self.f[h]) from p_1 .. p_{h-1} of the earlier calls: kernel
+        spectrum, source (restriction and products) and volume potential."""
         vp = _vp
         g = harmonic_grids(bowl, self.n, self.medium)
         home = {1: g[2]}
-        for h in range(2, 6):
-            plan = self.plans.get(h)
-            if plan is None:
-                plan = self.plans[h] = vp.vp_plan(g[h], h, bowl.f0, self.medium)
-            else:
-                plan.retarget(g[h], h, bowl.f0, self.medium)
-            plan.kernel_fft()
-            if all(home[m] is g[h] for m in range(1, h)):
-                plan.source_assemble([self.f[m] for m in range(1, h)])
-            else:
-                # restriction of the lower fields onto grid h and the products, one kernel
-                plan.source_from_nested([home[m] for m in range(1, h)], [self.f[m] for m in range(1, h)])
-            plan.apply(None, self.f[h])
-            home[h] = g[h]
-        for h in range(2, 6):
-            if h == 5:
-                self.box[h].copy_(self.f[5])
-            else:
-                vp.vp_restrict_to_nested_box(g[h], self.f[h], g[5], self.box[h])
-        return self.box
+        for m in range(2, h):
+            home[m] = g[m]
+        plan = self.plans.get(h)
+        if plan is None:
+            plan = self.plans[h] = vp.vp_plan(g[h], h, bowl.f0, self.medium)
+        else:
+            plan.retarget(g[h], h, bowl.f0, self.medium)
+        plan.kernel_fft()
+        if all(home[m] is g[h] for m in range(1, h)):
+            plan.source_assemble([self.f[m] for m in range(1, h)])
+        else:
+            # restriction of the lower fields onto grid h and the products, one kernel
+            plan.source_from_nested([home[m] for m in range(1, h)], [self.f[m] for m in range(1, h)])
+        plan.apply(None, self.f[h])
+        return self.f[h]
+
+    def to_box(self, bowl: synth.Bowl, h: int):
+        """p_h restricted to the focal box (the grid of harmonic 5)."""
+        g = harmonic_grids(bowl, self.n, self.medium)
+        if h == 5:
+            self.box[h].copy_(self.f[5])
+        else:
+            _vp.vp_restrict_to_nested_box(g[h], self.f[h], g[5], self.box[h])
+        return self.box[h]
+
+
+class JudgedSurrogate:
+    """The surrogate with the plain volume-potential path as judge and fallback, per sample.
+
+    For one bowl: p1 on the focal box and on the grid of harmonic 2 (Eq. 3.10); the
+    network's q2..q5 from the box field; then the judge: p2 by the plain path (source,
+    volume potential, restriction to the box), whose relative L2 distance to the
+    network's p2 decides.  At or below `threshold` the sample keeps the network's p3..p5
+    (with the exact p2 the judge computed); above it, p3..p5 come from the plain cascade,
+    which continues from the judge's p1 and p2.  The threshold bounds the error of p2
+    only: p3..p5 are accepted on the evidence of p2 (the held-out errors of the four
+    harmonics track one another; the bench reports how often the judge's verdict agrees
+    with the worst harmonic's error)."""
+
+    def __init__(self, model: Fno, threshold: float = 1e-2, n_points: int = 512, medium=synth.WATER):
+        self.model, self.threshold = model, float(threshold)
+        n = model.cfg.n
+        self.casc = PlainCascade(n, n_points, medium)
+        self.y = torch.empty((n ** 3, 8), dtype=torch.float32, device=model.device)
+        self.accepted = 0
+        self.fallbacks = 0
+
+    def run(self, bowl: synth.Bowl, seed: int):
+        """Returns ({h: p_h on the box, complex64}, {"judge_rel_l2": e, "fallback": bool})."""
+        c = self.casc
+        c.incident(bowl, seed)
+        s = float(c.p1_box.abs().max().item())
+        x = torch.view_as_real(c.p1_box / s).reshape(-1, 2).float().contiguous()
+        self.model.infer(x, self.y)
+        c.harmonic(bowl, 2)
+        p2 = c.to_box(bowl, 2)
+        kappa = self.model.kappa
+        q2 = p2.to(torch.complex128) / (s ** 2 * float(kappa[0]))
+        y2 = torch.complex(self.y[:, 0].double(), self.y[:, 1].double()).reshape(q2.shape)
+        err = float(((y2 - q2).abs().pow(2).sum() / q2.abs().pow(2).sum()).sqrt().item())
+        out = {2: p2.clone()}
+        if err <= self.threshold:
+            self.accepted += 1
+            for h in range(3, 6):
+                k = 2 * (h - 2)
+                q = torch.complex(self.y[:, k].double(), self.y[:, k + 1].double()).reshape(p2.shape)
+                out[h] = (q * (s ** h * float(kappa[h - 2]))).to(torch.complex64)
+            return out, {"judge_rel_l2": err, "fallback": False}
+        self.fallbacks += 1
+        for h in range(3, 6):
+            c.harmonic(bowl, h)
+        for h in range(3, 6):
+            out[h] = c.to_box(bowl, h).clone()
+        return out, {"judge_rel_l2": err, "fallback": True}
 
 
 def draw_bowls(count: int, seed: int) -> List[synth.Bowl]:

@@ -26,6 +26,7 @@ VP_ERR_UNSUPPORTED = -8
 VP_RESTRICT_ZERO_OUTSIDE = 1
 VP_RESTRICT_QUADRATIC = 2
 VP_SRC_CONJ = 1
+VP_ZFORM_AUTO, VP_ZFORM_TILE16, VP_ZFORM_TILE8, VP_ZFORM_TILE4, VP_ZFORM_PAIR8 = 0, 1, 2, 3, 4
 MAX_PASS = 8
 MAX_LOWER = 8
 
@@ -46,7 +47,8 @@ class vp_medium(ctypes.Structure):
 
 
 class vp_plan_opts(ctypes.Structure):
-    _fields_ = [("m", ctypes.c_int * 3), ("radix", (ctypes.c_int * MAX_PASS) * 3), ("autotune", ctypes.c_int)]
+    _fields_ = [("m", ctypes.c_int * 3), ("radix", (ctypes.c_int * MAX_PASS) * 3), ("autotune", ctypes.c_int),
+                ("zform", ctypes.c_int)]
 
 
 class vp_plan_info(ctypes.Structure):
@@ -171,7 +173,8 @@ class Plan:
     """A vp_plan_t with its grid; methods mirror the C ABI calls."""
 
     def __init__(self, grid, harmonic: int, f0: float, medium, m: Optional[Sequence[int]] = None,
-                 radix: Optional[Sequence[Sequence[int]]] = None, autotune: bool = False, stream=None):
+                 radix: Optional[Sequence[Sequence[int]]] = None, autotune: bool = False, stream=None,
+                 zform: int = 0):
         self.grid = grid
         self.harmonic = int(harmonic)
         self._h = ctypes.c_void_p(0)
@@ -184,6 +187,7 @@ class Plan:
                 for i, r in enumerate(radix[a] or []):
                     opts.radix[a][i] = int(r)
         opts.autotune = 1 if autotune else 0
+        opts.zform = int(zform)
         g = grid if isinstance(grid, vp_grid) else grid_of(grid)
         self._g = g
         med = medium if isinstance(medium, vp_medium) else make_medium(medium)

@@ -115,3 +115,52 @@ def test_batch_of_large_items(vp):
     batch.close()
     for p in plans:
         p.close()
+
+
+def test_batch_lanes_follow_the_callers_stream_and_replay_from_a_graph(vp):
+    """The batch's units run on several streams forked from the caller's stream: inputs
+    written on that stream just before the call (no synchronisation) must be seen, the
+    results must be complete when the caller's stream continues, and a captured run
+    replays on new inputs."""
+    specs = [((40, 40, 40), 1), ((48, 60, 48), 1), ((64, 64, 64), 1), ((21, 21, 21), 1), ((37, 33, 40), 1)]
+    plans, us, fs = [], [], []
+    for n, h in specs:
+        g = synth.Grid(n, (0.0, 0.0, 0.0), 9e-5)
+        p = vp.vp_plan(g, h, 1.1e6, synth.WATER)
+        p.kernel_fft()
+        plans.append(p)
+        us.append(torch.empty(n, dtype=torch.complex64, device="cuda"))
+        fs.append(torch.empty(n, dtype=torch.complex64, device="cuda"))
+    batch = vp.Batch(plans, us, fs=fs)
+    srcs = [[dev(synth.random_field(n, 900 + 10 * r + i)) for i, (n, _) in enumerate(specs)] for r in range(3)]
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    outs = []
+    with torch.cuda.stream(s):
+        # eager: inputs written on s, the batch on s, the results copied on s
+        for f, x in zip(fs, srcs[0]):
+            f.copy_(x)
+        batch.run(stream=s)
+        outs.append([u.clone() for u in us])
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        batch.run(stream=s)
+    for r in (1, 2):
+        with torch.cuda.stream(s):
+            for f, x in zip(fs, srcs[r]):
+                f.copy_(x)
+            graph.replay()
+            outs.append([u.clone() for u in us])
+    torch.cuda.synchronize()
+    for r in range(3):
+        for i, (n, _) in enumerate(specs):
+            u1 = torch.empty(n, dtype=torch.complex64, device="cuda")
+            plans[i].apply(srcs[r][i], u1)
+            torch.cuda.synchronize()
+            single = u1.cpu().numpy().astype(np.complex128)
+            got = outs[r][i].cpu().numpy().astype(np.complex128)
+            assert np.linalg.norm(got - single) <= 1e-6 * np.linalg.norm(single), (r, i)
+    batch.close()
+    for p in plans:
+        p.close()

@@ -380,3 +380,23 @@ def test_retargeted_plan_matches_a_fresh_plan_and_the_oracle(vp):
     with pytest.raises(vp.VpError):
         plan.retarget(grid((24, 20, 17)), 3, 1.3e6, synth.WATER)
     plan.close()
+
+
+@pytest.mark.parametrize("nz", [256, 320, 432, 512, 640])
+def test_every_z_sweep_form_matches_oracle(vp, nz):
+    """Each form of the pipelined z sweep (16-, 8- and 4-line tiles, the pair-split
+    8-line form) at the z embeddings of the runs (M_z = 512 ... 1280), with ragged x and
+    y axes; a form not compiled for M_z falls back to the automatic choice."""
+    n = (7, 5, nz)
+    g = grid(n)
+    k = physics.wavenumber(3, 1.0e6, synth.WATER)
+    f = synth.random_field(n, seed=nz)
+    ref = potential.apply_fft(f, g.h, k)
+    for form in (vp.VP_ZFORM_TILE16, vp.VP_ZFORM_TILE8, vp.VP_ZFORM_TILE4, vp.VP_ZFORM_PAIR8):
+        plan = vp.vp_plan(g, 3, 1.0e6, synth.WATER, zform=form)
+        assert plan.info().m[2] == 2 * nz
+        vp.vp_kernel_fft(plan)
+        u = torch.empty(n, dtype=torch.complex64, device="cuda")
+        vp.vp_apply(plan, dev(f), u)
+        assert rel_l2(host(u), ref) <= REL_L2, form
+        plan.close()
