@@ -301,11 +301,7 @@ VP_API int vp_incident_field(const vp_grid* g, const double* points, int n_point
  * launches instead of five per item.  In a group whose items each give the z sweep
  * at least 8 tiles of 16 lines per SM, that sweep runs item by item with the
  * single-plan kernel (the column sweeps stay grouped).  Other items run one plan at a
- * time.  The groups (in chunks of at most 64 items) and the single items are independent
- * units: vp_batch_run spreads them over up to three streams, the caller's and two of the
- * batch's own, which wait for the caller's earlier work and which the caller's stream
- * waits for before the call's later work (event fork and join, so a stream capture
- * records them as parallel branches).  All
+ * time.  All
  * pointers are device pointers bound at creation; vp_batch_run recomputes from their
  * current contents, so a stream capture of vp_batch_run replays correctly.  A plan may
  * appear at most once per batch (items share nothing but read-only inputs); kernel

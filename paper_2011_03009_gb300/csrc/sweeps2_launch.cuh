@@ -116,7 +116,7 @@ __host__ __device__ constexpr int conv4_threads(int A, int B) { return ((4 * (A 
 // The pipelined z sweep in one of its forms (VP_ZFORM_*): 16-line tiles (256 threads),
 // 8-line half tiles (256 threads), 4-line quarter tiles (4 max(A, B) threads), or the
 // pair-split 8-line form (512 threads, L = 1280 only).  p.zform = 0 takes the form that
-// keeps the most warps resident per SM (ties: the longer tile); a form that is not
+// keeps the most warps resident per SM (ties: the shorter tile); a form that is not
 // compiled for L or whose shared memory does not fit is skipped.  *used = false: no form
 // applies (the caller falls back to the unpipelined kernel).
 template <int A, int B>
@@ -164,8 +164,9 @@ cudaError_t line2_conv_pipe_launch(const LineSweep& p, cudaStream_t s, bool* use
   int best = 0;
   for (int f = 1; f < kForms; ++f) {
     if (grid[f] < 1) continue;
-    // more resident warps wins; on a tie the earlier (longer) tile
-    if (best == 0 || (long long)grid[f] * threads[f] > (long long)grid[best] * threads[best]) best = f;
+    // more resident warps wins; on a tie the later (shorter) tile, which measured faster
+    // at L = 640-864 (e.g. 2.31 against 2.49 ms at L = 864 on 432^3)
+    if (best == 0 || (long long)grid[f] * threads[f] >= (long long)grid[best] * threads[best]) best = f;
   }
   if (best == 0) return cudaSuccess;  // too large to pipeline (or the form asked for is not compiled)
   *used = true;

@@ -465,20 +465,6 @@ struct vp_batch_s {
   std::vector<void*> u;
   std::vector<BatchGroup> groups;
   std::vector<int> singles;  // items evaluated one plan at a time
-  // The work units (each chunk of each group, each single item) are independent: they run
-  // on up to kBatchLanes streams at once.  Lane 0 is the caller's stream; lanes 1.. are
-  // streams of the batch, forked from the caller's stream and joined back to it by events,
-  // so a stream capture of vp_batch_run records them as parallel branches.
-  std::vector<cudaStream_t> side;   // lanes 1 .. K-1
-  std::vector<cudaEvent_t> joined;  // one per side lane
-  cudaEvent_t fork = nullptr;
-  std::vector<int> chunk_lane;      // lane of each chunk, groups and chunks in order
-  std::vector<int> single_lane;     // lane of each single item
-  ~vp_batch_s() {
-    for (cudaEvent_t e : joined) cudaEventDestroy(e);
-    for (cudaStream_t t : side) cudaStreamDestroy(t);
-    if (fork) cudaEventDestroy(fork);
-  }
 };
 
 namespace {
@@ -536,51 +522,6 @@ int build_group(vp_batch_s* b, BatchGroup& g) {
 }
 
 int autotune_m(const vp_grid* g, double f0, const vp_medium* med, cudaStream_t s, int* best_m);
-
-constexpr int kBatchLanes = 3;
-
-// Spread the batch's units over the lanes, longest first onto the least loaded lane
-// (cost: embedding voxels of the unit's items), and create the lanes' streams and events.
-int assign_lanes(vp_batch_s* b) {
-  struct Unit {
-    double cost;
-    int kind, index;  // kind 0: chunk (index into chunk_lane), 1: single
-  };
-  std::vector<Unit> units;
-  int ci = 0;
-  for (auto& g : b->groups)
-    for (auto& ch : g.chunks) {
-      double c = 0;
-      for (int j = 0; j < ch->line.count; ++j) c += (double)g.m[0] * g.m[1] * g.m[2];
-      units.push_back({c, 0, ci++});
-    }
-  b->chunk_lane.assign(ci, 0);
-  for (size_t k = 0; k < b->singles.size(); ++k) {
-    const vp_plan_s* p = b->plans[b->singles[k]];
-    units.push_back({(double)p->m[0] * p->m[1] * p->m[2], 1, (int)k});
-  }
-  b->single_lane.assign(b->singles.size(), 0);
-  const int lanes = std::min<int>(kBatchLanes, (int)units.size());
-  std::stable_sort(units.begin(), units.end(), [](const Unit& x, const Unit& y) { return x.cost > y.cost; });
-  std::vector<double> load(std::max(1, lanes), 0.0);
-  for (const Unit& u : units) {
-    const int l = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-    load[l] += u.cost;
-    (u.kind == 0 ? b->chunk_lane : b->single_lane)[u.index] = l;
-  }
-  if (lanes > 1) {
-    if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) return VP_ERR_CUDA;
-    for (int l = 1; l < lanes; ++l) {
-      cudaStream_t t = nullptr;
-      cudaEvent_t e = nullptr;
-      if (cudaStreamCreateWithFlags(&t, cudaStreamNonBlocking) != cudaSuccess) return VP_ERR_CUDA;
-      b->side.push_back(t);
-      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return VP_ERR_CUDA;
-      b->joined.push_back(e);
-    }
-  }
-  return VP_OK;
-}
 
 }  // namespace
 
@@ -1139,11 +1080,6 @@ VP_API int vp_batch_create(int count, const vp_plan_t* plans, const void* const*
       return st;
     }
   }
-  const int st = assign_lanes(b);
-  if (st != VP_OK) {
-    free_batch(b);
-    return st;
-  }
   *out = b;
   return VP_OK;
 }
@@ -1153,52 +1089,35 @@ VP_API int vp_batch_run(vp_batch_t b, vp_stream_t stream) {
   for (int i = 0; i < b->count; ++i)
     if (!b->plans[i]->khat_ready || b->plans[i]->generation != b->generation[i]) return VP_ERR_STATE;
   cudaStream_t s = (cudaStream_t)stream;
-  // fork: every side lane waits for the work the caller queued before this call
-  if (!b->side.empty()) {
-    VP_TRY_CUDA(cudaEventRecord(b->fork, s));
-    for (cudaStream_t t : b->side) VP_TRY_CUDA(cudaStreamWaitEvent(t, b->fork, 0));
-  }
-  auto lane = [&](int l) { return l == 0 ? s : b->side[l - 1]; };
-  int st = VP_OK;
-  int ci = 0;
   for (auto& g : b->groups) {
     for (auto& chp : g.chunks) {
       const BatchChunk& ch = *chp;
-      const cudaStream_t ls = lane(b->chunk_lane[ci++]);
-      if (st != VP_OK) continue;
-      cudaError_t e = col2_batch(g.m[0], ch.col[0], ch.total[0], vp::kForward, g.src, ls);
-      if (e == cudaSuccess) e = col2_batch(g.m[1], ch.col[1], ch.total[1], vp::kForward, false, ls);
+      cudaError_t e = col2_batch(g.m[0], ch.col[0], ch.total[0], vp::kForward, g.src, s);
+      if (e == cudaSuccess) e = col2_batch(g.m[1], ch.col[1], ch.total[1], vp::kForward, false, s);
       if (e == cudaSuccess) {
         if (ch.z_per_item) {
-          for (int j = 0; j < ch.line.count && e == cudaSuccess; ++j) e = vp::launch_line_any(ch.line.item[j], vp::kConv, ls);
+          for (int j = 0; j < ch.line.count && e == cudaSuccess; ++j) e = vp::launch_line_any(ch.line.item[j], vp::kConv, s);
         } else {
-          e = line2_batch(g.m[2], ch.first, ch.ni_max, ch.line, ch.total[2], ls);
+          e = line2_batch(g.m[2], ch.first, ch.ni_max, ch.line, ch.total[2], s);
         }
       }
-      if (e == cudaSuccess) e = col2_batch(g.m[1], ch.col[2], ch.total[3], vp::kInverse, false, ls);
-      if (e == cudaSuccess) e = col2_batch(g.m[0], ch.col[3], ch.total[4], vp::kInverse, false, ls);
-      if (e != cudaSuccess) st = cuda_status(e);
+      if (e == cudaSuccess) e = col2_batch(g.m[1], ch.col[2], ch.total[3], vp::kInverse, false, s);
+      if (e == cudaSuccess) e = col2_batch(g.m[0], ch.col[3], ch.total[4], vp::kInverse, false, s);
+      if (e != cudaSuccess) return cuda_status(e);
     }
   }
-  for (size_t k = 0; k < b->singles.size() && st == VP_OK; ++k) {
-    const int i = b->singles[k];
+  for (int i : b->singles) {
     vp_plan_s* p = b->plans[i];
-    vp_stream_t ls = (vp_stream_t)lane(b->single_lane[k]);
+    int st;
     if (b->f[i]) {
-      st = vp_apply(p, b->f[i], b->u[i], ls);
+      st = vp_apply(p, b->f[i], b->u[i], stream);
     } else {
-      st = vp_source_assemble(p, b->lower[i].data(), (int)b->lower[i].size(), 0, nullptr, ls);
-      if (st == VP_OK) st = vp_apply(p, nullptr, b->u[i], ls);
+      st = vp_source_assemble(p, b->lower[i].data(), (int)b->lower[i].size(), 0, nullptr, stream);
+      if (st == VP_OK) st = vp_apply(p, nullptr, b->u[i], stream);
     }
+    if (st != VP_OK) return st;
   }
-  // join: the caller's stream waits for every side lane (also after an error, so that a
-  // capture in progress never ends with a side lane left unjoined)
-  for (size_t l = 0; l < b->side.size(); ++l) {
-    cudaError_t e = cudaEventRecord(b->joined[l], b->side[l]);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->joined[l], 0);
-    if (e != cudaSuccess && st == VP_OK) st = VP_ERR_CUDA;
-  }
-  return st;
+  return VP_OK;
 }
 
 VP_API int vp_batch_destroy(vp_batch_t b) {

@@ -117,11 +117,10 @@ def test_batch_of_large_items(vp):
         p.close()
 
 
-def test_batch_lanes_follow_the_callers_stream_and_replay_from_a_graph(vp):
-    """The batch's units run on several streams forked from the caller's stream: inputs
-    written on that stream just before the call (no synchronisation) must be seen, the
-    results must be complete when the caller's stream continues, and a captured run
-    replays on new inputs."""
+def test_batch_follows_the_callers_stream_and_replays_from_a_graph(vp):
+    """vp_batch_run on a non-default stream: inputs written on that stream just before
+    the call (no synchronisation) must be seen, the results must be complete when the
+    caller's stream continues, and a captured run replays on new inputs."""
     specs = [((40, 40, 40), 1), ((48, 60, 48), 1), ((64, 64, 64), 1), ((21, 21, 21), 1), ((37, 33, 40), 1)]
     plans, us, fs = [], [], []
     for n, h in specs:
