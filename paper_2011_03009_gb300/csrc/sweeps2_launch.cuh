@@ -70,16 +70,25 @@ inline bool col2_half(const ColSweep& p, int L, int dir) {
 }
 
 template <int A, int B>
-cudaError_t col2_dispatch(const ColSweep& p, int dir, bool src, cudaStream_t s) {
-  const bool half = col2_half(p, A * B, dir);
-  if (dir == kForward && src) {
+cudaError_t col2_dispatch_forward(const ColSweep& p, bool src, cudaStream_t s) {
+  const bool half = col2_half(p, A * B, kForward);
+  if (src) {
     // the source's grid is the embedded one: N <= M / 2 for every even M >= 2 N - 1
     if (!half) return cudaErrorInvalidValue;
     return col2_launch<A, B, kForward, true, true>(p, s);
   }
-  if (dir == kForward) return half ? col2_launch<A, B, kForward, false, true>(p, s)
-                                   : col2_launch<A, B, kForward, false, false>(p, s);
-  return half ? col2_launch<A, B, kInverse, false, true>(p, s) : col2_launch<A, B, kInverse, false, false>(p, s);
+  return half ? col2_launch<A, B, kForward, false, true>(p, s) : col2_launch<A, B, kForward, false, false>(p, s);
+}
+
+template <int A, int B>
+cudaError_t col2_dispatch_inverse(const ColSweep& p, cudaStream_t s) {
+  return col2_half(p, A * B, kInverse) ? col2_launch<A, B, kInverse, false, true>(p, s)
+                                       : col2_launch<A, B, kInverse, false, false>(p, s);
+}
+
+template <int A, int B>
+cudaError_t col2_dispatch(const ColSweep& p, int dir, bool src, cudaStream_t s) {
+  return dir == kForward ? col2_dispatch_forward<A, B>(p, src, s) : col2_dispatch_inverse<A, B>(p, s);
 }
 
 // Persistent pipelined convolution sweep: one CTA per resident slot, tiles strided.
@@ -116,8 +125,8 @@ __host__ __device__ constexpr int conv4_threads(int A, int B) { return ((4 * (A 
 // The pipelined z sweep in one of its forms (VP_ZFORM_*): 16-line tiles (256 threads),
 // 8-line half tiles (256 threads), 4-line quarter tiles (4 max(A, B) threads), or the
 // pair-split 8-line form (512 threads, L = 1280 only).  p.zform = 0 takes the form that
-// keeps the most warps resident per SM (ties: the shorter tile); a form that is not
-// compiled for L or whose shared memory does not fit is skipped.  *used = false: no form
+// keeps the most warps resident per SM (ties below); a form asked for that is not
+// compiled for L or whose shared memory does not fit leaves the choice to that rule.  *used = false: no form
 // applies (the caller falls back to the unpipelined kernel).
 template <int A, int B>
 cudaError_t line2_conv_pipe_launch(const LineSweep& p, cudaStream_t s, bool* used) {
@@ -138,7 +147,14 @@ cudaError_t line2_conv_pipe_launch(const LineSweep& p, cudaStream_t s, bool* use
   size_t smem[kForms] = {0, conv_pipe_smem(A, B, p.Oz), conv_pipe_smem(A, B, p.Oz, 8), conv_pipe_smem(A, B, p.Oz, 4),
                          conv_pair8_smem(A, B, p.Oz)};
   cudaError_t e;
-  auto want = [&](int f) { return p.zform == 0 || p.zform == f; };
+  // a form asked for that is not compiled for L, or does not fit, leaves the choice open
+  bool any = p.zform == 0;
+  if (!any) {
+    const bool compiled = p.zform == 1 || (p.zform == 2 && L >= 640) || (p.zform == 3 && L >= 512) ||
+                          (p.zform == 4 && A == 32 && B == 40);
+    any = !compiled || smem[p.zform] > 200 * 1024;
+  }
+  auto want = [&](int f) { return any || p.zform == f; };
   if (want(1) && smem[1] <= 200 * 1024) {
     e = resident_slots(line2_conv_pipe_kernel<A, B, false>, smem[1], granted16, &grid[1]);
     if (e != cudaSuccess) return e;
@@ -161,12 +177,15 @@ cudaError_t line2_conv_pipe_launch(const LineSweep& p, cudaStream_t s, bool* use
       if (e != cudaSuccess) return e;
     }
   }
+  // ties: from L = 640 the shorter tile (measured faster: 2.31 against 2.49 ms at L = 864
+  // on 432^3, 1.64 against 1.73 ms at L = 768); below, the longer one (at L = 512 the
+  // 4-line form leaves half its threads idle in the second step: 0.65 against 0.41 ms)
+  auto rank = [&](int f) { return L >= 640 ? f : kForms - f; };
   int best = 0;
   for (int f = 1; f < kForms; ++f) {
     if (grid[f] < 1) continue;
-    // more resident warps wins; on a tie the later (shorter) tile, which measured faster
-    // at L = 640-864 (e.g. 2.31 against 2.49 ms at L = 864 on 432^3)
-    if (best == 0 || (long long)grid[f] * threads[f] >= (long long)grid[best] * threads[best]) best = f;
+    const long long wf = (long long)grid[f] * threads[f], wb = best ? (long long)grid[best] * threads[best] : 0;
+    if (best == 0 || wf > wb || (wf == wb && rank(f) > rank(best))) best = f;
   }
   if (best == 0) return cudaSuccess;  // too large to pipeline (or the form asked for is not compiled)
   *used = true;
