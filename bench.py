@@ -43,7 +43,10 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="nested5",
                     choices=["small", "nested3", "nested5", "batch64", "vie", "fullcascade", "q0", "nw", "restrict",
-                             "fno"])
+                             "fno", "apply"])
+    ap.add_argument("--grid", default="128,128,640", help="voxels per axis for --workload apply")
+    ap.add_argument("--harmonic", type=int, default=2, help="harmonic for --workload apply")
+    ap.add_argument("--zform", type=int, default=0, help="z-sweep form for --workload apply (VP_ZFORM_*)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT comparison timing")
@@ -1172,6 +1175,38 @@ def run_fno(args):
           plain_route={"fields_per_s": 1e3 / t_plain_route, "ms_per_bowl": t_plain_route})
 
 
+def run_apply(args):
+    """One plan on one grid (--grid, --harmonic, --zform; 1.1 MHz water, 227 um voxels):
+    the kernel spectrum, then --warmup and --steps applications of a random field, each
+    after an L2 flush; per-sweep CUDA-event times.  The small single-sweep cases of the
+    ncu captures under profiles/ run through this workload."""
+    import torch
+    from paper_2011_03009_gb300 import synth, vp
+    n = tuple(int(v) for v in args.grid.split(","))
+    g = synth.Grid(n, (0.0, 0.0, 0.0), 2.27e-4)
+    plan = vp.vp_plan(g, args.harmonic, 1.1e6, synth.WATER, zform=args.zform)
+    plan.kernel_fft()
+    f = torch.randn(n, dtype=torch.complex64, device="cuda")
+    u = torch.empty_like(f)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        plan.apply(f, u)
+    torch.cuda.synchronize()
+    plan.profile_enable(True)
+    for _ in range(args.steps):
+        flush.zero_()
+        plan.apply(f, u)
+    ms, cnt = plan.profile_read()
+    inf = plan.info()
+    by = sweep_bytes(tuple(inf.n), tuple(inf.m), args.harmonic, False)
+    rows = [{"sweep": SWEEP_NAMES[i] if i else "x_forward", "ms": ms[i] / max(1, cnt[i]),
+             "gbs": by[i] / (ms[i] / max(1, cnt[i]) * 1e-3) / 1e9} for i in range(5)]
+    t = sum(r["ms"] for r in rows)
+    _line(METRIC, g.voxels / (t * 1e-3), METRIC, t, args.steps, args.warmup, True,
+          {"workload": f"apply_{'x'.join(map(str, n))}_h{args.harmonic}", "m": list(inf.m), "zform": args.zform},
+          sweeps=rows)
+
+
 def run_nw(args):
     """Section 3's mesh refinement: p2 of the H131 transducer in liver on meshes of
     h = lambda / (2 n_w), n_w = 5..25 (odd), over one box around the focus, against
@@ -1218,12 +1253,12 @@ def main():
     world, rank, local = dist_init(args)
     if args.workload == "batch64":
         run_batch(args, world, rank, local)
-    elif args.workload in ("vie", "fullcascade", "q0", "nw", "restrict", "fno"):
+    elif args.workload in ("vie", "fullcascade", "q0", "nw", "restrict", "fno", "apply"):
         import torch
         torch.cuda.set_device(local)
         if rank == 0:
             {"vie": run_vie, "fullcascade": run_fullcascade, "q0": run_q0, "nw": run_nw,
-             "restrict": run_restrict, "fno": run_fno}[args.workload](args)
+             "restrict": run_restrict, "fno": run_fno, "apply": run_apply}[args.workload](args)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

@@ -8,10 +8,7 @@ cudaError_t launch_col2_part2(const ColSweep& p, int dir, bool src, cudaStream_t
     case 768: return col2_dispatch<24, 32>(p, dir, src, s);
     case 864: return col2_dispatch<27, 32>(p, dir, src, s);
     case 1024: return col2_dispatch<32, 32>(p, dir, src, s);
-    // forward 40 x 30: the first step's tasks (column, b < 30) are 240 on 256 threads, so
-    // every column's loads issue in one round (30 x 40 takes two); the inverse loads in
-    // its first step over k1 < 30 with 30 x 40
-    case 1200: return dir == kForward ? col2_dispatch_forward<40, 30>(p, src, s) : col2_dispatch_inverse<30, 40>(p, s);
+    case 1200: return col2_dispatch<30, 40>(p, dir, src, s);
     case 1280: return col2_dispatch<32, 40>(p, dir, src, s);
     default: return cudaErrorNotSupported;
   }
