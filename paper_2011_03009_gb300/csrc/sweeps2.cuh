@@ -164,17 +164,6 @@ __global__ void __launch_bounds__(kThreads2, 2) col2_kernel8(const ColSweep p) {
   col2_tile<A, B, DIR, SRC, HALF, 8>(p, blockIdx.x, S);
 }
 
-// Long columns, 4 per CTA: one 32-byte row segment per quarter of a half-warp, and
-// 4 max(A, B) threads (one task of each step per thread), so that three or four CTAs
-// share an SM and their load and compute phases overlap.
-__host__ __device__ constexpr int col4_threads(int A, int B) { return ((4 * (A > B ? A : B) + 31) / 32) * 32; }
-template <int A, int B, int DIR, bool SRC, bool HALF>
-__global__ void __launch_bounds__(col4_threads(A, B), 65536 / (col4_threads(A, B) * 128))
-    col2_kernel4(const ColSweep p) {
-  extern __shared__ float2 S[];
-  col2_tile<A, B, DIR, SRC, HALF, 4>(p, blockIdx.x, S);
-}
-
 // Batched form: the parameters of up to kMaxBatch plans travel in the kernel's own
 // parameter block (constant bank), with offsets[i] the first CTA (or tile) of plan i;
 // CTA b finds its plan by a binary search over the constant-bank offsets.

@@ -20,24 +20,9 @@ cudaError_t grant_smem(K kernel, size_t bytes, volatile int* granted) {
   return e;
 }
 
-// Column sweeps longer than 512: 4-column CTAs (kColTiles4) or 8-column CTAs.
-constexpr bool kColTiles4 = false;
-
 template <int A, int B, int DIR, bool SRC, bool HALF>
 cudaError_t col2_launch(const ColSweep& p, cudaStream_t s) {
   static volatile int granted[64] = {0};
-  if constexpr (A * B > 512 && kColTiles4) {
-    static volatile int granted4[64] = {0};
-    const size_t smem = (size_t)4 * col2_pitch(A * B) * sizeof(float2);
-    const long long blocks = (long long)((p.C + 3) / 4) * p.n_outer;
-    if (blocks <= 0) return cudaSuccess;
-    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    auto k = col2_kernel4<A, B, DIR, SRC, HALF>;
-    cudaError_t e = grant_smem(k, smem, granted4);
-    if (e != cudaSuccess) return e;
-    k<<<(unsigned)blocks, col4_threads(A, B), smem, s>>>(p);
-    return cudaGetLastError();
-  }
   if constexpr (A * B > 512) {
     // one 16-column CTA per SM at these lengths: 8-column CTAs, two per SM, instead
     static volatile int granted8[64] = {0};
