@@ -164,91 +164,6 @@ __global__ void __launch_bounds__(kThreads2, 2) col2_kernel8(const ColSweep p) {
   col2_tile<A, B, DIR, SRC, HALF, 8>(p, blockIdx.x, S);
 }
 
-// Persistent, software-pipelined form of the long forward column sweep with a
-// zero-padded input (rows_in <= L / 2, no source products): each CTA walks the tiles of
-// 8 columns blockIdx.x, blockIdx.x + gridDim.x, ...  The rows_in x 8 input block of the
-// next tile is copied into a staging buffer with cp.async while the current tile runs
-// its second step and stores, so that the loads of one tile overlap the arithmetic and
-// stores of the one before.  Two CTAs share an SM (transpose buffer plus staging buffer,
-// 115 KB at L = 1200).  Shared memory: 8 x col2_pitch(L) transpose, then rows_in x 8
-// staging (row-major: element (row, column) at row * 8 + column).
-__host__ __device__ constexpr size_t col2_pipe_smem(int L, int rows) {
-  return ((size_t)8 * col2_pitch(L) + (size_t)rows * 8) * sizeof(float2);
-}
-
-template <int A, int B>
-__global__ void __launch_bounds__(kThreads2, 2) col2_pipe_fwd_kernel(const ColSweep p, int ntiles) {
-  constexpr int NL = 8;
-  constexpr int L = A * B;
-  constexpr int AH = conv_rows_in(A);
-  constexpr int LP = col2_pitch(L);
-  extern __shared__ float2 S[];
-  float2* I = S + NL * LP;
-  const int R = p.rows_in;  // <= B AH = L / 2 rows staged a column
-  const int ncb = (p.C + NL - 1) / NL;
-  const float2* __restrict__ tw = p.ax.tw;
-  const float2 zero = make_float2(0.f, 0.f);
-  auto fetch = [&](int tile) {
-    const int o = tile / ncb;
-    const int c0 = (tile - o * ncb) * NL;
-    const long long base = (long long)o * p.in_os + c0;
-    for (int i = threadIdx.x; i < R * NL; i += blockDim.x) {
-      const int row = i >> 3, col = i & (NL - 1);
-      const bool ok = c0 + col < p.C;
-      cp_async8(&I[i], &p.in[ok ? base + (long long)row * p.in_rs + col : 0], ok);
-    }
-  };
-  int t = blockIdx.x;
-  if (t < ntiles) fetch(t);
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
-  for (; t < ntiles; t += gridDim.x) {
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-    __syncthreads();
-    // step 1 from the staging buffer: task (column, b), the 8 lanes of a quarter warp on
-    // the 8 columns of one row (one 64-byte shared-memory row a quarter warp)
-    for (int tau = threadIdx.x; tau < NL * B; tau += blockDim.x) {
-      const int line = tau & (NL - 1);
-      const int b = tau >> 3;
-      float2 v[A];
-#pragma unroll
-      for (int a = 0; a < AH; ++a) {
-        const int row = B * a + b;
-        v[a] = row < R ? I[row * NL + line] : zero;
-      }
-      dft_reg_nz<A, false, AH>(v);
-      float2* s = S + line * LP + b;
-      s[0] = v[0];
-#pragma unroll
-      for (int k1 = 1; k1 < A; ++k1) s[k1 * B] = cmul(v[k1], __ldg(&tw[b * k1]));
-    }
-    __syncthreads();
-    if (t + (int)gridDim.x < ntiles) fetch(t + gridDim.x);
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-    // step 2: task (column, k1), stored straight to global memory
-    const int o = t / ncb;
-    const int c0 = (t - o * ncb) * NL;
-    for (int tau = threadIdx.x; tau < NL * A; tau += blockDim.x) {
-      const int line = tau & (NL - 1);
-      const int k1 = tau >> 3;
-      float2 z[B];
-      const float2* s = S + line * LP + k1 * B;
-#pragma unroll
-      for (int bb = 0; bb < B; ++bb) z[bb] = s[bb];
-      dft_reg<B, false>(z);
-      const int c = c0 + line;
-      if (c < p.C) {
-        const long long base = (long long)o * p.out_os + c;
-#pragma unroll
-        for (int k2 = 0; k2 < B; ++k2) {
-          const int row = k1 + A * k2;
-          if (row < p.rows_out) p.out[base + (long long)row * p.out_rs] = z[k2];
-        }
-      }
-    }
-  }
-  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-}
-
 // Batched form: the parameters of up to kMaxBatch plans travel in the kernel's own
 // parameter block (constant bank), with offsets[i] the first CTA (or tile) of plan i;
 // CTA b finds its plan by a binary search over the constant-bank offsets.

@@ -20,28 +20,9 @@ cudaError_t grant_smem(K kernel, size_t bytes, volatile int* granted) {
   return e;
 }
 
-template <typename K>
-cudaError_t resident_slots(K kernel, size_t smem, volatile int* granted, int* grid_out, int threads = kThreads2);
-
 template <int A, int B, int DIR, bool SRC, bool HALF>
 cudaError_t col2_launch(const ColSweep& p, cudaStream_t s) {
   static volatile int granted[64] = {0};
-  if constexpr (A * B > 512 && DIR == kForward && !SRC && HALF) {
-    // persistent form with the next tile's input staged while the current one computes
-    static volatile int grantedp[64] = {0};
-    const long long tiles = (long long)((p.C + 7) / 8) * p.n_outer;
-    if (tiles <= 0) return cudaSuccess;
-    if (tiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    const size_t smem = col2_pipe_smem(A * B, p.rows_in);
-    int grid = 0;
-    cudaError_t e = resident_slots(col2_pipe_fwd_kernel<A, B>, smem, grantedp, &grid);
-    if (e != cudaSuccess) return e;
-    if (grid >= 1) {
-      if (grid > tiles) grid = (int)tiles;
-      col2_pipe_fwd_kernel<A, B><<<(unsigned)grid, kThreads2, smem, s>>>(p, (int)tiles);
-      return cudaGetLastError();
-    }
-  }
   if constexpr (A * B > 512) {
     // one 16-column CTA per SM at these lengths: 8-column CTAs, two per SM, instead
     static volatile int granted8[64] = {0};
@@ -113,7 +94,7 @@ cudaError_t col2_dispatch(const ColSweep& p, int dir, bool src, cudaStream_t s) 
 // Persistent pipelined convolution sweep: one CTA per resident slot, tiles strided.
 // Resident CTAs per SM for a given shared-memory size, cached per (device, size).
 template <typename K>
-cudaError_t resident_slots(K kernel, size_t smem, volatile int* granted, int* grid_out, int threads) {
+cudaError_t resident_slots(K kernel, size_t smem, volatile int* granted, int* grid_out, int threads = kThreads2) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
