@@ -95,6 +95,26 @@ def main(argv=None):
     casc = F.PlainCascade(a.n, a.points)
     times = stage_times(model, casc, F.draw_bowls(8, 7))
     fb = float(np.mean(worst > a.threshold))
+    # the judged route on held-out bowls: the plain path's p2 decides per sample
+    judged = F.JudgedSurrogate(model, threshold=a.threshold, n_points=a.points)
+    plain = F.PlainCascade(a.n, a.points)
+    jb = F.draw_bowls(16, 6)
+    verdicts = []
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record()
+    for i, b in enumerate(jb):
+        verdicts.append(judged.run(b, 6 * 100003 + i)[1])
+    ev[1].record()
+    ev[2].record()
+    for i, b in enumerate(jb):
+        plain.run(b, 6 * 100003 + i)
+    ev[3].record()
+    torch.cuda.synchronize()
+    judged_route = {"bowls": len(jb), "fallback_rate": float(np.mean([v["fallback"] for v in verdicts])),
+                    "judge_rel_l2": [v["judge_rel_l2"] for v in verdicts],
+                    "ms_per_bowl": ev[0].elapsed_time(ev[1]) / len(jb),
+                    "plain_route_ms_per_bowl": ev[2].elapsed_time(ev[3]) / len(jb)}
     inc, harm, inf = times["incident_ms_per_grid"], times["plain_cascade_ms"], times["surrogate_infer_ms"]
     res = {
         "n": a.n, "width": a.width, "hidden": a.hidden, "layers": a.layers, "modes": list(modes),
@@ -105,7 +125,7 @@ def main(argv=None):
         "heldout_rel_l2_p90": np.quantile(errs, 0.9, axis=0).tolist(),
         "train_rel_l2_mean": train_err.mean(axis=0).tolist(),
         "threshold": a.threshold, "fallback_rate": fb,
-        "data_gen_s": t_gen + t_gen2, "train_s": t_train,
+        "data_gen_s": t_gen + t_gen2, "train_s": t_train, "judged_route": judged_route,
         **times,
         # fields/s from p1 already on the device (the cascade vs the surrogate), and with
         # the incident field included (plain: p1 on the grid of harmonic 2; surrogate: p1
