@@ -84,8 +84,10 @@ typedef struct vp_plan_opts {
     int radix[3][8];    /* radix schedule per axis (product must equal M); 0-terminated,
                            all zero = default schedule                                    */
     int autotune;       /* nonzero and no m / radix given: time the default embedding
-                           against the smallest even 5-smooth one (three applications
-                           each, on `stream`) and keep the faster; cached per grid shape */
+                           against the smallest even 5-smooth one, then (zform 0 and
+                           M_z >= 512 on the two-level engine) every z-sweep form on the
+                           winner (three applications each, on `stream`), and keep the
+                           fastest; cached per grid shape                                */
     int zform;          /* form of the pipelined z sweep (two-level engine): VP_ZFORM_*;
                            0 = the form that keeps the most warps resident per SM.  A form
                            that is not compiled for M_z or does not fit in shared memory
@@ -97,6 +99,7 @@ typedef struct vp_plan_opts {
 #define VP_ZFORM_TILE8  2  /* 8 lines a CTA (2 mirror groups), 256 threads, M_z >= 640   */
 #define VP_ZFORM_TILE4  3  /* 4 lines a CTA (1 mirror group), 4 max(A, B) threads, M_z >= 512 */
 #define VP_ZFORM_PAIR8  4  /* 8 lines, step 2 split over lane pairs, 512 threads, M_z = 1280 */
+#define VP_ZFORM_TILE4T 5  /* 4 lines, the two steps' factors swapped (40 x 32), 160 threads, M_z = 1280 */
 
 typedef struct vp_plan_info {
     int n[3];
@@ -108,6 +111,7 @@ typedef struct vp_plan_info {
     unsigned long long workspace_bytes;  /* device bytes held by the plan               */
     int khat_ready;      /* 1 once vp_kernel_fft has been enqueued                       */
     int engine[3];       /* per axis: 1 two-level register FFT, 0 shared-memory radix passes */
+    int zform;           /* z-sweep form asked for or chosen by the autotuner (VP_ZFORM_*) */
 } vp_plan_info;
 
 /* ---- plans --------------------------------------------------------------------

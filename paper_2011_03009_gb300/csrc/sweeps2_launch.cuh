@@ -134,24 +134,26 @@ cudaError_t line2_conv_pipe_launch(const LineSweep& p, cudaStream_t s, bool* use
   static volatile int granted8[64] = {0};
   static volatile int granted4[64] = {0};
   static volatile int grantedp[64] = {0};
+  static volatile int granted4t[64] = {0};
   constexpr int L = A * B;
   constexpr int NT4 = conv4_threads(A, B);
+  constexpr bool kSwap = A == 32 && B == 40;  // the transposed 4-line form (40 x 32) at L = 1280
   *used = false;
   // the kernel reads and writes the first half of each line only (zero-padded input,
   // cropped output); any other line goes to line2_kernel
   if (2 * p.n_in > L || 2 * p.n_out > L) return cudaSuccess;
   const int ni = conv_stage_pitch(A, B);
-  constexpr int kForms = 5;
-  int grid[kForms] = {0, 0, 0, 0, 0};  // resident CTAs on the GPU, per form
-  int threads[kForms] = {0, kThreads2, kThreads2, NT4, kThreadsPair};
+  constexpr int kForms = 6;
+  int grid[kForms] = {0, 0, 0, 0, 0, 0};  // resident CTAs on the GPU, per form
+  int threads[kForms] = {0, kThreads2, kThreads2, NT4, kThreadsPair, conv4_threads(B, A)};
   size_t smem[kForms] = {0, conv_pipe_smem(A, B, p.Oz), conv_pipe_smem(A, B, p.Oz, 8), conv_pipe_smem(A, B, p.Oz, 4),
-                         conv_pair8_smem(A, B, p.Oz)};
+                         conv_pair8_smem(A, B, p.Oz), conv_pipe_smem(B, A, p.Oz, 4)};
   cudaError_t e;
   // a form asked for that is not compiled for L, or does not fit, leaves the choice open
   bool any = p.zform == 0;
   if (!any) {
     const bool compiled = p.zform == 1 || (p.zform == 2 && L >= 640) || (p.zform == 3 && L >= 512) ||
-                          (p.zform == 4 && A == 32 && B == 40);
+                          (p.zform == 4 && A == 32 && B == 40) || (p.zform == 5 && kSwap);
     any = !compiled || smem[p.zform] > 200 * 1024;
   }
   auto want = [&](int f) { return any || p.zform == f; };
@@ -177,6 +179,13 @@ cudaError_t line2_conv_pipe_launch(const LineSweep& p, cudaStream_t s, bool* use
       if (e != cudaSuccess) return e;
     }
   }
+  if constexpr (kSwap) {
+    if (want(5) && smem[5] <= 200 * 1024) {
+      e = resident_slots(line2_conv_pipe_kernel<B, A, false, 4, conv4_threads(B, A)>, smem[5], granted4t, &grid[5],
+                         conv4_threads(B, A));
+      if (e != cudaSuccess) return e;
+    }
+  }
   // ties: from L = 640 the shorter tile (measured faster: 2.31 against 2.49 ms at L = 864
   // on 432^3, 1.64 against 1.73 ms at L = 768); below, the longer one (at L = 512 the
   // 4-line form leaves half its threads idle in the second step: 0.65 against 0.41 ms)
@@ -191,7 +200,7 @@ cudaError_t line2_conv_pipe_launch(const LineSweep& p, cudaStream_t s, bool* use
   *used = true;
   if (p.nlines <= 0) return cudaSuccess;
   static BatchParams<LineSweep> none{};  // unused by the single-plan form
-  const long long units = p.nlines * (best == 1 ? 1 : (best == 3 ? 4 : 2));
+  const long long units = p.nlines * (best == 1 ? 1 : (best == 3 || best == 5 ? 4 : 2));
   const int g = (int)(grid[best] > units ? units : grid[best]);
   switch (best) {
     case 1:
@@ -203,6 +212,11 @@ cudaError_t line2_conv_pipe_launch(const LineSweep& p, cudaStream_t s, bool* use
     case 3:
       if constexpr (L >= 512)
         line2_conv_pipe_kernel<A, B, false, 4, NT4><<<(unsigned)g, NT4, smem[3], s>>>(p, none, units, ni);
+      break;
+    case 5:
+      if constexpr (kSwap)
+        line2_conv_pipe_kernel<B, A, false, 4, conv4_threads(B, A)>
+            <<<(unsigned)g, conv4_threads(B, A), smem[5], s>>>(p, none, units, conv_stage_pitch(B, A));
       break;
     default:
       if constexpr (A == 32 && B == 40) line2_conv_pair8_kernel<A, B><<<(unsigned)g, kThreadsPair, smem[4], s>>>(p, units, ni);

@@ -406,14 +406,16 @@ int run_sweep(vp_plan_s* p, int which, const float2* f, const float2* const* low
   return prof_end(rec, s);
 }
 
-// ---- autotuner: embedding size per grid shape -----------------------------------------
-// Candidates: the default (two-level engine where its menu allows) and the smallest even
-// 5-smooth size per axis (radix-pass engine unless that size is on the menu).  Each is
-// timed over three applications on the caller's stream; the winner is cached per grid
-// shape for the life of the process.
+// ---- autotuner: embedding size and z-sweep form per grid shape -------------------------
+// Embedding candidates: the default (two-level engine where its menu allows) and the
+// smallest even 5-smooth size per axis (radix-pass engine unless that size is on the
+// menu).  Then, for the winner, every form of the pipelined z sweep (VP_ZFORM_*) when
+// M_z >= 512 and no form was asked for.  Each candidate is timed over three
+// applications on the caller's stream; the winners are cached per grid shape for the
+// life of the process.
 
 std::mutex g_tune_mu;
-std::map<std::array<int, 3>, std::array<int, 3>> g_tune_cache;
+std::map<std::array<int, 3>, std::array<int, 4>> g_tune_cache;  // m[3], zform
 
 // ---- batched evaluation ------------------------------------------------------------
 
@@ -521,7 +523,7 @@ int build_group(vp_batch_s* b, BatchGroup& g) {
   return VP_OK;
 }
 
-int autotune_m(const vp_grid* g, double f0, const vp_medium* med, cudaStream_t s, int* best_m);
+int autotune_m(const vp_grid* g, double f0, const vp_medium* med, cudaStream_t s, int* best_m, int* best_zform);
 
 }  // namespace
 
@@ -609,7 +611,7 @@ VP_API int vp_plan(const vp_grid* g, int harmonic_n, double f0_hz, const vp_medi
       !std::isfinite(f0_hz))
     return VP_ERR_ARG;
   if (harmonic_n - 1 > vp::kMaxLower) return VP_ERR_UNSUPPORTED;
-  if (opts && (opts->zform < VP_ZFORM_AUTO || opts->zform > VP_ZFORM_PAIR8)) return VP_ERR_ARG;
+  if (opts && (opts->zform < VP_ZFORM_AUTO || opts->zform > VP_ZFORM_TILE4T)) return VP_ERR_ARG;
   if (opts && opts->autotune) {
     bool explicit_choice = false;
     for (int a = 0; a < 3; ++a) explicit_choice |= opts->m[a] != 0 || opts->radix[a][0] != 0;
@@ -623,14 +625,19 @@ VP_API int vp_plan(const vp_grid* g, int harmonic_n, double f0_hz, const vp_medi
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
           for (int a = 0; a < 3; ++a) o.m[a] = it->second[a];
+          if (o.zform == VP_ZFORM_AUTO) o.zform = it->second[3];
           cached = true;
         }
       }
       if (!cached) {
-        const int st = autotune_m(g, f0_hz, med, (cudaStream_t)stream, o.m);
+        int zf = o.zform;
+        const int st = autotune_m(g, f0_hz, med, (cudaStream_t)stream, o.m, &zf);
         if (st != VP_OK) return st;
-        std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune_cache[key] = {o.m[0], o.m[1], o.m[2]};
+        if (o.zform == VP_ZFORM_AUTO) {
+          std::lock_guard<std::mutex> lk(g_tune_mu);
+          g_tune_cache[key] = {o.m[0], o.m[1], o.m[2], zf};
+        }
+        o.zform = zf;
       }
       return vp_plan(g, harmonic_n, f0_hz, med, &o, stream, out);
     }
@@ -735,6 +742,7 @@ VP_API int vp_plan_get_info(vp_plan_t p, vp_plan_info* info) {
   info->workspace_bytes = p->bytes;
   info->khat_ready = p->khat_ready ? 1 : 0;
   for (int a = 0; a < 3; ++a) info->engine[a] = p->fast[a];
+  info->zform = p->zform;
   return VP_OK;
 }
 
@@ -1157,7 +1165,7 @@ VP_API int vp_profile_read(vp_plan_t p, double ms[5], int count[5], int reset) {
 
 namespace {
 
-int autotune_m(const vp_grid* g, double f0, const vp_medium* med, cudaStream_t s, int* best_m) {
+int autotune_m(const vp_grid* g, double f0, const vp_medium* med, cudaStream_t s, int* best_m, int* best_zform) {
   int cand[2][3];
   for (int a = 0; a < 3; ++a) {
     cand[0][a] = default_m(g->n[a]);
@@ -1165,7 +1173,10 @@ int autotune_m(const vp_grid* g, double f0, const vp_medium* med, cudaStream_t s
     best_m[a] = cand[0][a];
   }
   const bool same = cand[0][0] == cand[1][0] && cand[0][1] == cand[1][1] && cand[0][2] == cand[1][2];
-  if (same) return VP_OK;
+  // candidates in order: the two embeddings (form as asked), then the z forms 1..5 on
+  // the winning embedding when no form was asked for and M_z >= 512 on the fast engine
+  const bool tune_z = *best_zform == VP_ZFORM_AUTO;
+  if (same && !(tune_z && fast_size(cand[0][2]) && cand[0][2] >= 512)) return VP_OK;
   const size_t nv = (size_t)g->n[0] * g->n[1] * g->n[2];
   float2* f = nullptr;
   float2* u = nullptr;
@@ -1175,15 +1186,16 @@ int autotune_m(const vp_grid* g, double f0, const vp_medium* med, cudaStream_t s
   cudaEvent_t t0 = nullptr, t1 = nullptr;
   if (e == cudaSuccess) e = cudaEventCreate(&t0);
   if (e == cudaSuccess) e = cudaEventCreate(&t1);
-  float best = 1e30f;
-  for (int c = 0; c < 2 && e == cudaSuccess; ++c) {
+  // milliseconds of three applications with embedding m and z form zf (1e30: not timed)
+  auto time_plan = [&](const int* m, int zf) -> float {
     vp_plan_opts o{};
-    for (int a = 0; a < 3; ++a) o.m[a] = cand[c][a];
+    for (int a = 0; a < 3; ++a) o.m[a] = m[a];
+    o.zform = zf;
     vp_plan_t p = nullptr;
-    if (vp_plan(g, 1, f0, med, &o, s, &p) != VP_OK) continue;
+    if (vp_plan(g, 1, f0, med, &o, s, &p) != VP_OK) return 1e30f;
     p->khat_ready = true;  // timing only: the spectrum's values do not change the work
     e = cudaMemsetAsync(p->khat, 0, (size_t)p->oct[0] * p->oct[1] * p->oct[2] * sizeof(float2), s);
-    float ms = 0.f;
+    float ms = 1e30f;
     for (int r = 0; r < 4 && e == cudaSuccess; ++r) {
       if (r == 1) e = cudaEventRecord(t0, s);
       if (e == cudaSuccess && vp_apply(p, f, u, s) != VP_OK) e = cudaErrorUnknown;
@@ -1192,9 +1204,26 @@ int autotune_m(const vp_grid* g, double f0, const vp_medium* med, cudaStream_t s
     if (e == cudaSuccess) e = cudaEventSynchronize(t1);
     if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
     vp_destroy(p);
-    if (e == cudaSuccess && ms < best) {
-      best = ms;
-      for (int a = 0; a < 3; ++a) best_m[a] = cand[c][a];
+    return e == cudaSuccess ? ms : 1e30f;
+  };
+  if (!same) {
+    float best = 1e30f;
+    for (int c = 0; c < 2 && e == cudaSuccess; ++c) {
+      const float ms = time_plan(cand[c], *best_zform);
+      if (ms < best) {
+        best = ms;
+        for (int a = 0; a < 3; ++a) best_m[a] = cand[c][a];
+      }
+    }
+  }
+  if (e == cudaSuccess && tune_z && fast_size(best_m[2]) && best_m[2] >= 512) {
+    float best = 1e30f;
+    for (int zf = VP_ZFORM_TILE16; zf <= VP_ZFORM_TILE4T && e == cudaSuccess; ++zf) {
+      const float ms = time_plan(best_m, zf);
+      if (ms < best) {
+        best = ms;
+        *best_zform = zf;
+      }
     }
   }
   if (t0) cudaEventDestroy(t0);

@@ -26,7 +26,7 @@ VP_ERR_UNSUPPORTED = -8
 VP_RESTRICT_ZERO_OUTSIDE = 1
 VP_RESTRICT_QUADRATIC = 2
 VP_SRC_CONJ = 1
-VP_ZFORM_AUTO, VP_ZFORM_TILE16, VP_ZFORM_TILE8, VP_ZFORM_TILE4, VP_ZFORM_PAIR8 = 0, 1, 2, 3, 4
+VP_ZFORM_AUTO, VP_ZFORM_TILE16, VP_ZFORM_TILE8, VP_ZFORM_TILE4, VP_ZFORM_PAIR8, VP_ZFORM_TILE4T = 0, 1, 2, 3, 4, 5
 MAX_PASS = 8
 MAX_LOWER = 8
 
@@ -55,7 +55,8 @@ class vp_plan_info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int * 3), ("m", ctypes.c_int * 3), ("radix", (ctypes.c_int * MAX_PASS) * 3),
                 ("k_re", ctypes.c_double), ("k_im", ctypes.c_double), ("c_n", ctypes.c_double),
                 ("self_re", ctypes.c_double), ("self_im", ctypes.c_double),
-                ("workspace_bytes", ctypes.c_ulonglong), ("khat_ready", ctypes.c_int), ("engine", ctypes.c_int * 3)]
+                ("workspace_bytes", ctypes.c_ulonglong), ("khat_ready", ctypes.c_int), ("engine", ctypes.c_int * 3),
+                ("zform", ctypes.c_int)]
 
 
 def _load():

@@ -385,14 +385,14 @@ def test_retargeted_plan_matches_a_fresh_plan_and_the_oracle(vp):
 @pytest.mark.parametrize("nz", [256, 320, 432, 512, 640])
 def test_every_z_sweep_form_matches_oracle(vp, nz):
     """Each form of the pipelined z sweep (16-, 8- and 4-line tiles, the pair-split
-    8-line form) at the z embeddings of the runs (M_z = 512 ... 1280), with ragged x and
+    8-line form, the 4-line form with its factors swapped) at the z embeddings of the runs (M_z = 512 ... 1280), with ragged x and
     y axes; a form not compiled for M_z falls back to the automatic choice."""
     n = (7, 5, nz)
     g = grid(n)
     k = physics.wavenumber(3, 1.0e6, synth.WATER)
     f = synth.random_field(n, seed=nz)
     ref = potential.apply_fft(f, g.h, k)
-    for form in (vp.VP_ZFORM_TILE16, vp.VP_ZFORM_TILE8, vp.VP_ZFORM_TILE4, vp.VP_ZFORM_PAIR8):
+    for form in (vp.VP_ZFORM_TILE16, vp.VP_ZFORM_TILE8, vp.VP_ZFORM_TILE4, vp.VP_ZFORM_PAIR8, vp.VP_ZFORM_TILE4T):
         plan = vp.vp_plan(g, 3, 1.0e6, synth.WATER, zform=form)
         assert plan.info().m[2] == 2 * nz
         vp.vp_kernel_fft(plan)
@@ -400,3 +400,20 @@ def test_every_z_sweep_form_matches_oracle(vp, nz):
         vp.vp_apply(plan, dev(f), u)
         assert rel_l2(host(u), ref) <= REL_L2, form
         plan.close()
+
+
+def test_autotuned_z_form_matches_oracle(vp):
+    """The autotuner times the z-sweep forms for M_z >= 512 and keeps one; the plan it
+    returns reports that form and matches the oracle."""
+    n = (9, 6, 320)
+    g = grid(n)
+    k = physics.wavenumber(2, 1.0e6, synth.WATER)
+    f = synth.random_field(n, seed=77)
+    plan = vp.vp_plan(g, 2, 1.0e6, synth.WATER, autotune=True)
+    inf = plan.info()
+    assert inf.m[2] == 640 and vp.VP_ZFORM_TILE16 <= inf.zform <= vp.VP_ZFORM_TILE4T
+    vp.vp_kernel_fft(plan)
+    u = torch.empty(n, dtype=torch.complex64, device="cuda")
+    vp.vp_apply(plan, dev(f), u)
+    assert rel_l2(host(u), potential.apply_fft(f, g.h, k)) <= REL_L2
+    plan.close()
