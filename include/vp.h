@@ -315,6 +315,10 @@ VP_API int vp_incident_field(const vp_grid* g, const double* points, int n_point
 typedef struct vp_batch_s* vp_batch_t;
 VP_API int vp_batch_create(int count, const vp_plan_t* plans, const void* const* f, const void* const* lower,
                            void* const* u, vp_batch_t* out);
+/* The same as vp_batch_create with the plans first, as the batched call of the interface
+ * sketch names it (plans, count, ...); identical behaviour and errors. */
+VP_API int vp_batch_plan(const vp_plan_t* plans, int count, const void* const* f, const void* const* lower,
+                         void* const* u, vp_batch_t* out);
 VP_API int vp_batch_run(vp_batch_t b, vp_stream_t stream);
 VP_API int vp_batch_destroy(vp_batch_t b);
 

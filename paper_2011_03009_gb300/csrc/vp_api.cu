@@ -1039,7 +1039,7 @@ VP_API int vp_batch_create(int count, const vp_plan_t* plans, const void* const*
   if (!b) return VP_ERR_NOMEM;
   b->count = count;
   b->plans.assign(plans, plans + count);
-  for (int i = 0; i < count; ++i) b->generation.push_back(plans[i]->generation);
+  for (int i = 0; i < count; ++i) b->generation.push_back(plans[i] ? plans[i]->generation : 0);
   b->f.resize(count, nullptr);
   b->lower.resize(count);
   b->u.assign(u, u + count);
@@ -1090,6 +1090,11 @@ VP_API int vp_batch_create(int count, const vp_plan_t* plans, const void* const*
   }
   *out = b;
   return VP_OK;
+}
+
+VP_API int vp_batch_plan(const vp_plan_t* plans, int count, const void* const* f, const void* const* lower,
+                         void* const* u, vp_batch_t* out) {
+  return vp_batch_create(count, plans, f, lower, u, out);
 }
 
 VP_API int vp_batch_run(vp_batch_t b, vp_stream_t stream) {

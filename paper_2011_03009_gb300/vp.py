@@ -92,6 +92,8 @@ def _load():
         "vp_q0_box": (I, [ctypes.POINTER(I), P, D, ctypes.POINTER(I), ctypes.POINTER(D), P]),
         "vp_batch_create": (I, [I, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P),
                                 ctypes.POINTER(P)]),
+        "vp_batch_plan": (I, [ctypes.POINTER(P), I, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P),
+                              ctypes.POINTER(P)]),
         "vp_batch_run": (I, [P, P]),
         "vp_batch_destroy": (I, [P]),
     }

@@ -31,7 +31,7 @@ def test_header_declares_the_boundary():
     names = _declared_functions()
     for required in ("vp_plan", "vp_kernel_fft", "vp_source_assemble", "vp_apply",
                      "vp_restrict_to_nested_box", "vp_destroy", "vp_status_string",
-                     "vp_batch_create", "vp_batch_run", "vp_apply_static",
+                     "vp_batch_create", "vp_batch_plan", "vp_batch_run", "vp_apply_static",
                      "vp_fno_forward", "vp_fno_backward", "vp_fno_adam"):
         assert required in names
 
@@ -306,3 +306,14 @@ def test_surrogate_binding_checks_activation_buffers(vp, monkeypatch):
         with pytest.raises(ValueError):
             bad()
     assert len(fake.calls) == 5
+
+
+def test_batch_plan_refuses_bad_arguments_on_the_host(vp):
+    """vp_batch_plan (plans first) validates like vp_batch_create before any device work."""
+    P = ctypes.c_void_p
+    out = P(0)
+    plans = (P * 1)(None)
+    us = (P * 1)(None)
+    assert vp.lib.vp_batch_plan(plans, 0, None, None, us, ctypes.byref(out)) == vp.VP_ERR_ARG
+    assert vp.lib.vp_batch_plan(plans, 1, None, None, us, ctypes.byref(out)) == vp.VP_ERR_ARG
+    assert not out.value
