@@ -100,6 +100,8 @@ def main(argv=None):
     plain = F.PlainCascade(a.n, a.points)
     jb = F.draw_bowls(16, 6)
     verdicts = []
+    judged.run(jb[0], 0)  # warm-up: plans and workspaces of both routes
+    plain.run(jb[0], 0)
     torch.cuda.synchronize()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     ev[0].record()
