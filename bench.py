@@ -225,10 +225,9 @@ def kernel_name(sweep: int, m, engine, fused_source: bool = True) -> str:
     L = m[axis]
     if engine[axis]:
         if sweep == 2:
-            # the longest compiled line runs the pair-split form (its lines are always
-            # half-padded here: N <= M / 2 on every axis)
-            kern = "line2_conv_pair8_kernel" if L == 1280 else "line2_conv_pipe_kernel"
-            return f"{kern} (L={L})"
+            # the pipelined z sweep (its lines are always half-padded here: N <= M / 2 on
+            # every axis); at L = 1280 its 4-line form with the factors swapped (40 x 32)
+            return f"line2_conv_pipe_kernel (L={L})"
         kind = ("forward, source" if sweep == 0 and fused_source else "forward") if sweep < 2 else "inverse"
         return f"col2_kernel {kind} (L={L})"
     if sweep == 2:

@@ -196,6 +196,13 @@ cudaError_t line2_conv_pipe_launch(const LineSweep& p, cudaStream_t s, bool* use
     const long long wf = (long long)grid[f] * threads[f], wb = best ? (long long)grid[best] * threads[best] : 0;
     if (best == 0 || wf > wb || (wf == wb && rank(f) > rank(best))) best = f;
   }
+  // L = 1280: the swapped 40 x 32 split puts the 40-point DFTs in the pruned first and
+  // last steps (half their inputs zero, half their outputs cropped) and leaves radix-2
+  // 32-point DFTs for the full middle step: 7.64 against 8.34 ms for the pair-split
+  // form on the 600 x 600 x 640 grid, with fewer resident warps
+  if constexpr (kSwap) {
+    if (grid[5] >= 1 && (p.zform == 0 || p.zform == 5 || any)) best = 5;
+  }
   if (best == 0) return cudaSuccess;  // too large to pipeline (or the form asked for is not compiled)
   *used = true;
   if (p.nlines <= 0) return cudaSuccess;
