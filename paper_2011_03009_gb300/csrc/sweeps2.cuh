@@ -326,13 +326,24 @@ __global__ void __launch_bounds__(kThreads2) line2_batch_kernel(const __grid_con
 // memory at L >= 1024, or more CTAs share an SM.  NT threads a CTA (NT / 32 warps): the
 // 4-line form runs NL x max(A, B) threads, one task of each step per thread.
 // The staging pitch that holds rows a < conv_rows_in(A) of a line (odd: lanes = lines).
-__host__ __device__ constexpr int conv_stage_pitch(int A, int B) { return (B * conv_rows_in(A)) | 1; }
+// Pitches (in float2 elements) of the pipelined z sweep's buffers.  With 16 or 8 lines a
+// tile, the 16 lanes of a half-warp access the same element of 16 (or 8) lines, so an odd
+// pitch keeps them on distinct banks.  With 4 lines a half-warp touches 4 consecutive
+// elements of each of the 4 lines (or 4 twiddle rows): a pitch of 4 (mod 16) puts the
+// lines 8 banks apart, conflict-free.
+__host__ __device__ constexpr int pitch_mod(int v, int m, int r) { return v + (((r - v % m) % m) + m) % m; }
+__host__ __device__ constexpr int conv_line_pitch(int A, int B, int NL) {
+  return NL == 4 ? pitch_mod(A * (B + 1), 16, 4) : line2_pitch(A, B);
+}
+__host__ __device__ constexpr int conv_stage_pitch(int A, int B, int NL = kLines2) {
+  return NL == 4 ? pitch_mod(B * conv_rows_in(A), 16, 4) : (B * conv_rows_in(A)) | 1;
+}
 // Row pitch of the z sweep's twiddle table: 8 elements past B, so that rows k1 and k1 + 1
 // start 16 banks apart.
-__host__ __device__ constexpr int conv_tw_pitch(int B) { return B + 8; }
+__host__ __device__ constexpr int conv_tw_pitch(int B, int NL = kLines2) { return NL == 4 ? pitch_mod(B, 16, 4) : B + 8; }
 __host__ __device__ constexpr size_t conv_pipe_smem(int A, int B, int Oz, int NL = kLines2) {
-  return ((size_t)NL * line2_pitch(A, B) + (size_t)NL * conv_stage_pitch(A, B) + (size_t)(NL / 4) * Oz +
-          (size_t)A * conv_tw_pitch(B)) *
+  return ((size_t)NL * conv_line_pitch(A, B, NL) + (size_t)NL * conv_stage_pitch(A, B, NL) + (size_t)(NL / 4) * Oz +
+          (size_t)A * conv_tw_pitch(B, NL)) *
          sizeof(float2);
 }
 
@@ -347,9 +358,9 @@ __global__ void __launch_bounds__(NT)
                            long long ntiles, int NI) {
   constexpr int L = A * B;
   constexpr int BP = line2_bpitch(B);
-  constexpr int LP = line2_pitch(A, B);
+  constexpr int LP = conv_line_pitch(A, B, NL);
   constexpr int AH = conv_rows_in(A);
-  constexpr int TP = conv_tw_pitch(B);
+  constexpr int TP = conv_tw_pitch(B, NL);
   static_assert(B % 2 == 0, "the spectrum fold takes an even B");
   extern __shared__ float2 S[];
   const int Oz = p.Oz;  // shared by every plan of a batch group

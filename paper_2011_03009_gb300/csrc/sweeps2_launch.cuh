@@ -218,12 +218,13 @@ cudaError_t line2_conv_pipe_launch(const LineSweep& p, cudaStream_t s, bool* use
       break;
     case 3:
       if constexpr (L >= 512)
-        line2_conv_pipe_kernel<A, B, false, 4, NT4><<<(unsigned)g, NT4, smem[3], s>>>(p, none, units, ni);
+        line2_conv_pipe_kernel<A, B, false, 4, NT4><<<(unsigned)g, NT4, smem[3], s>>>(p, none, units,
+                                                                                     conv_stage_pitch(A, B, 4));
       break;
     case 5:
       if constexpr (kSwap)
         line2_conv_pipe_kernel<B, A, false, 4, conv4_threads(B, A)>
-            <<<(unsigned)g, conv4_threads(B, A), smem[5], s>>>(p, none, units, conv_stage_pitch(B, A));
+            <<<(unsigned)g, conv4_threads(B, A), smem[5], s>>>(p, none, units, conv_stage_pitch(B, A, 4));
       break;
     default:
       if constexpr (A == 32 && B == 40) line2_conv_pair8_kernel<A, B><<<(unsigned)g, kThreadsPair, smem[4], s>>>(p, units, ni);
