@@ -23,6 +23,21 @@ constexpr int kLines2 = 16;    // lines per CTA
 constexpr int kThreads2 = 256;
 
 __host__ __device__ constexpr int col2_pitch(int L) { return L + 1; }
+// Transpose buffer of a column tile, element (column line, k1, b) of x[B k1' ...]:
+// - 16 columns: line-major, pitch L + 1 (odd): the 16 lanes of a half-warp, one per
+//   column, fall on distinct banks;
+// - 8 columns: [k1][b][column] with rows of 8 (B + 1) elements: a half-warp holds 8
+//   columns x 2 consecutive b (first step) or 8 columns x 2 consecutive k1 (second
+//   step), and both read 16 distinct bank pairs (with the line-major odd pitch the
+//   second pair of a half-warp landed on the first's banks).
+__host__ __device__ constexpr size_t col2_smem_elems(int A, int B, int NL) {
+  return NL == 8 ? (size_t)A * 8 * (B + 1) : (size_t)NL * col2_pitch(A * B);
+}
+template <int A, int B, int NL>
+__device__ __forceinline__ int col2_at(int line, int k1, int b) {
+  if constexpr (NL == 8) return k1 * (8 * (B + 1)) + b * 8 + line;
+  else return line * col2_pitch(A * B) + k1 * B + b;
+}
 // Resident CTAs per SM the column kernels are compiled for: three while three tiles fit
 // in shared memory (the register cap then is 85 per thread), else one.
 __host__ __device__ constexpr int col2_min_blocks(int L, int dir) {
@@ -40,9 +55,7 @@ __host__ __device__ constexpr int line2_pitch(int A, int B) { return A * (B + 1)
 // rows_out <= L / 2 (cropped), so only rows a < AH of x[B a + b] are read or written.
 template <int A, int B, int DIR, bool SRC, bool HALF, int NL = kLines2>
 __device__ __forceinline__ void col2_tile(const ColSweep& p, int tile, float2* S) {
-  constexpr int L = A * B;
   constexpr int AH = HALF ? conv_rows_in(A) : A;
-  constexpr int LP = col2_pitch(L);
   constexpr int LSH = NL == 16 ? 4 : (NL == 8 ? 3 : 2);
   const int ncb = (p.C + NL - 1) / NL;
   const int o = tile / ncb;
@@ -87,19 +100,17 @@ __device__ __forceinline__ void col2_tile(const ColSweep& p, int tile, float2* S
         }
       }
       dft_reg_nz<A, false, AH>(v);
-      float2* s = S + line * LP + b;
-      s[0] = v[0];
+      S[col2_at<A, B, NL>(line, 0, b)] = v[0];
 #pragma unroll
-      for (int k1 = 1; k1 < A; ++k1) s[k1 * B] = cmul(v[k1], __ldg(&tw[b * k1]));
+      for (int k1 = 1; k1 < A; ++k1) S[col2_at<A, B, NL>(line, k1, b)] = cmul(v[k1], __ldg(&tw[b * k1]));
     }
     __syncthreads();
     for (int tau = threadIdx.x; tau < NL * A; tau += blockDim.x) {
       const int line = tau & (NL - 1);
       const int k1 = tau >> LSH;
       float2 z[B];
-      const float2* s = S + line * LP + k1 * B;
 #pragma unroll
-      for (int b = 0; b < B; ++b) z[b] = s[b];
+      for (int b = 0; b < B; ++b) z[b] = S[col2_at<A, B, NL>(line, k1, b)];
       dft_reg<B, false>(z);
       const int c = c0 + line;
       if (c < p.C) {
@@ -123,19 +134,17 @@ __device__ __forceinline__ void col2_tile(const ColSweep& p, int tile, float2* S
       for (int k2 = 0; k2 < B; ++k2)
         z[k2] = colok ? __ldg(&p.in[base + (long long)(k1 + A * k2) * p.in_rs]) : zero;
       dft_reg<B, true>(z);
-      float2* s = S + line * LP + k1 * B;
-      s[0] = z[0];
+      S[col2_at<A, B, NL>(line, k1, 0)] = z[0];
 #pragma unroll
-      for (int b = 1; b < B; ++b) s[b] = cmulc(z[b], __ldg(&tw[b * k1]));
+      for (int b = 1; b < B; ++b) S[col2_at<A, B, NL>(line, k1, b)] = cmulc(z[b], __ldg(&tw[b * k1]));
     }
     __syncthreads();
     for (int tau = threadIdx.x; tau < NL * B; tau += blockDim.x) {
       const int line = tau & (NL - 1);
       const int b = tau >> LSH;
       float2 v[A];
-      const float2* s = S + line * LP + b;
 #pragma unroll
-      for (int k1 = 0; k1 < A; ++k1) v[k1] = s[k1 * B];
+      for (int k1 = 0; k1 < A; ++k1) v[k1] = S[col2_at<A, B, NL>(line, k1, b)];
       dft_reg<A, true>(v);
       const int c = c0 + line;
       if (c < p.C) {

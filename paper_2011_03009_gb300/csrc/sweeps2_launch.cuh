@@ -26,7 +26,7 @@ cudaError_t col2_launch(const ColSweep& p, cudaStream_t s) {
   if constexpr (A * B > 512) {
     // one 16-column CTA per SM at these lengths: 8-column CTAs, two per SM, instead
     static volatile int granted8[64] = {0};
-    const size_t smem = (size_t)8 * col2_pitch(A * B) * sizeof(float2);
+    const size_t smem = col2_smem_elems(A, B, 8) * sizeof(float2);
     const long long blocks = (long long)((p.C + 7) / 8) * p.n_outer;
     if (blocks <= 0) return cudaSuccess;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
