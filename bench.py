@@ -1166,6 +1166,7 @@ def run_fno(args):
     t_judged = _dev_timeit(judged_all, 2, 1) / len(bowls)
     t_plain_route = _dev_timeit(plain_all, 2, 1) / len(bowls)
     fb = sum(v["fallback"] for v in verdicts) / len(verdicts)
+    locality = _box_locality(F, plain, bowls)
     _line("surrogate fields/s", 1e3 / t_inf, "fields/s", t_inf, reps, max(1, args.warmup), True,
           {"workload": "fno_infer_128cube_w48_l4_m32x32x16", "params": model.count,
            "weights": args.fno_checkpoint or "random initialisation"},
@@ -1173,7 +1174,42 @@ def run_fno(args):
           judged_route={"fields_per_s": 1e3 / t_judged, "ms_per_bowl": t_judged, "fallback_rate": fb,
                         "threshold": 1e-2, "judge_rel_l2": [v["judge_rel_l2"] for v in verdicts],
                         "bowls": len(bowls)},
-          plain_route={"fields_per_s": 1e3 / t_plain_route, "ms_per_bowl": t_plain_route})
+          plain_route={"fields_per_s": 1e3 / t_plain_route, "ms_per_bowl": t_plain_route},
+          box_locality=locality)
+
+
+def _box_locality(F, casc, bowls):
+    """How much of p2 on the focal box comes from sources outside the box: p2 from the
+    source restricted to the box's extent (zero elsewhere on the grid of harmonic 2)
+    against p2 from the whole source, relative L2 on the box.  The surrogate sees p1 on
+    the box only, so this part of p2 is outside what its input determines."""
+    import math
+    import torch
+    from paper_2011_03009_gb300 import vp
+    out = []
+    for i, b in enumerate(bowls):
+        casc.incident(b, i)
+        casc.harmonic(b, 2)
+        full = casc.to_box(b, 2).clone()
+        g = F.harmonic_grids(b, casc.n, casc.medium)
+        g2, g5 = g[2], g[5]
+        src = torch.empty_like(casc.f[1])
+        plan = casc.plans[2]
+        plan.source_assemble([casc.f[1]], f_out=src)
+        keep = torch.zeros_like(src)
+        sl = []
+        for a in range(3):
+            lo = max(0, math.ceil((g5.origin[a] - g2.origin[a]) / g2.h - 1e-9))
+            hi = min(g2.n[a] - 1, math.floor((g5.origin[a] + (g5.n[a] - 1) * g5.h - g2.origin[a]) / g2.h + 1e-9))
+            sl.append(slice(lo, hi + 1))
+        keep[sl[0], sl[1], sl[2]] = src[sl[0], sl[1], sl[2]]
+        local = torch.empty_like(src)
+        plan.apply(keep, local)
+        local_box = torch.empty_like(full)
+        vp.vp_restrict_to_nested_box(g2, local, g5, local_box)
+        out.append(float(((local_box - full).abs().pow(2).sum() / full.abs().pow(2).sum()).sqrt().item()))
+    return {"what": "rel-L2 on the box between p2 from the source inside the box only and p2 from the whole "
+                    "source (grid of harmonic 2)", "per_bowl": out, "median": sorted(out)[len(out) // 2]}
 
 
 def run_apply(args):
