@@ -21,7 +21,7 @@ def test_sweep_byte_model_is_25_plus_n_words_per_voxel():
 
 def test_kernel_names_follow_the_engine():
     assert bench.kernel_name(2, (512, 512, 512), (1, 1, 1)).startswith("line2_conv_pipe_kernel")
-    assert bench.kernel_name(2, (1200, 1200, 1280), (1, 1, 1)).startswith("line2_conv_pair8_kernel")
+    assert bench.kernel_name(2, (1200, 1200, 1280), (1, 1, 1)) == "line2_conv_pipe_kernel (L=1280)"
     assert bench.kernel_name(2, (200, 200, 200), (0, 0, 0)).startswith("line_sweep_kernel")
     assert "source" in bench.kernel_name(0, (512, 512, 512), (1, 1, 1))
     # after a nested source the first sweep reads f: the plain forward sweep
