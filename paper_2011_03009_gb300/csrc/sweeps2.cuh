@@ -167,12 +167,18 @@ __global__ void __launch_bounds__(kThreads2, col2_min_blocks(A * B, DIR)) col2_k
 
 // Long columns (L > 512): 8 columns per CTA, so that two CTAs share an SM; a quarter warp
 // covers one 64-byte row segment.
-// Three CTAs an SM up to L = 1024 (80 registers, a few bytes of spills; the column
-// sweeps wait on memory, so the third CTA's loads pay); two at L = 1200, whose tiles
-// allow no third CTA in shared memory.
-__host__ __device__ constexpr int col2_min_blocks8(int L) { return L <= 1024 ? 3 : 2; }
 template <int A, int B, int DIR, bool SRC, bool HALF>
-__global__ void __launch_bounds__(kThreads2, col2_min_blocks8(A * B)) col2_kernel8(const ColSweep p) {
+__global__ void __launch_bounds__(kThreads2, 2) col2_kernel8(const ColSweep p) {
+  extern __shared__ float2 S[];
+  col2_tile<A, B, DIR, SRC, HALF, 8>(p, blockIdx.x, S);
+}
+
+// The same, compiled for three CTAs an SM (80 registers, a few bytes of spills).  The
+// column sweeps wait on memory, and a third CTA's loads pay where rows are close in
+// memory; where each row of a column is megabytes from the next (the x sweeps of the
+// larger grids) the third CTA measured slower.  Used up to L = 864.
+template <int A, int B, int DIR, bool SRC, bool HALF>
+__global__ void __launch_bounds__(kThreads2, 3) col2_kernel8x3(const ColSweep p) {
   extern __shared__ float2 S[];
   col2_tile<A, B, DIR, SRC, HALF, 8>(p, blockIdx.x, S);
 }
