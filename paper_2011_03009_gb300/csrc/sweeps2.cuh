@@ -360,9 +360,11 @@ __host__ __device__ constexpr int conv_stage_pitch(int A, int B, int NL = kLines
 // Row pitch of the z sweep's twiddle table: 8 elements past B, so that rows k1 and k1 + 1
 // start 16 banks apart.
 __host__ __device__ constexpr int conv_tw_pitch(int B, int NL = kLines2) { return NL == 4 ? pitch_mod(B, 16, 4) : B + 8; }
-__host__ __device__ constexpr size_t conv_pipe_smem(int A, int B, int Oz, int NL = kLines2) {
+// TWG: the inter-step twiddles are read from the plan's table in global memory (through
+// L1) instead of a shared-memory copy, which frees A x conv_tw_pitch elements a CTA.
+__host__ __device__ constexpr size_t conv_pipe_smem(int A, int B, int Oz, int NL = kLines2, bool TWG = false) {
   return ((size_t)NL * conv_line_pitch(A, B, NL) + (size_t)NL * conv_stage_pitch(A, B, NL) + (size_t)(NL / 4) * Oz +
-          (size_t)A * conv_tw_pitch(B, NL)) *
+          (TWG ? 0 : (size_t)A * conv_tw_pitch(B, NL))) *
          sizeof(float2);
 }
 
@@ -371,7 +373,7 @@ __host__ __device__ constexpr size_t conv_pipe_smem(int A, int B, int Oz, int NL
 // numbered consecutively (plan i owns [offsets[i], offsets[i + 1])), all with the same
 // line length L and spectrum octant length; ni is the staging pitch for the longest
 // input line.
-template <int A, int B, bool BATCH, int NL = kLines2, int NT = kThreads2>
+template <int A, int B, bool BATCH, int NL = kLines2, int NT = kThreads2, bool TWG = false>
 __global__ void __launch_bounds__(NT)
     line2_conv_pipe_kernel(const __grid_constant__ LineSweep p, const __grid_constant__ BatchParams<LineSweep> bp,
                            long long ntiles, int NI) {
@@ -462,10 +464,13 @@ __global__ void __launch_bounds__(NT)
   // inter-step twiddles laid out as T[k1 TP + b] = w_L^(b k1), TP = B + 8: with either
   // index fixed at compile time, every read is a register base plus a constant offset,
   // and the two k1 rows a warp reads in step 2 fall on different banks
-  for (int i = threadIdx.x; i < A * TP; i += blockDim.x) {
-    const int k1 = i / TP, b = i - k1 * TP;
-    cp_async8(&T[i], &p.ax.tw[b < B ? b * k1 : 0], true);
+  if constexpr (!TWG) {
+    for (int i = threadIdx.x; i < A * TP; i += blockDim.x) {
+      const int k1 = i / TP, b = i - k1 * TP;
+      cp_async8(&T[i], &p.ax.tw[b < B ? b * k1 : 0], true);
+    }
   }
+  const float2* __restrict__ twg = p.ax.tw;
   long long t = blockIdx.x;
   if (t < ntiles) {
     const Rec r0 = read_rec(t);
@@ -502,7 +507,7 @@ __global__ void __launch_bounds__(NT)
       const float2* tw = T + b;
       s[0] = v[0];
 #pragma unroll
-      for (int k1 = 1; k1 < A; ++k1) s[k1 * BP] = cmul(v[k1], tw[k1 * TP]);
+      for (int k1 = 1; k1 < A; ++k1) s[k1 * BP] = cmul(v[k1], TWG ? __ldg(&twg[b * k1]) : tw[k1 * TP]);
     }
     __syncthreads();
     if (BATCH && tn < ntiles) nrec = read_rec(tn);
@@ -529,7 +534,7 @@ __global__ void __launch_bounds__(NT)
       const float2* tw = T + k1 * TP;
       s[0] = z[0];
 #pragma unroll
-      for (int b = 1; b < B; ++b) s[b] = cmulc(z[b], tw[b]);
+      for (int b = 1; b < B; ++b) s[b] = cmulc(z[b], TWG ? __ldg(&twg[b * k1]) : tw[b]);
     }
     __syncthreads();
     if (BATCH && tn < ntiles) nrec = read_rec(tn);

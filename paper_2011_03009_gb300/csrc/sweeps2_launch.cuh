@@ -151,6 +151,9 @@ cudaError_t line2_conv_pipe_launch(const LineSweep& p, cudaStream_t s, bool* use
   constexpr int L = A * B;
   constexpr int NT4 = conv4_threads(A, B);
   constexpr bool kSwap = A == 32 && B == 40;  // the transposed 4-line form (40 x 32) at L = 1280
+  // from L = 1024 the 4-line forms read their twiddles from global memory: the shared
+  // copy would cost them a resident CTA an SM
+  constexpr bool kTwg = L >= 1024;
   *used = false;
   // the kernel reads and writes the first half of each line only (zero-padded input,
   // cropped output); any other line goes to line2_kernel
@@ -159,8 +162,8 @@ cudaError_t line2_conv_pipe_launch(const LineSweep& p, cudaStream_t s, bool* use
   constexpr int kForms = 6;
   int grid[kForms] = {0, 0, 0, 0, 0, 0};  // resident CTAs on the GPU, per form
   int threads[kForms] = {0, kThreads2, kThreads2, NT4, kThreadsPair, conv4_threads(B, A)};
-  size_t smem[kForms] = {0, conv_pipe_smem(A, B, p.Oz), conv_pipe_smem(A, B, p.Oz, 8), conv_pipe_smem(A, B, p.Oz, 4),
-                         conv_pair8_smem(A, B, p.Oz), conv_pipe_smem(B, A, p.Oz, 4)};
+  size_t smem[kForms] = {0, conv_pipe_smem(A, B, p.Oz), conv_pipe_smem(A, B, p.Oz, 8), conv_pipe_smem(A, B, p.Oz, 4, kTwg),
+                         conv_pair8_smem(A, B, p.Oz), conv_pipe_smem(B, A, p.Oz, 4, kTwg)};
   cudaError_t e;
   // a form asked for that is not compiled for L, or does not fit, leaves the choice open
   bool any = p.zform == 0;
@@ -182,7 +185,7 @@ cudaError_t line2_conv_pipe_launch(const LineSweep& p, cudaStream_t s, bool* use
   }
   if constexpr (L >= 512) {
     if (want(3) && smem[3] <= 200 * 1024) {
-      e = resident_slots(line2_conv_pipe_kernel<A, B, false, 4, NT4>, smem[3], granted4, &grid[3], NT4);
+      e = resident_slots(line2_conv_pipe_kernel<A, B, false, 4, NT4, kTwg>, smem[3], granted4, &grid[3], NT4);
       if (e != cudaSuccess) return e;
     }
   }
@@ -194,8 +197,8 @@ cudaError_t line2_conv_pipe_launch(const LineSweep& p, cudaStream_t s, bool* use
   }
   if constexpr (kSwap) {
     if (want(5) && smem[5] <= 200 * 1024) {
-      e = resident_slots(line2_conv_pipe_kernel<B, A, false, 4, conv4_threads(B, A)>, smem[5], granted4t, &grid[5],
-                         conv4_threads(B, A));
+      e = resident_slots(line2_conv_pipe_kernel<B, A, false, 4, conv4_threads(B, A), kTwg>, smem[5], granted4t,
+                         &grid[5], conv4_threads(B, A));
       if (e != cudaSuccess) return e;
     }
   }
@@ -231,12 +234,12 @@ cudaError_t line2_conv_pipe_launch(const LineSweep& p, cudaStream_t s, bool* use
       break;
     case 3:
       if constexpr (L >= 512)
-        line2_conv_pipe_kernel<A, B, false, 4, NT4><<<(unsigned)g, NT4, smem[3], s>>>(p, none, units,
+        line2_conv_pipe_kernel<A, B, false, 4, NT4, kTwg><<<(unsigned)g, NT4, smem[3], s>>>(p, none, units,
                                                                                      conv_stage_pitch(A, B, 4));
       break;
     case 5:
       if constexpr (kSwap)
-        line2_conv_pipe_kernel<B, A, false, 4, conv4_threads(B, A)>
+        line2_conv_pipe_kernel<B, A, false, 4, conv4_threads(B, A), kTwg>
             <<<(unsigned)g, conv4_threads(B, A), smem[5], s>>>(p, none, units, conv_stage_pitch(B, A, 4));
       break;
     default:
