@@ -167,8 +167,11 @@ __global__ void __launch_bounds__(kThreads2, col2_min_blocks(A * B, DIR)) col2_k
 
 // Long columns (L > 512): 8 columns per CTA, so that two CTAs share an SM; a quarter warp
 // covers one 64-byte row segment.
+// 8 max(A, B) threads (rounded to warps), so that each step's tasks take one round: 320
+// at L = 1200 (30 x 40), whose first forward step has 320 tasks; 256 elsewhere.
+__host__ __device__ constexpr int col8_threads(int A, int B) { return ((8 * (A > B ? A : B) + 31) / 32) * 32; }
 template <int A, int B, int DIR, bool SRC, bool HALF>
-__global__ void __launch_bounds__(kThreads2, 2) col2_kernel8(const ColSweep p) {
+__global__ void __launch_bounds__(col8_threads(A, B), 2) col2_kernel8(const ColSweep p) {
   extern __shared__ float2 S[];
   col2_tile<A, B, DIR, SRC, HALF, 8>(p, blockIdx.x, S);
 }

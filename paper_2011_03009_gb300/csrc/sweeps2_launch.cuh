@@ -46,7 +46,7 @@ cudaError_t col2_launch(const ColSweep& p, cudaStream_t s) {
     auto k = col2_kernel8<A, B, DIR, SRC, HALF>;
     cudaError_t e = grant_smem(k, smem, granted8);
     if (e != cudaSuccess) return e;
-    k<<<(unsigned)blocks, kThreads2, smem, s>>>(p);
+    k<<<(unsigned)blocks, col8_threads(A, B), smem, s>>>(p);
     return cudaGetLastError();
   }
   const size_t smem = (size_t)kLines2 * col2_pitch(A * B) * sizeof(float2);
