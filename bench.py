@@ -579,6 +579,27 @@ def cufft_comparison(gw, flush):
     return out
 
 
+def gpu_local_cpus(dev_index: int):
+    """(NUMA node, set of CPUs) the GPU is attached to, from sysfs; None if unknown."""
+    try:
+        import torch
+        pr = torch.cuda.get_device_properties(dev_index)
+        base = f"/sys/bus/pci/devices/{pr.pci_domain_id:04x}:{pr.pci_bus_id:02x}:{pr.pci_device_id:02x}.0"
+        with open(base + "/numa_node") as fh:
+            node = int(fh.read().strip())
+        if node < 0:
+            return None
+        with open(f"/sys/devices/system/node/node{node}/cpulist") as fh:
+            text = fh.read().strip()
+        cpus = set()
+        for part in text.split(","):
+            lo, _, hi = part.partition("-")
+            cpus.update(range(int(lo), int(hi or lo) + 1))
+        return node, cpus
+    except (OSError, ValueError, AttributeError, RuntimeError):
+        return None
+
+
 def measure_e2e(gw, args, world, voxels, flush):
     """Same metric through the public API with pinned host inputs/outputs, copies inside.
 
@@ -589,6 +610,16 @@ def measure_e2e(gw, args, world, voxels, flush):
     before the first input copy to after the last result has reached host memory, so
     every step's copies are inside it."""
     import torch
+    # the pinned host buffers are allocated (and their pages placed) from the CPUs of the
+    # GPU's own NUMA node, and the copies are issued from there
+    local = gpu_local_cpus(gw.dev.index if gw.dev.index is not None else 0)
+    old_affinity = None
+    if local is not None and hasattr(os, "sched_setaffinity"):
+        try:
+            old_affinity = os.sched_getaffinity(0)
+            os.sched_setaffinity(0, local[1] & old_affinity or local[1])
+        except OSError:
+            old_affinity = None
     h2d_s, comp_s, d2h_s = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
     nb = 2
     h_p1 = [gw.p1.cpu().pin_memory() for _ in range(nb)]
@@ -650,7 +681,10 @@ def measure_e2e(gw, args, world, voxels, flush):
         reps.append(max_over_ranks(a.elapsed_time(b), world))
     ms = statistics.median(reps)
     gw.outs = saved
+    if old_affinity is not None:
+        os.sched_setaffinity(0, old_affinity)
     return {"value": voxels * K * world / (ms / 1e3), "unit": METRIC, "h2d_bytes_per_step": bi,
+            "host_numa_node": local[0] if local is not None else None,
             "d2h_bytes_per_step": bo, "steps": K, "repeats_ms_per_step": [round(r / K, 3) for r in reps],
             "pipelined": "inputs/outputs double-buffered on copy streams; median of three timed runs"}
 
