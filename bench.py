@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--grid", default="128,128,640", help="voxels per axis for --workload apply")
     ap.add_argument("--harmonic", type=int, default=2, help="harmonic for --workload apply")
     ap.add_argument("--zform", type=int, default=0, help="z-sweep form for --workload apply (VP_ZFORM_*)")
+    ap.add_argument("--staging", type=int, default=0,
+                    help="z-sweep staging for --workload apply: 0 bulk copies (4-line forms), 1 cp.async")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT comparison timing")
@@ -420,6 +422,10 @@ def run_ours(args, world, rank, local):
     barrier(world)
     t_wall = time.perf_counter() - t_wall0
     clk = clocks.stop()
+    # outside the timed region: no bounded device wait expired and no buffer was refused
+    for n, p in gw.plans.items():
+        if p.check() != 0:
+            raise RuntimeError(f"harmonic {n}: the plan's device status reports an expired wait or a refused buffer")
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = max_over_ranks(sum(step_ms), world)
     ms_per_step = total_ms / args.steps
@@ -1252,7 +1258,7 @@ def _box_locality(F, casc, bowls):
 
 
 def run_apply(args):
-    """One plan on one grid (--grid, --harmonic, --zform; 1.1 MHz water, 227 um voxels):
+    """One plan on one grid (--grid, --harmonic, --zform, --staging; 1.1 MHz water, 227 um voxels):
     the kernel spectrum, then --warmup and --steps applications of a random field, each
     after an L2 flush; per-sweep CUDA-event times.  The small single-sweep cases of the
     ncu captures under profiles/ run through this workload."""
@@ -1260,7 +1266,7 @@ def run_apply(args):
     from paper_2011_03009_gb300 import synth, vp
     n = tuple(int(v) for v in args.grid.split(","))
     g = synth.Grid(n, (0.0, 0.0, 0.0), 2.27e-4)
-    plan = vp.vp_plan(g, args.harmonic, 1.1e6, synth.WATER, zform=args.zform)
+    plan = vp.vp_plan(g, args.harmonic, 1.1e6, synth.WATER, zform=args.zform, staging=args.staging)
     plan.kernel_fft()
     f = torch.randn(n, dtype=torch.complex64, device="cuda")
     u = torch.empty_like(f)
@@ -1273,13 +1279,16 @@ def run_apply(args):
         flush.zero_()
         plan.apply(f, u)
     ms, cnt = plan.profile_read()
+    if plan.check() != vp.VP_OK:
+        raise RuntimeError("the plan's device status reports an expired wait or a refused buffer")
     inf = plan.info()
     by = sweep_bytes(tuple(inf.n), tuple(inf.m), args.harmonic, False)
     rows = [{"sweep": SWEEP_NAMES[i] if i else "x_forward", "ms": ms[i] / max(1, cnt[i]),
              "gbs": by[i] / (ms[i] / max(1, cnt[i]) * 1e-3) / 1e9} for i in range(5)]
     t = sum(r["ms"] for r in rows)
     _line(METRIC, g.voxels / (t * 1e-3), METRIC, t, args.steps, args.warmup, True,
-          {"workload": f"apply_{'x'.join(map(str, n))}_h{args.harmonic}", "m": list(inf.m), "zform": args.zform},
+          {"workload": f"apply_{'x'.join(map(str, n))}_h{args.harmonic}", "m": list(inf.m), "zform": args.zform,
+           "staging": args.staging},
           sweeps=rows)
 
 

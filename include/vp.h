@@ -56,8 +56,7 @@ extern "C" {
 #define VP_ERR_CUDA        -4  /* a CUDA runtime call or kernel launch failed              */
 #define VP_ERR_NOT_NESTED  -5  /* restriction target not inside the source grid           */
 #define VP_ERR_STATE       -6  /* call out of order (no staged source; spectrum not built) */
-#define VP_ERR_TIMEOUT     -7  /* reserved: no call of this build returns it (no kernel
-                                  waits on another launch or on the host)                  */
+#define VP_ERR_TIMEOUT     -7  /* a bounded device wait expired (reported by vp_plan_check) */
 #define VP_ERR_UNSUPPORTED -8  /* valid request outside what this build implements        */
 
 typedef void* vp_stream_t; /* cudaStream_t */
@@ -92,6 +91,15 @@ typedef struct vp_plan_opts {
                            0 = the form that keeps the most warps resident per SM.  A form
                            that is not compiled for M_z or does not fit in shared memory
                            is not used (the choice falls back as for 0)                  */
+    int staging;        /* input staging of the 4-line z-sweep forms: 0 = one bulk
+                           asynchronous copy per line and per spectrum octant line,
+                           completion counted on an mbarrier, wherever every line starts
+                           on a 16-byte boundary (even N_z), else as 1; 1 = 8-byte
+                           cp.async per element (the other forms always stage this way) */
+    int test_expire_waits; /* test hook, 0 in normal use: nonzero makes the bulk-staged z
+                           sweep issue none of its first copies, so that its bounded waits
+                           expire (about one second each) and the next vp_plan_check
+                           returns VP_ERR_TIMEOUT; the output of that apply is undefined */
 } vp_plan_opts;
 
 #define VP_ZFORM_AUTO   0
@@ -112,6 +120,7 @@ typedef struct vp_plan_info {
     int khat_ready;      /* 1 once vp_kernel_fft has been enqueued                       */
     int engine[3];       /* per axis: 1 two-level register FFT, 0 shared-memory radix passes */
     int zform;           /* z-sweep form asked for or chosen by the autotuner (VP_ZFORM_*) */
+    int staging;         /* vp_plan_opts.staging of the plan                             */
 } vp_plan_info;
 
 /* ---- plans --------------------------------------------------------------------
@@ -153,6 +162,16 @@ VP_API int vp_plan_retarget(vp_plan_t p, const vp_grid* g, int harmonic_n, doubl
 
 /* Fill *info.  Errors: VP_ERR_ARG. */
 VP_API int vp_plan_get_info(vp_plan_t p, vp_plan_info* info);
+
+/* Device-side status of the plan's kernels.  The bulk-staged z sweep waits on its
+ * copies with a bound of about one second (2^31 SM clock cycles) per wait; a CTA whose
+ * wait expires records it in a device word of the plan, waits (again bounded) for its
+ * copies still in flight and returns, leaving the context usable.  This call
+ * synchronises `stream`, reads and clears that word, and returns VP_ERR_TIMEOUT if a
+ * wait expired since the last check (the outputs of the applies in between are then
+ * undefined), VP_ERR_STATE if a kernel refused a buffer that broke the alignment its
+ * launcher checked, else VP_OK.  Errors: VP_ERR_ARG, VP_ERR_CUDA. */
+VP_API int vp_plan_check(vp_plan_t p, vp_stream_t stream);
 
 /* ---- kernel spectrum ----------------------------------------------------------
  * Build the spectrum of the circulant-embedded quadrature kernel (Section 6,

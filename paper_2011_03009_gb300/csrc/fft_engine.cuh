@@ -215,6 +215,51 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
+// ---- bulk asynchronous copies (one instruction per contiguous run) and mbarriers ----
+// A bulk copy moves `bytes` (a multiple of 16) from a 16-byte aligned global address to
+// a 16-byte aligned shared address and reports its bytes to the mbarrier at `bar`
+// (complete_tx).  A phase of the mbarrier completes when its expected arrivals have
+// arrived and every byte announced by arrive.expect_tx has landed.
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned arrivals) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(arrivals) : "memory");
+}
+// makes the initialised mbarriers visible to the bulk-copy unit
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+// one arrival that also announces `bytes` still to land in the current phase
+__device__ __forceinline__ void mbar_arrive_expect(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned bytes, unsigned bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned bar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// Bounded wait for the phase of parity `parity` on two mbarriers: false once about
+// `limit` SM clock cycles have passed without both completing.
+__device__ __forceinline__ bool mbar_wait2(unsigned bar0, unsigned bar1, unsigned parity, long long limit) {
+  const long long t0 = clock64();
+  bool d0 = false, d1 = false;
+  while (true) {
+    if (!d0) d0 = mbar_test(bar0, parity);
+    if (!d1) d1 = mbar_test(bar1, parity);
+    if (d0 && d1) return true;
+    if (clock64() - t0 > limit) return false;
+  }
+}
+// about one second at the GB300's 2.07 GHz SM clock
+constexpr long long kWaitCycles = 1LL << 31;
+
 // u / s for 0 <= u < 2^16 and 1 < s < 2^16 with magic = floor(2^32 / s) + 1: the
 // high word of u * magic is u/s + u e / 2^32 with 0 < e <= 1, exact below 2^16.
 // magic = 0 encodes s = 1.

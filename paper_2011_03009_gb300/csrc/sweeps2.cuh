@@ -38,6 +38,28 @@ __device__ __forceinline__ int col2_at(int line, int k1, int b) {
   if constexpr (NL == 8) return k1 * (8 * (B + 1)) + b * 8 + line;
   else return line * col2_pitch(A * B) + k1 * B + b;
 }
+// Loads of the column sweeps.  A CTA reads one 64-byte (8 columns) or 128-byte (16
+// columns) segment of each row of its columns, and the CTAs holding the neighbouring
+// columns of the same rows are launched next to it.  VP_COL_PREFETCH = 128 or 256 adds
+// the L2 prefetch-size hint, so that the first of them to miss fetches the whole aligned
+// block (a block never crosses a page, so the hint cannot reach unmapped memory); 0 is a
+// plain read-only load.
+#ifndef VP_COL_PREFETCH
+#define VP_COL_PREFETCH 256
+#endif
+__device__ __forceinline__ float2 ldg_col(const float2* q) {
+#if VP_COL_PREFETCH == 256
+  float2 v;
+  asm("ld.global.nc.L2::256B.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(q));
+  return v;
+#elif VP_COL_PREFETCH == 128
+  float2 v;
+  asm("ld.global.nc.L2::128B.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(q));
+  return v;
+#else
+  return __ldg(q);
+#endif
+}
 // Resident CTAs per SM the column kernels are compiled for: three while three tiles fit
 // in shared memory (the register cap then is 85 per thread), else one.
 __host__ __device__ constexpr int col2_min_blocks(int L, int dir) {
@@ -85,7 +107,7 @@ __device__ __forceinline__ void col2_tile(const ColSweep& p, int tile, float2* S
             const int row = B * a + b;
             if (colok && row < p.rows_in) {
               const long long off = base + (long long)row * p.in_rs;
-              const float2 x = __ldg(&pa[off]), y = __ldg(&pb[off]);
+              const float2 x = ldg_col(&pa[off]), y = ldg_col(&pb[off]);
               const float2 xy = cmul(x, y);
               v[a].x = fmaf(w, xy.x, v[a].x);
               v[a].y = fmaf(w, xy.y, v[a].y);
@@ -96,7 +118,7 @@ __device__ __forceinline__ void col2_tile(const ColSweep& p, int tile, float2* S
 #pragma unroll
         for (int a = 0; a < AH; ++a) {
           const int row = B * a + b;
-          v[a] = (colok && row < p.rows_in) ? __ldg(&p.in[base + (long long)row * p.in_rs]) : zero;
+          v[a] = (colok && row < p.rows_in) ? ldg_col(&p.in[base + (long long)row * p.in_rs]) : zero;
         }
       }
       dft_reg_nz<A, false, AH>(v);
@@ -132,7 +154,7 @@ __device__ __forceinline__ void col2_tile(const ColSweep& p, int tile, float2* S
       float2 z[B];
 #pragma unroll
       for (int k2 = 0; k2 < B; ++k2)
-        z[k2] = colok ? __ldg(&p.in[base + (long long)(k1 + A * k2) * p.in_rs]) : zero;
+        z[k2] = colok ? ldg_col(&p.in[base + (long long)(k1 + A * k2) * p.in_rs]) : zero;
       dft_reg<B, true>(z);
       S[col2_at<A, B, NL>(line, k1, 0)] = z[0];
 #pragma unroll
@@ -161,7 +183,7 @@ __device__ __forceinline__ void col2_tile(const ColSweep& p, int tile, float2* S
 
 template <int A, int B, int DIR, bool SRC, bool HALF>
 __global__ void __launch_bounds__(kThreads2, col2_min_blocks(A * B, DIR)) col2_kernel(const ColSweep p) {
-  extern __shared__ float2 S[];
+  extern __shared__ __align__(16) float2 S[];
   col2_tile<A, B, DIR, SRC, HALF>(p, blockIdx.x, S);
 }
 
@@ -172,7 +194,7 @@ __global__ void __launch_bounds__(kThreads2, col2_min_blocks(A * B, DIR)) col2_k
 __host__ __device__ constexpr int col8_threads(int A, int B) { return ((8 * (A > B ? A : B) + 31) / 32) * 32; }
 template <int A, int B, int DIR, bool SRC, bool HALF>
 __global__ void __launch_bounds__(col8_threads(A, B), 2) col2_kernel8(const ColSweep p) {
-  extern __shared__ float2 S[];
+  extern __shared__ __align__(16) float2 S[];
   col2_tile<A, B, DIR, SRC, HALF, 8>(p, blockIdx.x, S);
 }
 
@@ -182,7 +204,7 @@ __global__ void __launch_bounds__(col8_threads(A, B), 2) col2_kernel8(const ColS
 // larger grids) the third CTA measured slower.  Used up to L = 864.
 template <int A, int B, int DIR, bool SRC, bool HALF>
 __global__ void __launch_bounds__(kThreads2, 3) col2_kernel8x3(const ColSweep p) {
-  extern __shared__ float2 S[];
+  extern __shared__ __align__(16) float2 S[];
   col2_tile<A, B, DIR, SRC, HALF, 8>(p, blockIdx.x, S);
 }
 
@@ -211,7 +233,7 @@ __device__ __forceinline__ void copy_params(T* dst, const T* src) {
 template <int A, int B, int DIR, bool SRC, bool HALF>
 __global__ void __launch_bounds__(kThreads2, col2_min_blocks(A * B, DIR))
     col2_batch_kernel(const __grid_constant__ BatchParams<ColSweep> bp) {
-  extern __shared__ float2 S[];
+  extern __shared__ __align__(16) float2 S[];
   const int owner = batch_owner(bp, blockIdx.x);
   col2_tile<A, B, DIR, SRC, HALF>(bp.item[owner], blockIdx.x - bp.offsets[owner], S);
 }
@@ -322,13 +344,13 @@ __device__ __forceinline__ void line2_tile(const LineSweep& p, long long tile, f
 
 template <int A, int B, int MODE>
 __global__ void __launch_bounds__(kThreads2) line2_kernel(const LineSweep p) {
-  extern __shared__ float2 S[];
+  extern __shared__ __align__(16) float2 S[];
   line2_tile<A, B, MODE>(p, blockIdx.x, S);
 }
 
 template <int A, int B>
 __global__ void __launch_bounds__(kThreads2) line2_batch_kernel(const __grid_constant__ BatchParams<LineSweep> bp) {
-  extern __shared__ float2 S[];
+  extern __shared__ __align__(16) float2 S[];
   const int owner = batch_owner(bp, blockIdx.x);
   line2_tile<A, B, kConv>(bp.item[owner], blockIdx.x - bp.offsets[owner], S);
 }
@@ -365,8 +387,10 @@ __host__ __device__ constexpr int conv_stage_pitch(int A, int B, int NL = kLines
 __host__ __device__ constexpr int conv_tw_pitch(int B, int NL = kLines2) { return NL == 4 ? pitch_mod(B, 16, 4) : B + 8; }
 // TWG: the inter-step twiddles are read from the plan's table in global memory (through
 // L1) instead of a shared-memory copy, which frees A x conv_tw_pitch elements a CTA.
-__host__ __device__ constexpr size_t conv_pipe_smem(int A, int B, int Oz, int NL = kLines2, bool TWG = false) {
-  return ((size_t)NL * conv_line_pitch(A, B, NL) + (size_t)NL * conv_stage_pitch(A, B, NL) + (size_t)(NL / 4) * Oz +
+__host__ __device__ constexpr size_t conv_pipe_smem(int A, int B, int Oz, int NL = kLines2, bool TWG = false,
+                                                    bool BULK = false) {
+  return ((size_t)NL * conv_line_pitch(A, B, NL) + (size_t)NL * conv_stage_pitch(A, B, NL) +
+          (size_t)(NL / 4) * (Oz + (BULK ? 2 : 0)) +
           (TWG ? 0 : (size_t)A * conv_tw_pitch(B, NL))) *
          sizeof(float2);
 }
@@ -376,7 +400,12 @@ __host__ __device__ constexpr size_t conv_pipe_smem(int A, int B, int Oz, int NL
 // numbered consecutively (plan i owns [offsets[i], offsets[i + 1])), all with the same
 // line length L and spectrum octant length; ni is the staging pitch for the longest
 // input line.
-template <int A, int B, bool BATCH, int NL = kLines2, int NT = kThreads2, bool TWG = false>
+// BULK (single plan, 4-line tiles, lines and spectrum 16-byte aligned): each line and the
+// octant line are staged by one bulk asynchronous copy each (cp.async.bulk, issued by
+// one thread, completion counted in bytes on an mbarrier) instead of 8-byte cp.async
+// per element; the waits on those mbarriers are bounded (kWaitCycles), and a CTA whose
+// wait expires records it in *p.status and returns.
+template <int A, int B, bool BATCH, int NL = kLines2, int NT = kThreads2, bool TWG = false, bool BULK = false>
 __global__ void __launch_bounds__(NT)
     line2_conv_pipe_kernel(const __grid_constant__ LineSweep p, const __grid_constant__ BatchParams<LineSweep> bp,
                            long long ntiles, int NI) {
@@ -386,7 +415,7 @@ __global__ void __launch_bounds__(NT)
   constexpr int AH = conv_rows_in(A);
   constexpr int TP = conv_tw_pitch(B, NL);
   static_assert(B % 2 == 0, "the spectrum fold takes an even B");
-  extern __shared__ float2 S[];
+  extern __shared__ __align__(16) float2 S[];
   const int Oz = p.Oz;  // shared by every plan of a batch group
   constexpr int NG = NL / 4;       // mirror groups per CTA tile
   constexpr int LSH = NL == 16 ? 4 : (NL == 8 ? 3 : 2);
@@ -397,10 +426,13 @@ __global__ void __launch_bounds__(NT)
   constexpr int WPL = NW >= NL ? NW / NL : 1;
   constexpr int LPW = NW >= NL ? 1 : NL / NW;
   constexpr int STAGERS = NW >= NL ? NL * WPL : NW;
+  static_assert(!BULK || (!BATCH && NL == 4), "bulk staging: one plan, 4-line tiles");
   float2* I = S + NL * LP;
-  float2* K = I + NL * NI;  // [NG][Oz]
-  float2* T = K + NG * Oz;  // twiddles
+  float2* K = I + NL * NI;  // [NG][Oz]; with BULK one row of Oz + 2, element i at K[i + (oc Oz mod 2)]
+  float2* T = K + NG * (Oz + (BULK ? 2 : 0));  // twiddles
   __shared__ long long line_of[2][NL];
+  __shared__ __align__(8) unsigned long long bars[2];  // BULK: lines, spectrum
+  const unsigned bar_lines = smem_addr(&bars[0]), bar_spec = smem_addr(&bars[1]);
   __shared__ int oct_of[2][NG];
   __shared__ const LineSweep* plan_of[2];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -434,12 +466,22 @@ __global__ void __launch_bounds__(NT)
     r.spec_oct = tiles[ob + warp % NG];
     return r;
   };
-  auto fetch_lines = [&](const Rec& r, int slot) {
+  auto fetch_lines = [&](const Rec& r, int slot, bool skip) {
     const LineSweep& q = BATCH ? *r.q : p;
     const float2* data = q.data;
     const long long ld = q.ld;
     const int n_in = q.n_in;
-    if (warp < STAGERS) {
+    if constexpr (BULK) {
+      // thread h < 4 stages line slot h: one arrival each, announcing its bytes; a
+      // padding slot (-1) arrives with none and keeps stale data, whose output is
+      // never stored
+      if (threadIdx.x < NL && !skip) {
+        const long long l = r.my_line;
+        const unsigned bytes = l >= 0 ? 8u * (unsigned)n_in : 0u;
+        mbar_arrive_expect(bar_lines, bytes);
+        if (l >= 0) bulk_g2s(smem_addr(&I[threadIdx.x * NI]), data + l * ld, bytes, bar_lines);
+      }
+    } else if (warp < STAGERS) {
 #pragma unroll
       for (int h = 0; h < LPW; ++h) {
         const int b = NW >= NL ? warp % NL : warp + NW * h;
@@ -453,17 +495,42 @@ __global__ void __launch_bounds__(NT)
     if (threadIdx.x < NG) oct_of[slot][threadIdx.x] = r.my_oct;
     if (threadIdx.x == 0) plan_of[slot] = r.q;
   };
-  auto fetch_spectrum = [&](const Rec& r) {
+  auto fetch_spectrum = [&](const Rec& r, bool skip) {
     const float2* khat = BATCH ? r.q->khat : p.khat;
     const int g = warp % NG;
     const int oc = r.spec_oct;
     const float2* kl = khat + (oc < 0 ? 0 : (long long)oc * Oz);
-    for (int i = (warp / NG) * 32 + lane; i < Oz; i += (NW / NG) * 32)
-      cp_async8(&K[g * Oz + i], &kl[i], oc >= 0);
+    if constexpr (BULK) {
+      // element i of the octant line goes to K[s0 + i], s0 = (oc Oz) mod 2, so that the
+      // bulk run [s0, s0 + cnt) starts 16-byte aligned on both sides; the one element
+      // left over when Oz is odd travels by cp.async
+      if (threadIdx.x == 0 && !skip) {
+        const int s0 = oc < 0 ? 0 : (int)(((long long)oc * Oz) & 1);
+        const int cnt = (Oz - s0) & ~1;
+        mbar_arrive_expect(bar_spec, oc < 0 ? 0u : 8u * (unsigned)cnt);
+        if (oc >= 0) {
+          bulk_g2s(smem_addr(&K[2 * s0]), kl + s0, 8u * (unsigned)cnt, bar_spec);
+          if (s0 == 1) cp_async8(&K[1], kl, true);
+          if (s0 + cnt < Oz) cp_async8(&K[s0 + Oz - 1], kl + Oz - 1, true);
+        }
+      }
+    } else {
+      for (int i = (warp / NG) * 32 + lane; i < Oz; i += (NW / NG) * 32)
+        cp_async8(&K[g * Oz + i], &kl[i], oc >= 0);
+    }
   };
   static_assert((NL == 4 || NL == 8 || NL == 16) && NT % 32 == 0 && NW % NG == 0 && (NW >= NL || NL % NW == 0),
                 "tiles of 4, 8 or 16 lines; whole warps per mirror group and per staged line");
 
+  if constexpr (BULK) {
+    // the launcher takes this form only for aligned buffers; a violation is recorded
+    // (bit 1) and the CTA returns before any copy is issued
+    if (((smem_addr(I) | smem_addr(K)) & 15) != 0 || (((uintptr_t)p.data | (uintptr_t)p.khat) & 15) != 0 ||
+        ((p.ld | p.n_in) & 1) != 0) {
+      if (threadIdx.x == 0 && p.status != nullptr) atomicOr(p.status, 2);
+      return;
+    }
+  }
   // inter-step twiddles laid out as T[k1 TP + b] = w_L^(b k1), TP = B + 8: with either
   // index fixed at compile time, every read is a register base plus a constant offset,
   // and the two k1 rows a warp reads in step 2 fall on different banks
@@ -474,11 +541,25 @@ __global__ void __launch_bounds__(NT)
     }
   }
   const float2* __restrict__ twg = p.ax.tw;
+  if constexpr (BULK) {
+    // rows a < AH of a staged line hold elements [0, B AH); the bulk copies write
+    // [0, n_in), so the zeros of [n_in, B AH) are written once here
+    const int nz = B * AH - p.n_in;
+    if (nz > 0)
+      for (int i = threadIdx.x; i < NL * nz; i += blockDim.x) I[(i / nz) * NI + p.n_in + i % nz] = make_float2(0.f, 0.f);
+    if (threadIdx.x == 0) {
+      mbar_init(bar_lines, NL);
+      mbar_init(bar_spec, 1);
+      mbar_init_fence();
+    }
+    __syncthreads();
+  }
   long long t = blockIdx.x;
   if (t < ntiles) {
     const Rec r0 = read_rec(t);
-    fetch_lines(r0, 0);
-    fetch_spectrum(r0);
+    // test hook: the first copies are never issued, so the first wait expires
+    fetch_lines(r0, 0, BULK && p.expire_waits);
+    fetch_spectrum(r0, BULK && p.expire_waits);
   }
   asm volatile("cp.async.commit_group;\n" ::: "memory");
   for (int it = 0; t < ntiles; t += gridDim.x, ++it) {
@@ -489,7 +570,18 @@ __global__ void __launch_bounds__(NT)
     Rec nrec{};
     if (!BATCH && tn < ntiles) nrec = read_rec(tn);
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-    __syncthreads();
+    if constexpr (BULK) {
+      // both mbarriers complete one phase per tile
+      const bool ok = mbar_wait2(bar_lines, bar_spec, (unsigned)(it & 1), kWaitCycles);
+      if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0 && p.status != nullptr) atomicOr(p.status, 1);
+        // copies still in flight land before the CTA's shared memory is given up
+        mbar_wait2(bar_lines, bar_spec, (unsigned)(it & 1), kWaitCycles);
+        return;
+      }
+    } else {
+      __syncthreads();
+    }
     const LineSweep& q = BATCH ? *plan_of[cur] : p;
     const int n_out = q.n_out;
     float2* const data = q.data;
@@ -514,7 +606,7 @@ __global__ void __launch_bounds__(NT)
     }
     __syncthreads();
     if (BATCH && tn < ntiles) nrec = read_rec(tn);
-    if (tn < ntiles) fetch_lines(nrec, cur ^ 1);
+    if (tn < ntiles) fetch_lines(nrec, cur ^ 1, false);
     asm volatile("cp.async.commit_group;\n" ::: "memory");
     // forward step 2, spectrum multiply, inverse step 2 (lanes = lines again)
     for (int tau = threadIdx.x; tau < NL * A; tau += blockDim.x) {
@@ -525,11 +617,13 @@ __global__ void __launch_bounds__(NT)
 #pragma unroll
       for (int b = 0; b < B; ++b) z[b] = s[b];
       dft_reg<B, false>(z);
-      if (oct_of[cur][line >> 2] >= 0) {
+      const int oc = oct_of[cur][line >> 2];
+      if (oc >= 0) {
         // frequency f = k1 + A k2 folds to min(f, L - f): f itself below k2 = B / 2,
         // L - f from there on (B is even), so both reads take constant offsets
-        const float2* lo = K + (line >> 2) * Oz + k1;
-        const float2* hi = K + (line >> 2) * Oz + (L - k1);
+        const int kb = BULK ? (int)(((long long)oc * Oz) & 1) : (line >> 2) * Oz;
+        const float2* lo = K + kb + k1;
+        const float2* hi = K + kb + (L - k1);
 #pragma unroll
         for (int k2 = 0; k2 < B; ++k2) z[k2] = cmul(z[k2], 2 * k2 < B ? lo[A * k2] : hi[-A * k2]);
       }
@@ -541,7 +635,7 @@ __global__ void __launch_bounds__(NT)
     }
     __syncthreads();
     if (BATCH && tn < ntiles) nrec = read_rec(tn);
-    if (tn < ntiles) fetch_spectrum(nrec);
+    if (tn < ntiles) fetch_spectrum(nrec, false);
     asm volatile("cp.async.commit_group;\n" ::: "memory");
     // inverse step 1 and store
     for (int tau = threadIdx.x; tau < NL * B; tau += blockDim.x) {

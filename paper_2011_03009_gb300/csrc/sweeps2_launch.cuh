@@ -148,6 +148,8 @@ cudaError_t line2_conv_pipe_launch(const LineSweep& p, cudaStream_t s, bool* use
   static volatile int granted4[64] = {0};
   static volatile int grantedp[64] = {0};
   static volatile int granted4t[64] = {0};
+  static volatile int granted4b[64] = {0};
+  static volatile int granted4tb[64] = {0};
   constexpr int L = A * B;
   constexpr int NT4 = conv4_threads(A, B);
   constexpr bool kSwap = A == 32 && B == 40;  // the transposed 4-line form (40 x 32) at L = 1280
@@ -161,11 +163,16 @@ cudaError_t line2_conv_pipe_launch(const LineSweep& p, cudaStream_t s, bool* use
   // cropped output); any other line goes to line2_kernel
   if (2 * p.n_in > L || 2 * p.n_out > L) return cudaSuccess;
   const int ni = conv_stage_pitch(A, B);
+  // the 4-line forms stage each line and the octant line with one bulk copy where every
+  // line starts and ends on a 16-byte boundary (cudaMalloc'd buffers, even n_in and ld)
+  const bool bulk = p.staging == 0 && p.n_in % 2 == 0 && p.ld % 2 == 0 && ((uintptr_t)p.data & 15) == 0 &&
+                    ((uintptr_t)p.khat & 15) == 0;
   constexpr int kForms = 6;
   int grid[kForms] = {0, 0, 0, 0, 0, 0};  // resident CTAs on the GPU, per form
   int threads[kForms] = {0, kThreads2, kThreads2, NT4, kThreadsPair, conv4_threads(B, A)};
-  size_t smem[kForms] = {0, conv_pipe_smem(A, B, p.Oz), conv_pipe_smem(A, B, p.Oz, 8), conv_pipe_smem(A, B, p.Oz, 4, kTwg),
-                         conv_pair8_smem(A, B, p.Oz), conv_pipe_smem(B, A, p.Oz, 4, kTwg)};
+  size_t smem[kForms] = {0, conv_pipe_smem(A, B, p.Oz), conv_pipe_smem(A, B, p.Oz, 8),
+                         conv_pipe_smem(A, B, p.Oz, 4, kTwg, bulk), conv_pair8_smem(A, B, p.Oz),
+                         conv_pipe_smem(B, A, p.Oz, 4, kTwg, bulk)};
   cudaError_t e;
   // a form asked for that is not compiled for L, or does not fit, leaves the choice open
   bool any = p.zform == 0;
@@ -187,7 +194,8 @@ cudaError_t line2_conv_pipe_launch(const LineSweep& p, cudaStream_t s, bool* use
   }
   if constexpr (L >= 512) {
     if (want(3) && smem[3] <= 200 * 1024) {
-      e = resident_slots(line2_conv_pipe_kernel<A, B, false, 4, NT4, kTwg>, smem[3], granted4, &grid[3], NT4);
+      e = bulk ? resident_slots(line2_conv_pipe_kernel<A, B, false, 4, NT4, kTwg, true>, smem[3], granted4b, &grid[3], NT4)
+               : resident_slots(line2_conv_pipe_kernel<A, B, false, 4, NT4, kTwg>, smem[3], granted4, &grid[3], NT4);
       if (e != cudaSuccess) return e;
     }
   }
@@ -199,8 +207,10 @@ cudaError_t line2_conv_pipe_launch(const LineSweep& p, cudaStream_t s, bool* use
   }
   if constexpr (kSwap) {
     if (want(5) && smem[5] <= 200 * 1024) {
-      e = resident_slots(line2_conv_pipe_kernel<B, A, false, 4, conv4_threads(B, A), kTwg>, smem[5], granted4t,
-                         &grid[5], conv4_threads(B, A));
+      e = bulk ? resident_slots(line2_conv_pipe_kernel<B, A, false, 4, conv4_threads(B, A), kTwg, true>, smem[5],
+                                granted4tb, &grid[5], conv4_threads(B, A))
+               : resident_slots(line2_conv_pipe_kernel<B, A, false, 4, conv4_threads(B, A), kTwg>, smem[5], granted4t,
+                                &grid[5], conv4_threads(B, A));
       if (e != cudaSuccess) return e;
     }
   }
@@ -235,14 +245,24 @@ cudaError_t line2_conv_pipe_launch(const LineSweep& p, cudaStream_t s, bool* use
       if constexpr (L >= 640) line2_conv_pipe_kernel<A, B, false, 8><<<(unsigned)g, kThreads2, smem[2], s>>>(p, none, units, ni);
       break;
     case 3:
-      if constexpr (L >= 512)
-        line2_conv_pipe_kernel<A, B, false, 4, NT4, kTwg><<<(unsigned)g, NT4, smem[3], s>>>(p, none, units,
-                                                                                     conv_stage_pitch(A, B, 4));
+      if constexpr (L >= 512) {
+        if (bulk)
+          line2_conv_pipe_kernel<A, B, false, 4, NT4, kTwg, true>
+              <<<(unsigned)g, NT4, smem[3], s>>>(p, none, units, conv_stage_pitch(A, B, 4));
+        else
+          line2_conv_pipe_kernel<A, B, false, 4, NT4, kTwg>
+              <<<(unsigned)g, NT4, smem[3], s>>>(p, none, units, conv_stage_pitch(A, B, 4));
+      }
       break;
     case 5:
-      if constexpr (kSwap)
-        line2_conv_pipe_kernel<B, A, false, 4, conv4_threads(B, A), kTwg>
-            <<<(unsigned)g, conv4_threads(B, A), smem[5], s>>>(p, none, units, conv_stage_pitch(B, A, 4));
+      if constexpr (kSwap) {
+        if (bulk)
+          line2_conv_pipe_kernel<B, A, false, 4, conv4_threads(B, A), kTwg, true>
+              <<<(unsigned)g, conv4_threads(B, A), smem[5], s>>>(p, none, units, conv_stage_pitch(B, A, 4));
+        else
+          line2_conv_pipe_kernel<B, A, false, 4, conv4_threads(B, A), kTwg>
+              <<<(unsigned)g, conv4_threads(B, A), smem[5], s>>>(p, none, units, conv_stage_pitch(B, A, 4));
+      }
       break;
     default:
       if constexpr (A == 32 && B == 40) line2_conv_pair8_kernel<A, B><<<(unsigned)g, kThreadsPair, smem[4], s>>>(p, units, ni);

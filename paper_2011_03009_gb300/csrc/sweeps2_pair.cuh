@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(kThreadsPair)
   static_assert(H % 2 == 0, "the spectrum fold splits the half-length DFT at H / 2");
   static_assert(2 * NL * A == kThreadsPair, "one step-2 task per lane pair");
   static_assert(NL * B <= kThreadsPair, "one step-1 task per thread at most");
-  extern __shared__ float2 S[];
+  extern __shared__ __align__(16) float2 S[];
   const int Oz = p.Oz;
   float2* I = S + NL * LP;
   float2* K = I + NL * NI;   // [NG][Oz]

@@ -48,6 +48,9 @@ struct vp_plan_s {
   int npass[3] = {0, 0, 0};
   int fast[3] = {0, 0, 0};  // axis handled by the two-level register engine
   int zform = 0;            // pipelined z-sweep form (VP_ZFORM_*)
+  int staging = 0;          // vp_plan_opts.staging
+  int expire_waits = 0;     // vp_plan_opts.test_expire_waits
+  int* status = nullptr;    // device word: bit 0 a bounded wait expired, bit 1 an alignment refusal
   float2* tw[3] = {nullptr, nullptr, nullptr};
   int* pos[3] = {nullptr, nullptr, nullptr};   // frequency -> position after the DIF passes
   int* fold[3] = {nullptr, nullptr, nullptr};  // position -> min(f, M - f)
@@ -164,6 +167,7 @@ void free_plan(vp_plan_s* p) {
   cudaFree(p->wsA);
   cudaFree(p->wsB);
   cudaFree(p->ztiles);
+  cudaFree(p->status);
   for (auto& r : p->prof) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
@@ -386,6 +390,9 @@ LineSweep line_params(const vp_plan_s* p) {
   l.tiles = p->ztiles;
   l.fold_z = p->fold[2];
   l.zform = p->zform;
+  l.staging = p->staging;
+  l.expire_waits = p->expire_waits;
+  l.status = p->status;
   return l;
 }
 
@@ -612,12 +619,15 @@ VP_API int vp_plan(const vp_grid* g, int harmonic_n, double f0_hz, const vp_medi
     return VP_ERR_ARG;
   if (harmonic_n - 1 > vp::kMaxLower) return VP_ERR_UNSUPPORTED;
   if (opts && (opts->zform < VP_ZFORM_AUTO || opts->zform > VP_ZFORM_TILE4T)) return VP_ERR_ARG;
+  if (opts && (opts->staging < 0 || opts->staging > 1)) return VP_ERR_ARG;
   if (opts && opts->autotune) {
     bool explicit_choice = false;
     for (int a = 0; a < 3; ++a) explicit_choice |= opts->m[a] != 0 || opts->radix[a][0] != 0;
     if (!explicit_choice) {
       vp_plan_opts o{};
       o.zform = opts->zform;
+      o.staging = opts->staging;
+      o.test_expire_waits = opts->test_expire_waits;
       const std::array<int, 3> key = {g->n[0], g->n[1], g->n[2]};
       bool cached = false;
       {
@@ -683,6 +693,8 @@ VP_API int vp_plan(const vp_grid* g, int harmonic_n, double f0_hz, const vp_medi
     for (int i = 0; i < vp::kMaxPass; ++i) p->radix[a][i] = radix[a][i];
   }
   p->zform = opts ? opts->zform : 0;
+  p->staging = opts ? opts->staging : 0;
+  p->expire_waits = opts && opts->test_expire_waits ? 1 : 0;
   set_physics(p, g, harmonic_n, f0_hz, med);
 
   int st = VP_OK;
@@ -695,6 +707,8 @@ VP_API int vp_plan(const vp_grid* g, int harmonic_n, double f0_hz, const vp_medi
   if (st == VP_OK) st = cuda_status(cudaMalloc((void**)&p->wsA, nA * sizeof(float2)));
   if (st == VP_OK) st = cuda_status(cudaMalloc((void**)&p->wsB, nB * sizeof(float2)));
   if (st == VP_OK) st = cuda_status(cudaMalloc((void**)&p->khat, nK * sizeof(float2)));
+  if (st == VP_OK) st = cuda_status(cudaMalloc((void**)&p->status, sizeof(int)));
+  if (st == VP_OK) st = cuda_status(cudaMemset(p->status, 0, sizeof(int)));
   if (st != VP_OK) {
     free_plan(p);
     return st;
@@ -743,7 +757,20 @@ VP_API int vp_plan_get_info(vp_plan_t p, vp_plan_info* info) {
   info->khat_ready = p->khat_ready ? 1 : 0;
   for (int a = 0; a < 3; ++a) info->engine[a] = p->fast[a];
   info->zform = p->zform;
+  info->staging = p->staging;
   return VP_OK;
+}
+
+VP_API int vp_plan_check(vp_plan_t p, vp_stream_t stream) {
+  if (!p) return VP_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  int v = 0;
+  VP_TRY_CUDA(cudaMemcpyAsync(&v, p->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  VP_TRY_CUDA(cudaStreamSynchronize(s));
+  if (v == 0) return VP_OK;
+  VP_TRY_CUDA(cudaMemsetAsync(p->status, 0, sizeof(int), s));
+  VP_TRY_CUDA(cudaStreamSynchronize(s));
+  return (v & 1) ? VP_ERR_TIMEOUT : VP_ERR_STATE;
 }
 
 VP_API int vp_kernel_fft(vp_plan_t p, vp_stream_t stream) {

@@ -75,6 +75,9 @@ struct LineSweep {
   const int* tiles;     // 20 ints per tile
   const int* fold_z;    // z position -> folded frequency
   int zform;            // pipelined z-sweep form (VP_ZFORM_*; 0 = chosen by occupancy)
+  int staging;          // 0: bulk copies where the 4-line forms allow them, 1: cp.async only
+  int expire_waits;     // test hook: the bulk-staged z sweep issues no first copies
+  int* status;          // device word; bit 0 set when a bounded wait expired
 };
 
 enum SweepDir { kForward = 0, kInverse = 1 };

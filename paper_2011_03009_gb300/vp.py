@@ -48,7 +48,7 @@ class vp_medium(ctypes.Structure):
 
 class vp_plan_opts(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int * 3), ("radix", (ctypes.c_int * MAX_PASS) * 3), ("autotune", ctypes.c_int),
-                ("zform", ctypes.c_int)]
+                ("zform", ctypes.c_int), ("staging", ctypes.c_int), ("test_expire_waits", ctypes.c_int)]
 
 
 class vp_plan_info(ctypes.Structure):
@@ -56,7 +56,7 @@ class vp_plan_info(ctypes.Structure):
                 ("k_re", ctypes.c_double), ("k_im", ctypes.c_double), ("c_n", ctypes.c_double),
                 ("self_re", ctypes.c_double), ("self_im", ctypes.c_double),
                 ("workspace_bytes", ctypes.c_ulonglong), ("khat_ready", ctypes.c_int), ("engine", ctypes.c_int * 3),
-                ("zform", ctypes.c_int)]
+                ("zform", ctypes.c_int), ("staging", ctypes.c_int)]
 
 
 def _load():
@@ -72,6 +72,7 @@ def _load():
         "vp_destroy": (I, [P]),
         "vp_plan_retarget": (I, [P, ctypes.POINTER(vp_grid), I, D, ctypes.POINTER(vp_medium)]),
         "vp_plan_get_info": (I, [P, ctypes.POINTER(vp_plan_info)]),
+        "vp_plan_check": (I, [P, P]),
         "vp_kernel_fft": (I, [P, P]),
         "vp_kernel_spectrum_get": (I, [P, P, P]),
         "vp_kernel_spectrum_set": (I, [P, P, P]),
@@ -177,7 +178,7 @@ class Plan:
 
     def __init__(self, grid, harmonic: int, f0: float, medium, m: Optional[Sequence[int]] = None,
                  radix: Optional[Sequence[Sequence[int]]] = None, autotune: bool = False, stream=None,
-                 zform: int = 0):
+                 zform: int = 0, staging: int = 0, test_expire_waits: bool = False):
         self.grid = grid
         self.harmonic = int(harmonic)
         self._h = ctypes.c_void_p(0)
@@ -191,6 +192,8 @@ class Plan:
                     opts.radix[a][i] = int(r)
         opts.autotune = 1 if autotune else 0
         opts.zform = int(zform)
+        opts.staging = int(staging)
+        opts.test_expire_waits = 1 if test_expire_waits else 0
         g = grid if isinstance(grid, vp_grid) else grid_of(grid)
         self._g = g
         med = medium if isinstance(medium, vp_medium) else make_medium(medium)
@@ -211,6 +214,15 @@ class Plan:
         inf = vp_plan_info()
         _check(lib.vp_plan_get_info(self._h, ctypes.byref(inf)), "vp_plan_get_info")
         return inf
+
+    def check(self, stream=None) -> int:
+        """vp_plan_check: synchronise the stream, read and clear the plan's device status
+        word; returns VP_OK, VP_ERR_TIMEOUT (a bounded wait expired) or VP_ERR_STATE (an
+        alignment refusal) without raising, since the caller asked for the status."""
+        st = lib.vp_plan_check(self._h, _stream(stream))
+        if st not in (VP_OK, VP_ERR_TIMEOUT, VP_ERR_STATE):
+            _check(st, "vp_plan_check")
+        return st
 
     def kernel_fft(self, stream=None):
         _check(lib.vp_kernel_fft(self._h, _stream(stream)), "vp_kernel_fft")

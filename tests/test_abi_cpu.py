@@ -31,7 +31,7 @@ def test_header_declares_the_boundary():
     names = _declared_functions()
     for required in ("vp_plan", "vp_kernel_fft", "vp_source_assemble", "vp_apply",
                      "vp_restrict_to_nested_box", "vp_destroy", "vp_status_string",
-                     "vp_batch_create", "vp_batch_plan", "vp_batch_run", "vp_apply_static",
+                     "vp_batch_create", "vp_batch_plan", "vp_batch_run", "vp_apply_static", "vp_plan_check",
                      "vp_fno_forward", "vp_fno_backward", "vp_fno_adam"):
         assert required in names
 
@@ -76,6 +76,12 @@ def test_plan_rejects_bad_arguments_on_the_host(vp):
     assert _plan_status(vp, good, med=neg_att)[0] == vp.VP_ERR_ARG
     st, h = _plan_status(vp, good, harmonic=99)
     assert st == vp.VP_ERR_UNSUPPORTED and not h.value
+    for staging in (-1, 2):                      # 0 bulk copies, 1 cp.async
+        o = vp.vp_plan_opts()
+        o.staging = staging
+        st, h = _plan_status(vp, good, opts=o)
+        assert st == vp.VP_ERR_ARG and not h.value
+    assert vp.lib.vp_plan_check(None, None) == vp.VP_ERR_ARG
 
 
 def test_plan_rejects_bad_sizes_on_the_host(vp):

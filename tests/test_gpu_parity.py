@@ -402,6 +402,72 @@ def test_every_z_sweep_form_matches_oracle(vp, nz):
         plan.close()
 
 
+@pytest.mark.parametrize("nz", [256, 320, 432, 640])
+def test_bulk_and_element_staging_match_oracle_and_each_other(vp, nz):
+    """The 4-line z-sweep forms stage their lines and octant lines by bulk asynchronous
+    copies (staging 0) or by per-element cp.async (staging 1): both match the oracle and
+    give the same floating-point result, and the plan's device status stays clear."""
+    n = (9, 7, nz)
+    g = grid(n)
+    k = physics.wavenumber(2, 1.1e6, synth.WATER)
+    f = synth.random_field(n, seed=nz + 1)
+    ref = potential.apply_fft(f, g.h, k)
+    form = vp.VP_ZFORM_TILE4T if nz == 640 else vp.VP_ZFORM_TILE4
+    outs = []
+    for staging in (0, 1):
+        plan = vp.vp_plan(g, 2, 1.1e6, synth.WATER, zform=form, staging=staging)
+        assert plan.info().staging == staging
+        vp.vp_kernel_fft(plan)
+        u = torch.empty(n, dtype=torch.complex64, device="cuda")
+        vp.vp_apply(plan, dev(f), u)
+        assert plan.check() == vp.VP_OK
+        outs.append(host(u))
+        assert rel_l2(outs[-1], ref) <= REL_L2, staging
+        plan.close()
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_odd_line_length_falls_back_to_element_staging(vp):
+    """N_z odd: a line is not a whole number of 16-byte units, so the 4-line form keeps
+    cp.async staging; the result matches the oracle and no refusal is recorded."""
+    n = (6, 5, 255)
+    g = grid(n)
+    k = physics.wavenumber(2, 1.0e6, synth.WATER)
+    f = synth.random_field(n, seed=255)
+    plan = vp.vp_plan(g, 2, 1.0e6, synth.WATER, zform=vp.VP_ZFORM_TILE4)
+    assert plan.info().m[2] == 512
+    vp.vp_kernel_fft(plan)
+    u = torch.empty(n, dtype=torch.complex64, device="cuda")
+    vp.vp_apply(plan, dev(f), u)
+    assert plan.check() == vp.VP_OK
+    assert rel_l2(host(u), potential.apply_fft(f, g.h, k)) <= REL_L2
+    plan.close()
+
+
+def test_expired_bulk_wait_is_reported_and_the_context_stays_usable(vp):
+    """Test hook: the bulk-staged z sweep issues none of its first copies, so each CTA's
+    bounded wait (about one second) expires; the CTAs record it and return, vp_plan_check
+    reports VP_ERR_TIMEOUT once and clears it, and a normal plan then runs and matches the
+    oracle on the same context."""
+    n = (8, 6, 320)
+    g = grid(n)
+    k = physics.wavenumber(2, 1.0e6, synth.WATER)
+    f = synth.random_field(n, seed=5)
+    stalled = vp.vp_plan(g, 2, 1.0e6, synth.WATER, zform=vp.VP_ZFORM_TILE4, test_expire_waits=True)
+    vp.vp_kernel_fft(stalled)
+    u = torch.empty(n, dtype=torch.complex64, device="cuda")
+    vp.vp_apply(stalled, dev(f), u)
+    assert stalled.check() == vp.VP_ERR_TIMEOUT
+    assert stalled.check() == vp.VP_OK
+    stalled.close()
+    plan = vp.vp_plan(g, 2, 1.0e6, synth.WATER, zform=vp.VP_ZFORM_TILE4)
+    vp.vp_kernel_fft(plan)
+    vp.vp_apply(plan, dev(f), u)
+    assert plan.check() == vp.VP_OK
+    assert rel_l2(host(u), potential.apply_fft(f, g.h, k)) <= REL_L2
+    plan.close()
+
+
 def test_autotuned_z_form_matches_oracle(vp):
     """The autotuner times the z-sweep forms for M_z >= 512 and keeps one; the plan it
     returns reports that form and matches the oracle."""
