@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--zform", type=int, default=0, help="z-sweep form for --workload apply (VP_ZFORM_*)")
     ap.add_argument("--staging", type=int, default=0,
                     help="z-sweep staging for --workload apply: 0 bulk copies (4-line forms), 1 cp.async")
+    ap.add_argument("--layout", type=int, default=0,
+                    help="x-sweep output layout for --workload apply: 0 grouped by 4 y-planes, 1 plain")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT comparison timing")
@@ -1258,7 +1260,7 @@ def _box_locality(F, casc, bowls):
 
 
 def run_apply(args):
-    """One plan on one grid (--grid, --harmonic, --zform, --staging; 1.1 MHz water, 227 um voxels):
+    """One plan on one grid (--grid, --harmonic, --zform, --staging, --layout; 1.1 MHz water, 227 um voxels):
     the kernel spectrum, then --warmup and --steps applications of a random field, each
     after an L2 flush; per-sweep CUDA-event times.  The small single-sweep cases of the
     ncu captures under profiles/ run through this workload."""
@@ -1266,7 +1268,8 @@ def run_apply(args):
     from paper_2011_03009_gb300 import synth, vp
     n = tuple(int(v) for v in args.grid.split(","))
     g = synth.Grid(n, (0.0, 0.0, 0.0), 2.27e-4)
-    plan = vp.vp_plan(g, args.harmonic, 1.1e6, synth.WATER, zform=args.zform, staging=args.staging)
+    plan = vp.vp_plan(g, args.harmonic, 1.1e6, synth.WATER, zform=args.zform, staging=args.staging,
+                      layout=args.layout)
     plan.kernel_fft()
     f = torch.randn(n, dtype=torch.complex64, device="cuda")
     u = torch.empty_like(f)
@@ -1288,7 +1291,7 @@ def run_apply(args):
     t = sum(r["ms"] for r in rows)
     _line(METRIC, g.voxels / (t * 1e-3), METRIC, t, args.steps, args.warmup, True,
           {"workload": f"apply_{'x'.join(map(str, n))}_h{args.harmonic}", "m": list(inf.m), "zform": args.zform,
-           "staging": args.staging},
+           "staging": args.staging, "group_y": inf.group_y},
           sweeps=rows)
 
 

@@ -118,7 +118,9 @@ __device__ __forceinline__ void col2_tile(const ColSweep& p, int tile, float2* S
 #pragma unroll
         for (int a = 0; a < AH; ++a) {
           const int row = B * a + b;
-          v[a] = (colok && row < p.rows_in) ? ldg_col(&p.in[base + (long long)row * p.in_rs]) : zero;
+          v[a] = (colok && row < p.rows_in)
+                     ? ldg_col(&p.in[base + (long long)row * p.in_rs + (long long)(row >> p.in_rsh) * p.in_rs_extra])
+                     : zero;
         }
       }
       dft_reg_nz<A, false, AH>(v);

@@ -50,6 +50,7 @@ struct vp_plan_s {
   int zform = 0;            // pipelined z-sweep form (VP_ZFORM_*)
   int staging = 0;          // vp_plan_opts.staging
   int expire_waits = 0;     // vp_plan_opts.test_expire_waits
+  int group_y = 1;          // x sweep output rows grouped by this many y-planes (4 or 1)
   int* status = nullptr;    // device word: bit 0 a bounded wait expired, bit 1 an alignment refusal
   float2* tw[3] = {nullptr, nullptr, nullptr};
   int* pos[3] = {nullptr, nullptr, nullptr};   // frequency -> position after the DIF passes
@@ -327,6 +328,16 @@ ColSweep col_params(const vp_plan_s* p, int which, const float2* f, const float2
       c.rows_out = Mx;
       c.in_elems = (long long)Nx * Ny * Nz;
       c.out_elems = (long long)Mx * Ny * Nz;
+      if (p->group_y > 1) {
+        // grouped output: the G y-planes of a group are one run of G N_z columns, and
+        // consecutive x rows sit G N_z apart (the input f stays x-major)
+        const int G = p->group_y;
+        c.C = G * Nz;
+        c.n_outer = Ny / G;
+        c.in_os = (long long)G * Nz;
+        c.out_os = (long long)Mx * G * Nz;
+        c.out_rs = (long long)G * Nz;
+      }
       if (lower) {
         c.harmonic = p->harmonic;
         c.cn = (float)p->cn;
@@ -352,6 +363,13 @@ ColSweep col_params(const vp_plan_s* p, int which, const float2* f, const float2
       c.in = p->wsA;
       c.in_rs = Nz;
       c.in_os = (long long)Ny * Nz;
+      if (p->group_y > 1) {
+        // row y of column (x, z) at (y / G) M_x G N_z + x G N_z + (y % G) N_z + z
+        const int G = p->group_y;
+        c.in_os = (long long)G * Nz;
+        c.in_rsh = __builtin_ctz((unsigned)G);
+        c.in_rs_extra = (long long)Mx * G * Nz - (long long)G * Nz;
+      }
       c.rows_in = Ny;
       c.out = p->wsB;
       c.out_rs = Nz;
@@ -620,6 +638,7 @@ VP_API int vp_plan(const vp_grid* g, int harmonic_n, double f0_hz, const vp_medi
   if (harmonic_n - 1 > vp::kMaxLower) return VP_ERR_UNSUPPORTED;
   if (opts && (opts->zform < VP_ZFORM_AUTO || opts->zform > VP_ZFORM_TILE4T)) return VP_ERR_ARG;
   if (opts && (opts->staging < 0 || opts->staging > 1)) return VP_ERR_ARG;
+  if (opts && (opts->layout < 0 || opts->layout > 1)) return VP_ERR_ARG;
   if (opts && opts->autotune) {
     bool explicit_choice = false;
     for (int a = 0; a < 3; ++a) explicit_choice |= opts->m[a] != 0 || opts->radix[a][0] != 0;
@@ -628,6 +647,7 @@ VP_API int vp_plan(const vp_grid* g, int harmonic_n, double f0_hz, const vp_medi
       o.zform = opts->zform;
       o.staging = opts->staging;
       o.test_expire_waits = opts->test_expire_waits;
+      o.layout = opts->layout;
       const std::array<int, 3> key = {g->n[0], g->n[1], g->n[2]};
       bool cached = false;
       {
@@ -695,6 +715,9 @@ VP_API int vp_plan(const vp_grid* g, int harmonic_n, double f0_hz, const vp_medi
   p->zform = opts ? opts->zform : 0;
   p->staging = opts ? opts->staging : 0;
   p->expire_waits = opts && opts->test_expire_waits ? 1 : 0;
+  // the grouped layout needs the two-level engine on x (its writer) and y (its reader,
+  // which adds the group term to its row offsets); groups of 8 measured the same as 4
+  p->group_y = (!opts || opts->layout == 0) && fast[0] && fast[1] && g->n[1] % 4 == 0 ? 4 : 1;
   set_physics(p, g, harmonic_n, f0_hz, med);
 
   int st = VP_OK;
@@ -758,6 +781,7 @@ VP_API int vp_plan_get_info(vp_plan_t p, vp_plan_info* info) {
   for (int a = 0; a < 3; ++a) info->engine[a] = p->fast[a];
   info->zform = p->zform;
   info->staging = p->staging;
+  info->group_y = p->group_y;
   return VP_OK;
 }
 

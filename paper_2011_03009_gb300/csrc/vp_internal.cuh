@@ -38,11 +38,15 @@ struct AxisDesc {
 };
 
 // Column sweep: FFT along a strided axis, batched over 16 contiguous columns.
-// Element (outer o, row i, column c) lives at base + o*os + i*rs + c.
+// Element (outer o, row i, column c) lives at base + o*os + i*rs + c; an input read in
+// groups of rows (the y forward sweep over the grouped layout of the x sweep's output)
+// adds (i >> in_rsh) * in_rs_extra.
 struct ColSweep {
   const float2* in;
   float2* out;
   long long in_os, in_rs, out_os, out_rs;
+  long long in_rs_extra;  // 0 for a plain strided input
+  int in_rsh;
   int C;          // columns (contiguous extent)
   int n_outer;
   int rows_in;    // rows read (rows beyond are zero padding)

@@ -272,6 +272,8 @@ cudaError_t launch_line_sweep(const LineSweep& p, int mode, cudaStream_t s) {
 namespace vp {
 
 cudaError_t launch_col_any(const ColSweep& p, int dir, bool src, cudaStream_t s) {
+  // grouped row input: forward sweeps of the two-level engine without the source prologue
+  if (p.in_rs_extra != 0 && (!p.ax.fast || dir != kForward || src)) return cudaErrorInvalidValue;
   if (!p.ax.fast) return launch_col_sweep(p, dir, src, s);
   cudaError_t e = launch_col2_part0(p, dir, src, s);
   if (e == cudaErrorNotSupported) e = launch_col2_part1(p, dir, src, s);

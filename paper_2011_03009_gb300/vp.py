@@ -48,7 +48,8 @@ class vp_medium(ctypes.Structure):
 
 class vp_plan_opts(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int * 3), ("radix", (ctypes.c_int * MAX_PASS) * 3), ("autotune", ctypes.c_int),
-                ("zform", ctypes.c_int), ("staging", ctypes.c_int), ("test_expire_waits", ctypes.c_int)]
+                ("zform", ctypes.c_int), ("staging", ctypes.c_int), ("layout", ctypes.c_int),
+                ("test_expire_waits", ctypes.c_int)]
 
 
 class vp_plan_info(ctypes.Structure):
@@ -56,7 +57,7 @@ class vp_plan_info(ctypes.Structure):
                 ("k_re", ctypes.c_double), ("k_im", ctypes.c_double), ("c_n", ctypes.c_double),
                 ("self_re", ctypes.c_double), ("self_im", ctypes.c_double),
                 ("workspace_bytes", ctypes.c_ulonglong), ("khat_ready", ctypes.c_int), ("engine", ctypes.c_int * 3),
-                ("zform", ctypes.c_int), ("staging", ctypes.c_int)]
+                ("zform", ctypes.c_int), ("staging", ctypes.c_int), ("group_y", ctypes.c_int)]
 
 
 def _load():
@@ -178,7 +179,7 @@ class Plan:
 
     def __init__(self, grid, harmonic: int, f0: float, medium, m: Optional[Sequence[int]] = None,
                  radix: Optional[Sequence[Sequence[int]]] = None, autotune: bool = False, stream=None,
-                 zform: int = 0, staging: int = 0, test_expire_waits: bool = False):
+                 zform: int = 0, staging: int = 0, layout: int = 0, test_expire_waits: bool = False):
         self.grid = grid
         self.harmonic = int(harmonic)
         self._h = ctypes.c_void_p(0)
@@ -193,6 +194,7 @@ class Plan:
         opts.autotune = 1 if autotune else 0
         opts.zform = int(zform)
         opts.staging = int(staging)
+        opts.layout = int(layout)
         opts.test_expire_waits = 1 if test_expire_waits else 0
         g = grid if isinstance(grid, vp_grid) else grid_of(grid)
         self._g = g

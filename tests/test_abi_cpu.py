@@ -76,11 +76,12 @@ def test_plan_rejects_bad_arguments_on_the_host(vp):
     assert _plan_status(vp, good, med=neg_att)[0] == vp.VP_ERR_ARG
     st, h = _plan_status(vp, good, harmonic=99)
     assert st == vp.VP_ERR_UNSUPPORTED and not h.value
-    for staging in (-1, 2):                      # 0 bulk copies, 1 cp.async
-        o = vp.vp_plan_opts()
-        o.staging = staging
-        st, h = _plan_status(vp, good, opts=o)
-        assert st == vp.VP_ERR_ARG and not h.value
+    for field in ("staging", "layout"):          # each 0 or 1
+        for bad in (-1, 2):
+            o = vp.vp_plan_opts()
+            setattr(o, field, bad)
+            st, h = _plan_status(vp, good, opts=o)
+            assert st == vp.VP_ERR_ARG and not h.value, field
     assert vp.lib.vp_plan_check(None, None) == vp.VP_ERR_ARG
 
 

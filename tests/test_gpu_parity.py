@@ -340,6 +340,39 @@ def test_fused_source_on_two_level_engine(vp, harmonic):
     assert rel_l2(got, ref) <= REL_L2
 
 
+@pytest.mark.parametrize("n", [(20, 24, 18), (13, 36, 320), (60, 32, 64), (9, 30, 16)])
+def test_grouped_and_plain_intermediate_layouts_match_oracle(vp, n):
+    """The x sweep writes its output with x rows grouped by 4 y-planes where N_y is a
+    multiple of 4 and x, y run on the two-level engine (layout 0), or plain (layout 1);
+    with a field and with the fused source of Eq. 2.6 both match the oracle and each
+    other bit for bit (the same arithmetic in another order of memory).  N_y = 30 stays
+    plain under layout 0."""
+    g = grid(n, h=6e-5)
+    harmonic = 3
+    lower = [synth.random_field(n, seed=300 + m) for m in range(1, harmonic)]
+    f = synth.random_field(n, seed=301)
+    k = physics.wavenumber(harmonic, 1.1e6, synth.WATER)
+    outs = {}
+    for layout in (0, 1):
+        plan = vp.vp_plan(g, harmonic, 1.1e6, synth.WATER, layout=layout)
+        gy = plan.info().group_y
+        two_level = list(plan.info().engine)[:2] == [1, 1]
+        assert gy == 1 or (layout == 0 and two_level and gy > 1 and n[1] % gy == 0)
+        if layout == 0 and two_level and n[1] % 8 == 0:
+            assert gy > 1
+        vp.vp_kernel_fft(plan)
+        u = torch.empty(n, dtype=torch.complex64, device="cuda")
+        vp.vp_apply(plan, dev(f), u)
+        uf = host(u)
+        plan.source_assemble([dev(x) for x in lower])
+        plan.apply(None, u)
+        outs[layout] = (uf, host(u))
+        plan.close()
+    assert rel_l2(outs[0][0], potential.apply_fft(f, g.h, k)) <= REL_L2
+    assert rel_l2(outs[0][1], cascade.harmonic(harmonic, lower, g.h, 1.1e6, synth.WATER)) <= REL_L2
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
 def test_two_level_kernel_spectrum_octant(vp):
     n = (64, 96, 40)  # M = 128, 192, 80 -> 128, 192 two-level; 80 radix passes
     g = grid(n, h=8e-5)
