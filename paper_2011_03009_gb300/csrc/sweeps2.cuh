@@ -119,7 +119,7 @@ __device__ __forceinline__ void col2_tile(const ColSweep& p, int tile, float2* S
         for (int a = 0; a < AH; ++a) {
           const int row = B * a + b;
           v[a] = (colok && row < p.rows_in)
-                     ? ldg_col(&p.in[base + (long long)row * p.in_rs + (long long)(row >> p.in_rsh) * p.in_rs_extra])
+                     ? ldg_col(&p.in[base + (long long)row * p.in_rs + (long long)(row / kRowGroup) * p.in_rs_extra])
                      : zero;
         }
       }
@@ -198,6 +198,14 @@ template <int A, int B, int DIR, bool SRC, bool HALF>
 __global__ void __launch_bounds__(col8_threads(A, B), 2) col2_kernel8(const ColSweep p) {
   extern __shared__ __align__(16) float2 S[];
   col2_tile<A, B, DIR, SRC, HALF, 8>(p, blockIdx.x, S);
+}
+
+// 16 columns a CTA at the long lengths (one CTA an SM), 512 threads: the inverse sweeps
+// that write rows megabytes apart, whole 128-byte segments a row.
+template <int A, int B, int DIR, bool SRC, bool HALF>
+__global__ void __launch_bounds__(512, 1) col2_kernel16w(const ColSweep p) {
+  extern __shared__ __align__(16) float2 S[];
+  col2_tile<A, B, DIR, SRC, HALF>(p, blockIdx.x, S);
 }
 
 // The same, compiled for three CTAs an SM (80 registers, a few bytes of spills).  The

@@ -47,15 +47,19 @@ cudaError_t col2_launch(const ColSweep& p, cudaStream_t s) {
       // an inverse sweep whose output rows lie 1.25 MB apart or more (the x inverse
       // into the caller's x-major field from 432^3 up) writes whole 128-byte row
       // segments from 16-column CTAs: with 64-byte segments from two CTAs the writes
-      // ran at half the rate (x inverse at L = 1200: 1.53 against 1.74 ms; at L = 1024
-      // 0.81 against 0.99 ms; at L = 768, rows 1.2 MB apart, 0.40 against 0.38 ms)
+      // ran at half the rate (x inverse at L = 1200: 1.31 against 1.74 ms; at L = 1024
+      // 0.69 against 0.99 ms; at L = 768, rows 1.2 MB apart, 0.40 against 0.38 ms with
+      // 256 threads a CTA)
       if (p.out_rs * (long long)sizeof(float2) >= (5LL << 18)) {
         const size_t smem16 = (size_t)kLines2 * col2_pitch(A * B) * sizeof(float2);
         const long long b16 = (long long)((p.C + kLines2 - 1) / kLines2) * p.n_outer;
-        auto k16 = col2_kernel<A, B, DIR, SRC, HALF>;
-        cudaError_t e = grant_smem(k16, smem16, granted);
+        // 512 threads: each step's 16 A or 16 B tasks in one or two rounds (at 256
+        // threads, 1.52 against 1.31 ms at L = 1200)
+        static volatile int granted16w[64] = {0};
+        auto k16w = col2_kernel16w<A, B, DIR, SRC, HALF>;
+        cudaError_t e = grant_smem(k16w, smem16, granted16w);
         if (e != cudaSuccess) return e;
-        k16<<<(unsigned)b16, kThreads2, smem16, s>>>(p);
+        k16w<<<(unsigned)b16, 512, smem16, s>>>(p);
         return cudaGetLastError();
       }
     }

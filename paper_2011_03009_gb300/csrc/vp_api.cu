@@ -367,7 +367,6 @@ ColSweep col_params(const vp_plan_s* p, int which, const float2* f, const float2
         // row y of column (x, z) at (y / G) M_x G N_z + x G N_z + (y % G) N_z + z
         const int G = p->group_y;
         c.in_os = (long long)G * Nz;
-        c.in_rsh = __builtin_ctz((unsigned)G);
         c.in_rs_extra = (long long)Mx * G * Nz - (long long)G * Nz;
       }
       c.rows_in = Ny;
@@ -717,7 +716,7 @@ VP_API int vp_plan(const vp_grid* g, int harmonic_n, double f0_hz, const vp_medi
   p->expire_waits = opts && opts->test_expire_waits ? 1 : 0;
   // the grouped layout needs the two-level engine on x (its writer) and y (its reader,
   // which adds the group term to its row offsets); groups of 8 measured the same as 4
-  p->group_y = (!opts || opts->layout == 0) && fast[0] && fast[1] && g->n[1] % 4 == 0 ? 4 : 1;
+  p->group_y = (!opts || opts->layout == 0) && fast[0] && fast[1] && g->n[1] % vp::kRowGroup == 0 ? vp::kRowGroup : 1;
   set_physics(p, g, harmonic_n, f0_hz, med);
 
   int st = VP_OK;

@@ -39,14 +39,13 @@ struct AxisDesc {
 
 // Column sweep: FFT along a strided axis, batched over 16 contiguous columns.
 // Element (outer o, row i, column c) lives at base + o*os + i*rs + c; an input read in
-// groups of rows (the y forward sweep over the grouped layout of the x sweep's output)
-// adds (i >> in_rsh) * in_rs_extra.
+// groups of kRowGroup rows (the y forward sweep over the grouped layout of the x sweep's
+// output) adds (i / kRowGroup) * in_rs_extra.
 struct ColSweep {
   const float2* in;
   float2* out;
   long long in_os, in_rs, out_os, out_rs;
   long long in_rs_extra;  // 0 for a plain strided input
-  int in_rsh;
   int C;          // columns (contiguous extent)
   int n_outer;
   int rows_in;    // rows read (rows beyond are zero padding)
@@ -85,6 +84,10 @@ struct LineSweep {
 };
 
 enum SweepDir { kForward = 0, kInverse = 1 };
+// Rows per group of the grouped layout: a power of two that divides every second factor
+// B of the two-level engine, so that (B a + b) / kRowGroup = (B / kRowGroup) a + b / kRowGroup
+// and the group term of an unrolled column read is a constant stride.
+constexpr int kRowGroup = 4;
 enum LineMode { kConv = 0, kForwardOnly = 1 };
 
 // Launchers (vp_sweeps.cu).  Return a cudaError_t.
