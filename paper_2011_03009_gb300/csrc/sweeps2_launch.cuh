@@ -44,13 +44,13 @@ cudaError_t col2_launch(const ColSweep& p, cudaStream_t s) {
       }
     }
     if constexpr (DIR == kInverse) {
-      // an inverse sweep whose output rows lie 1.25 MB apart or more (the x inverse
-      // into the caller's x-major field from 432^3 up) writes whole 128-byte row
-      // segments from 16-column CTAs: with 64-byte segments from two CTAs the writes
-      // ran at half the rate (x inverse at L = 1200: 1.31 against 1.74 ms; at L = 1024
-      // 0.69 against 0.99 ms; at L = 768, rows 1.2 MB apart, 0.40 against 0.38 ms with
-      // 256 threads a CTA)
-      if (p.out_rs * (long long)sizeof(float2) >= (5LL << 18)) {
+      // an inverse sweep whose output rows lie 1 MB apart or more (the x inverse into
+      // the caller's x-major field from 384^3 up) writes whole 128-byte row segments
+      // from 16-column CTAs: with 64-byte segments from two CTAs the writes ran at half
+      // the rate (x inverse at L = 1200: 1.31 against 1.74 ms; at L = 1024 0.69 against
+      // 0.99 ms; at L = 768 0.33 against 0.38 ms).  The y inverse (rows N_z apart) keeps
+      // 8 columns: 16 measured slower at L = 1200 (2.63 against 2.44 ms)
+      if (p.out_rs * (long long)sizeof(float2) >= (1LL << 20)) {
         const size_t smem16 = (size_t)kLines2 * col2_pitch(A * B) * sizeof(float2);
         const long long b16 = (long long)((p.C + kLines2 - 1) / kLines2) * p.n_outer;
         // 512 threads: each step's 16 A or 16 B tasks in one or two rounds (at 256
