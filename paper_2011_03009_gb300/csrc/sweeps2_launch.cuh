@@ -173,11 +173,11 @@ cudaError_t line2_conv_pipe_launch(const LineSweep& p, cudaStream_t s, bool* use
   constexpr int L = A * B;
   constexpr int NT4 = conv4_threads(A, B);
   constexpr bool kSwap = A == 32 && B == 40;  // the transposed 4-line form (40 x 32) at L = 1280
-  // at L = 1280 the 4-line forms read their twiddles from global memory: the shared copy
-  // would cost them a resident CTA an SM (6.40 against 6.91 ms for the 600 x 600 x 640
-  // grid; at L = 1024 the extra CTA did not pay for the slower twiddle loads, 3.30 against
-  // 3.26 ms)
-  constexpr bool kTwg = L >= 1280;
+  // from L = 1024 the 4-line forms read their twiddles from global memory: the shared
+  // copy would cost them a resident CTA an SM (6.40 against 6.91 ms for the 600 x 600 x
+  // 640 grid; at L = 1024, with bulk staging, 2.98 against 3.02 ms, where with cp.async
+  // staging the extra CTA had not paid: 3.30 against 3.26 ms)
+  constexpr bool kTwg = L >= 1024;
   *used = false;
   // the kernel reads and writes the first half of each line only (zero-padded input,
   // cropped output); any other line goes to line2_kernel
