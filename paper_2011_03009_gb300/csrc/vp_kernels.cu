@@ -487,6 +487,98 @@ __global__ void __launch_bounds__(256) source_nested_tiled_kernel(const __grid_c
   }
 }
 
+// Linear form of the tiled kernel for sources with at least two voxels on every axis,
+// where every stencil is the 2 x 2 x 2 one (cnt = 2, w = (1 - f, f)): no per-target
+// stencil-size tests, and each interpolation is seven lerps a + f (b - a) on paired FP32
+// (f32x2) operations, the real and imaginary parts in one instruction each.  The
+// per-target stencil data is packed once per CTA: {row offset in the tile, (f, f)} for
+// the 16 y rows and the 64 z columns of each source, and (f, f) for x.
+struct LinStencil {
+  int off;
+  int pad;
+  float2 f;  // (f, f): the fraction on both lanes of a paired operation
+};
+
+__device__ __forceinline__ float2 lerp2(float2 a, float2 b, float2 f) {
+  return __ffma2_rn(f, __fadd2_rn(b, make_float2(-a.x, -a.y)), a);
+}
+
+template <int NS>
+__global__ void __launch_bounds__(256) source_nested_lin_kernel(const __grid_constant__ NestedSrcs<NS> q, float cn,
+                                                                float2* __restrict__ dst, int dny, int dnz, int fy,
+                                                                int fz) {
+  extern __shared__ float4 smem_raw[];
+  float2* tiles = reinterpret_cast<float2*>(smem_raw);
+  const int plane = fy * fz, tile_size = 2 * plane;
+  RStencil* st = reinterpret_cast<RStencil*>(tiles + 2 * tile_size);  // source m: x, y[16], z[64]
+  LinStencil* ls = reinterpret_cast<LinStencil*>(st + NS * kStencilsPerSrc);  // source m: x, y[16], z[64]
+  const int ix = blockIdx.z, iy0 = blockIdx.y * kRtY, iz0 = blockIdx.x * kRtZ;
+  const int lz = threadIdx.x & (kRtZ - 1);
+  for (int i = threadIdx.x; i < NS * kStencilsPerSrc; i += blockDim.x) {
+    const int m = i / kStencilsPerSrc, t = i - m * kStencilsPerSrc;
+    RStencil r;
+    if (t == 0) r.in = stencil<1>(q.m[m][0], ix, r.i0, r.w, r.cnt);
+    else if (t <= kRtY) r.in = stencil<1>(q.m[m][1], min(iy0 + t - 1, dny - 1), r.i0, r.w, r.cnt);
+    else r.in = stencil<1>(q.m[m][2], min(iz0 + t - 1 - kRtY, dnz - 1), r.i0, r.w, r.cnt);
+    st[i] = r;
+  }
+  __syncthreads();
+  // packed form: offsets from the staged block's first row and column
+  for (int i = threadIdx.x; i < NS * kStencilsPerSrc; i += blockDim.x) {
+    const int m = i / kStencilsPerSrc, t = i - m * kStencilsPerSrc;
+    const RStencil* s0 = st + m * kStencilsPerSrc;
+    LinStencil l;
+    l.pad = 0;
+    l.f = make_float2(st[i].w[1], st[i].w[1]);
+    if (t == 0) l.off = 0;
+    else if (t <= kRtY) l.off = (st[i].i0 - s0[1].i0) * fz;
+    else l.off = st[i].i0 - s0[1 + kRtY].i0;
+    ls[i] = l;
+  }
+  auto stage = [&](int m) {
+    const RStencil* s0 = st + m * kStencilsPerSrc;
+    stage_block_async<1>(q.f[m], q.sny[m], q.snz[m], s0, s0 + 1, s0 + 1 + kRtY, tiles + (m & 1) * tile_size, plane,
+                         fz);
+  };
+  stage(0);
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  if (NS > 1) stage(1);
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  float2 r[kRowsPerThread][NS];
+  const int row0 = (threadIdx.x / kRtZ) * kRowsPerThread;
+#pragma unroll
+  for (int m = 0; m < NS; ++m) {
+    asm volatile("cp.async.wait_group 1;\n" ::: "memory");  // source m's group is complete
+    __syncthreads();
+    const LinStencil* l0 = ls + m * kStencilsPerSrc;
+    const float2 fx = l0[0].f;
+    const LinStencil zl = l0[1 + kRtY + lz];
+    const float2* tile = tiles + (m & 1) * tile_size + zl.off;
+#pragma unroll
+    for (int k = 0; k < kRowsPerThread; ++k) {
+      const LinStencil yl = l0[1 + row0 + k];
+      const float2* t0 = tile + yl.off;
+      const float2* t1 = t0 + plane;
+      const float2 a0 = lerp2(t0[0], t0[1], zl.f), a1 = lerp2(t0[fz], t0[fz + 1], zl.f);
+      const float2 b0 = lerp2(t1[0], t1[1], zl.f), b1 = lerp2(t1[fz], t1[fz + 1], zl.f);
+      r[k][m] = lerp2(lerp2(a0, a1, yl.f), lerp2(b0, b1, yl.f), fx);
+    }
+    if (m + 2 < NS) {
+      __syncthreads();  // every thread is done with this tile
+      stage(m + 2);
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  }
+  const int iz = iz0 + lz;
+  if (iz >= dnz) return;
+#pragma unroll
+  for (int k = 0; k < kRowsPerThread; ++k) {
+    const int iy = iy0 + row0 + k;
+    if (iy >= dny) break;
+    dst[((long long)ix * dny + iy) * dnz + iz] = pair_products<NS>(r[k], cn);
+  }
+}
+
 // Direct form (any spacing ratio): one thread per target, gathers from global memory.
 template <int ORD, int NS>
 __global__ void __launch_bounds__(128) source_nested_kernel(const __grid_constant__ NestedSrcs<NS> q, float cn,
@@ -753,7 +845,28 @@ cudaError_t source_nested_launch(const NestedSrcDesc* d, float cn, float2* dst, 
       fy = std::max(fy, std::min(kRsY, block_footprint(d[m].b[1], kRtY, ORD)));
       fz = std::max(fz, std::min(kRsZ, block_footprint(d[m].b[2], kRtZ, ORD)));
     }
-    const size_t smem = nested_tiled_smem<ORD>(NS, fy, fz);
+    size_t smem = nested_tiled_smem<ORD>(NS, fy, fz);
+    // every source has two voxels or more on each axis: the linear kernel without
+    // stencil-size tests
+    bool lin = ORD == 1;
+    for (int m = 0; m < NS; ++m) lin = lin && d[m].n[0] >= 2 && d[m].n[1] >= 2 && d[m].n[2] >= 2;
+    if (lin) {
+      smem += sizeof(LinStencil) * (size_t)NS * kStencilsPerSrc;
+      static volatile int granted_lin[64] = {0};
+      int dev = 0;
+      cudaError_t e = cudaGetDevice(&dev);
+      if (e != cudaSuccess) return e;
+      if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+      if (!granted_lin[dev]) {
+        e = cudaFuncSetAttribute(source_nested_lin_kernel<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(nested_tiled_smem<1>(NS, kRsY, kRsZ) +
+                                       sizeof(LinStencil) * (size_t)NS * kStencilsPerSrc));
+        if (e != cudaSuccess) return e;
+        granted_lin[dev] = 1;
+      }
+      source_nested_lin_kernel<NS><<<grid, 256, smem, s>>>(q, cn, dst, nd[1], nd[2], fy, fz);
+      return cudaGetLastError();
+    }
     // the largest size, once per device; a repeated grant is harmless
     static volatile int granted[64] = {0};
     int dev = 0;

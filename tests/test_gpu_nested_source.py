@@ -72,6 +72,22 @@ def test_nested_source_every_harmonic_with_a_same_grid_field(vp, harmonic):
     plan.close()
 
 
+@pytest.mark.parametrize("quadratic", [False, True])
+def test_nested_source_from_a_one_voxel_axis(vp, quadratic):
+    """A source one voxel thick along x (one-point stencils there) takes the tiled kernel
+    with per-target stencil sizes; sources with two voxels or more on every axis (the
+    other tests, the runs) take the linear kernel without them."""
+    src = synth.Grid((1, 16, 28), (0.0005, 0.0, 0.0), 3.0e-4)
+    dst = synth.Grid((1, 37, 75), (0.0005, 0.0006, 0.0009), 0.8e-4)
+    fields = [synth.random_field(src.n, seed=81)]
+    plan = vp.vp_plan(dst, 2, F0, synth.WATER)
+    f = torch.empty(dst.n, dtype=torch.complex64, device="cuda")
+    plan.source_from_nested([src], [dev(x) for x in fields], f_out=f, quadratic=quadratic)
+    ref = oracle_source(2, [src], fields, dst, quadratic)
+    assert rel_l2(host(f), ref) <= 1e-6
+    plan.close()
+
+
 def test_nested_source_direct_form_for_a_coarser_target(vp):
     """Target spacing above the source spacing: the per-target gather form."""
     src = synth.Grid((30, 31, 32), (0.0, 0.0, 0.0), 1.0e-4)
