@@ -85,8 +85,9 @@ typedef struct vp_plan_opts {
     int autotune;       /* nonzero and no m / radix given: time the default embedding
                            against the smallest even 5-smooth one, then (zform 0 and
                            M_z >= 512 on the two-level engine) every z-sweep form on the
-                           winner (three applications each, on `stream`), and keep the
-                           fastest; cached per grid shape                                */
+                           winner (three applications each, on `stream`, with the
+                           staging and layout asked for), and keep the fastest; cached
+                           per grid shape, staging and layout                            */
     int zform;          /* form of the pipelined z sweep (two-level engine): VP_ZFORM_*;
                            0 = the form that keeps the most warps resident per SM.  A form
                            that is not compiled for M_z or does not fit in shared memory

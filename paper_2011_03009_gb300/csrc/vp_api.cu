@@ -435,11 +435,12 @@ int run_sweep(vp_plan_s* p, int which, const float2* f, const float2* const* low
 // smallest even 5-smooth size per axis (radix-pass engine unless that size is on the
 // menu).  Then, for the winner, every form of the pipelined z sweep (VP_ZFORM_*) when
 // M_z >= 512 and no form was asked for.  Each candidate is timed over three
-// applications on the caller's stream; the winners are cached per grid shape for the
-// life of the process.
+// applications on the caller's stream, with the staging and layout the caller asked
+// for; the winners are cached per grid shape, staging and layout for the life of the
+// process.
 
 std::mutex g_tune_mu;
-std::map<std::array<int, 3>, std::array<int, 4>> g_tune_cache;  // m[3], zform
+std::map<std::array<int, 5>, std::array<int, 4>> g_tune_cache;  // (n[3], staging, layout) -> m[3], zform
 
 // ---- batched evaluation ------------------------------------------------------------
 
@@ -547,7 +548,8 @@ int build_group(vp_batch_s* b, BatchGroup& g) {
   return VP_OK;
 }
 
-int autotune_m(const vp_grid* g, double f0, const vp_medium* med, cudaStream_t s, int* best_m, int* best_zform);
+int autotune_m(const vp_grid* g, double f0, const vp_medium* med, cudaStream_t s, int staging, int layout,
+               int* best_m, int* best_zform);
 
 }  // namespace
 
@@ -647,7 +649,7 @@ VP_API int vp_plan(const vp_grid* g, int harmonic_n, double f0_hz, const vp_medi
       o.staging = opts->staging;
       o.test_expire_waits = opts->test_expire_waits;
       o.layout = opts->layout;
-      const std::array<int, 3> key = {g->n[0], g->n[1], g->n[2]};
+      const std::array<int, 5> key = {g->n[0], g->n[1], g->n[2], o.staging, o.layout};
       bool cached = false;
       {
         std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -660,7 +662,7 @@ VP_API int vp_plan(const vp_grid* g, int harmonic_n, double f0_hz, const vp_medi
       }
       if (!cached) {
         int zf = o.zform;
-        const int st = autotune_m(g, f0_hz, med, (cudaStream_t)stream, o.m, &zf);
+        const int st = autotune_m(g, f0_hz, med, (cudaStream_t)stream, o.staging, o.layout, o.m, &zf);
         if (st != VP_OK) return st;
         if (o.zform == VP_ZFORM_AUTO) {
           std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -1220,7 +1222,8 @@ VP_API int vp_profile_read(vp_plan_t p, double ms[5], int count[5], int reset) {
 
 namespace {
 
-int autotune_m(const vp_grid* g, double f0, const vp_medium* med, cudaStream_t s, int* best_m, int* best_zform) {
+int autotune_m(const vp_grid* g, double f0, const vp_medium* med, cudaStream_t s, int staging, int layout,
+               int* best_m, int* best_zform) {
   int cand[2][3];
   for (int a = 0; a < 3; ++a) {
     cand[0][a] = default_m(g->n[a]);
@@ -1243,9 +1246,11 @@ int autotune_m(const vp_grid* g, double f0, const vp_medium* med, cudaStream_t s
   if (e == cudaSuccess) e = cudaEventCreate(&t1);
   // milliseconds of three applications with embedding m and z form zf (1e30: not timed)
   auto time_plan = [&](const int* m, int zf) -> float {
-    vp_plan_opts o{};
+    vp_plan_opts o{};  // (never the test hook: its waits would expire)
     for (int a = 0; a < 3; ++a) o.m[a] = m[a];
     o.zform = zf;
+    o.staging = staging;
+    o.layout = layout;
     vp_plan_t p = nullptr;
     if (vp_plan(g, 1, f0, med, &o, s, &p) != VP_OK) return 1e30f;
     p->khat_ready = true;  // timing only: the spectrum's values do not change the work
