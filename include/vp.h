@@ -118,7 +118,8 @@ typedef struct vp_plan_opts {
 #define VP_ZFORM_TILE8  2  /* 8 lines a CTA (2 mirror groups), 256 threads, M_z >= 640   */
 #define VP_ZFORM_TILE4  3  /* 4 lines a CTA (1 mirror group), 4 max(A, B) threads, M_z >= 512 */
 #define VP_ZFORM_PAIR8  4  /* 8 lines, step 2 split over lane pairs, 512 threads, M_z = 1280 */
-#define VP_ZFORM_TILE4T 5  /* 4 lines, the two steps' factors swapped (40 x 32), 160 threads, M_z = 1280 */
+#define VP_ZFORM_TILE4T 5  /* 4 lines, the two steps' factors swapped (40 x 32, 32 x 24, 32 x 20),
+                              M_z = 1280, 768, 640 */
 
 typedef struct vp_plan_info {
     int n[3];

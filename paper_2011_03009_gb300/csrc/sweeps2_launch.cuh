@@ -172,7 +172,8 @@ cudaError_t line2_conv_pipe_launch(const LineSweep& p, cudaStream_t s, bool* use
   static volatile int granted4tb[64] = {0};
   constexpr int L = A * B;
   constexpr int NT4 = conv4_threads(A, B);
-  constexpr bool kSwap = A == 32 && B == 40;  // the transposed 4-line form (40 x 32) at L = 1280
+  // the 4-line form with the two factors swapped (the shorter one in the full middle step)
+  constexpr bool kSwap = (A == 32 && B == 40) || (L >= 640 && A < B && A % 2 == 0);
   // from L = 1024 the 4-line forms read their twiddles from global memory: the shared
   // copy would cost them a resident CTA an SM (6.40 against 6.91 ms for the 600 x 600 x
   // 640 grid; at L = 1024, with bulk staging, 2.98 against 3.02 ms, where with cp.async

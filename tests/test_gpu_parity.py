@@ -415,7 +415,7 @@ def test_retargeted_plan_matches_a_fresh_plan_and_the_oracle(vp):
     plan.close()
 
 
-@pytest.mark.parametrize("nz", [256, 320, 432, 512, 640])
+@pytest.mark.parametrize("nz", [256, 320, 384, 432, 512, 640])
 def test_every_z_sweep_form_matches_oracle(vp, nz):
     """Each form of the pipelined z sweep (16-, 8- and 4-line tiles, the pair-split
     8-line form, the 4-line form with its factors swapped) at the z embeddings of the runs (M_z = 512 ... 1280), with ragged x and
