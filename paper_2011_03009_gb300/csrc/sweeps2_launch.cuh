@@ -31,10 +31,14 @@ cudaError_t col2_launch(const ColSweep& p, cudaStream_t s) {
     if (blocks <= 0) return cudaSuccess;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     if constexpr (A * B <= 864) {
-      // three CTAs an SM where a column's rows lie within 1 MB of each other (measured
-      // at L = 640-864: y sweeps 5-20 % faster, x sweeps of 384^3-432^3 grids slower)
+      // three CTAs an SM where the rows a sweep writes (forward) or reads and writes
+      // (inverse) lie within 1 MB of each other (measured at L = 640-864: y sweeps 5-20 %
+      // faster; x inverse sweeps of 384^3-432^3 grids slower; x forward sweeps into the
+      // grouped layout, whose far-apart rows are only read, 0.33 -> 0.28 ms at L = 768
+      // and 0.50 -> 0.43 ms at L = 864)
       static volatile int granted83[64] = {0};
-      const long long stride = (p.in_rs > p.out_rs ? p.in_rs : p.out_rs) * (long long)sizeof(float2);
+      const long long stride =
+          (DIR == kForward ? p.out_rs : (p.in_rs > p.out_rs ? p.in_rs : p.out_rs)) * (long long)sizeof(float2);
       if (stride < (1LL << 20)) {
         auto k3 = col2_kernel8x3<A, B, DIR, SRC, HALF>;
         cudaError_t e = grant_smem(k3, smem, granted83);
